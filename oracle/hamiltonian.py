@@ -1,0 +1,100 @@
+"""Spin-1/2 two-body Hamiltonian, matrix-free and dense (oracle).
+
+H = sum_{i<j} J_ij Z_i Z_j + sum_i h_i Z_i + sum_i Gamma_i X_i on 2^N basis
+states s; Z_i acts on bit i with z_i(s) = 1 - 2*bit_i(s) and X_i flips bit i.
+
+The paper works in matrix-free mode (Sec. II intro): H is a function taking a
+state to a state, each Pauli term "represented by a specific function"
+(Sec. III). ``apply_h`` is that function written out term by term.
+``dense_h`` builds the same operator independently, as a sum of Kronecker
+products of 2x2 Pauli matrices, for N <= 12.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def z_signs(N: int) -> np.ndarray:
+    """z_i(s) = 1 - 2*bit_i(s) as an (N, 2^N) float64 array."""
+    s = np.arange(1 << N)
+    return np.stack([1.0 - 2.0 * ((s >> i) & 1) for i in range(N)])
+
+
+def diagonal(model) -> np.ndarray:
+    """diag(s) = sum_{i<j} J_ij z_i z_j + sum_i h_i z_i for every basis state."""
+    N = model["N"]
+    z = z_signs(N)
+    d = np.zeros(1 << N)
+    for i in range(N):
+        d += model["h"][i] * z[i]
+        for j in range(i + 1, N):
+            if model["J"][i, j] != 0.0:
+                d += model["J"][i, j] * z[i] * z[j]
+    return d
+
+
+def apply_h(model, x: np.ndarray, diag: np.ndarray | None = None) -> np.ndarray:
+    """y = H x. x has shape (2^N,) or (2^N, b); columns are independent vectors."""
+    N = model["N"]
+    D = 1 << N
+    if diag is None:
+        diag = diagonal(model)
+    s = np.arange(D)
+    dd = diag if x.ndim == 1 else diag[:, None]
+    y = dd * x
+    for i in range(N):
+        g = model["gamma"][i]
+        if g != 0.0:
+            y = y + g * x[s ^ (1 << i)]
+    return y
+
+
+_I2 = np.eye(2)
+_X = np.array([[0.0, 1.0], [1.0, 0.0]])
+_Z = np.array([[1.0, 0.0], [0.0, -1.0]])
+
+
+def _site_op(N: int, ops: dict) -> np.ndarray:
+    """Kronecker product with ops[i] on spin i and identity elsewhere.
+
+    Spin i is bit i of the state index, so the factor for spin N-1 is leftmost.
+    """
+    out = np.ones((1, 1))
+    for i in reversed(range(N)):
+        out = np.kron(out, ops.get(i, _I2))
+    return out
+
+
+def dense_h(model) -> np.ndarray:
+    """Dense 2^N x 2^N matrix of H from Kronecker products (N <= 12)."""
+    N = model["N"]
+    if N > 12:
+        raise ValueError("dense_h is limited to N <= 12")
+    D = 1 << N
+    H = np.zeros((D, D))
+    for i in range(N):
+        if model["gamma"][i] != 0.0:
+            H += model["gamma"][i] * _site_op(N, {i: _X})
+        if model["h"][i] != 0.0:
+            H += model["h"][i] * _site_op(N, {i: _Z})
+        for j in range(i + 1, N):
+            if model["J"][i, j] != 0.0:
+                H += model["J"][i, j] * _site_op(N, {i: _Z, j: _Z})
+    return H
+
+
+def pauli_norm_bound(model) -> float:
+    """sum |J| + sum |h| + sum |Gamma|: a rigorous bound on the spectral radius."""
+    N = model["N"]
+    iu = np.triu_indices(N, 1)
+    return float(np.abs(model["J"][iu]).sum() + np.abs(model["h"]).sum()
+                 + np.abs(model["gamma"]).sum())
+
+
+def trace_h2_per_state(model) -> float:
+    """Tr(H^2)/2^N = sum J_ij^2 + sum h_i^2 + sum Gamma_i^2 (Pauli strings are orthonormal)."""
+    N = model["N"]
+    iu = np.triu_indices(N, 1)
+    return float((model["J"][iu] ** 2).sum() + (model["h"] ** 2).sum()
+                 + (model["gamma"] ** 2).sum())

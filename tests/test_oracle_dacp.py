@@ -1,0 +1,138 @@
+"""Pins for the oracle's DACP steps against the exact eigendecomposition.
+
+For N <= 10 the dense spectral decomposition H = sum_i E_i |phi_i><phi_i| gives
+closed forms for every step: the filtered coefficients, every moment, the
+product identity, the Gram matrices and, with a complete basis, the whole
+spectrum. The end-to-end case is the N=10 mixed-field chain against dense eigh.
+"""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import chebyshev as C
+from oracle import dacp as DA
+from oracle import hamiltonian as Hm
+from oracle import metrics as MT
+from oracle import params as P
+from tests.conftest import read_golden
+
+
+@pytest.fixture(scope="module")
+def small():
+    m = W.random_model(8, seed=21)
+    H = Hm.dense_h(m)
+    E, V = np.linalg.eigh(H)
+    emax = Hm.pauli_norm_bound(m)
+    return m, E, V, emax
+
+
+def test_filter_coefficients(small):
+    m, E, V, emax = small
+    psi = W.start_vectors(8, 2, seed=1)
+    a, K = 0.3 * emax / 4, 37
+    out = DA.exp_semicircle_filter(m, psi, emax, a, K)
+    c = V.T @ psi
+    ref = C.filter_exact(E, emax, a, K)[:, None] * c
+    ref /= np.linalg.norm(ref, axis=0)
+    assert np.abs(V.T @ out - ref).max() < 1e-12
+
+
+def test_moments_from_spectrum(small):
+    m, E, V, emax = small
+    psi = W.start_vectors(8, 2, seed=2)
+    psi /= np.linalg.norm(psi, axis=0)
+    kmax = 300
+    mu, nu = DA.chebyshev_moments(m, psi, emax, kmax)
+    c = V.T @ psi
+    for k in (0, 1, 2, 17, 150, 299, 300):
+        Tk = C.cheb_closed(k, E / emax)
+        assert np.abs(mu[k] - c.T @ (Tk[:, None] * c)).max() < 1e-12, k
+        assert np.abs(nu[k] - c.T @ ((E * Tk)[:, None] * c)).max() < 1e-11, k
+
+
+def test_product_and_doubling_identities(small):
+    m, E, V, emax = small
+    psi = W.start_vectors(8, 1, seed=3)
+    psi /= np.linalg.norm(psi)
+    vecs = DA.chebyshev_vectors(m, psi, emax, 60)
+    mu, _ = DA.chebyshev_moments(m, psi, emax, 120)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        i, j = rng.integers(0, 61, size=2)
+        lhs = float(vecs[i][:, 0] @ vecs[j][:, 0])
+        assert abs(lhs - 0.5 * (mu[i + j, 0, 0] + mu[abs(i - j), 0, 0])) < 1e-12
+    for k in range(0, 60):
+        # T_2k = 2 T_k^2 - 1 and T_{2k+1} = 2 T_{k+1} T_k - T_1
+        assert abs(mu[2 * k, 0, 0] - (2 * vecs[k][:, 0] @ vecs[k][:, 0] - mu[0, 0, 0])) < 1e-12
+        assert abs(mu[2 * k + 1, 0, 0] - (2 * vecs[k + 1][:, 0] @ vecs[k][:, 0] - mu[1, 0, 0])) < 1e-12
+
+
+def test_assembly_equals_explicit_gram(small):
+    m, E, V, emax = small
+    b = 2
+    psi = W.start_vectors(8, b, seed=4)
+    psi /= np.linalg.norm(psi, axis=0)
+    x = C.basis_orders(0.2, 4)
+    vecs = DA.chebyshev_vectors(m, psi, emax, int(x[-1]))
+    A = np.concatenate([vecs[k] for k in x], axis=1)   # column i*b + p
+    mu, nu = DA.chebyshev_moments(m, psi, emax, int(2 * x[-1]))
+    S, Hs = DA.assemble(mu, nu, x)
+    assert np.abs(S - A.T @ A).max() < 1e-12
+    assert np.abs(Hs - A.T @ Hm.apply_h(m, A)).max() < 1e-11
+
+
+def test_complete_basis_gives_whole_spectrum():
+    m = W.random_model(6, seed=9)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    emax = Hm.pauli_norm_bound(m)
+    psi = W.start_vectors(6, 1, seed=5)
+    # no filtering (K = 0) and a basis far larger than 2^6
+    r = DA.dacp(m, psi, emax, a=0.5 * emax, K=0, n=60, n_eigs=64, window=emax)
+    assert r["rank"] == 64
+    assert np.abs(r["eigs"] - E).max() < 1e-10 * emax
+
+
+def test_select_central():
+    lams = np.array([-3.0, -0.5, -0.1, 0.2, 0.4, 2.0])
+    assert np.allclose(DA.select_central(lams, 3, 1.0), [-0.1, 0.2, 0.4])
+    assert np.allclose(DA.select_central(lams, 10, 1.0), [-0.5, -0.1, 0.2, 0.4])
+
+
+def test_paper_constants(golden):
+    consts = {r[0]: float(r[1]) for r in golden("paper_parameters.txt")}
+    assert P.filter_order(1.0, 0.5, c=consts["filter_order_constant"]) == 36
+    assert P.basis_half_size(100, 1, d_ratio=1.0, basis_ratio=consts["basis_ratio"]) == 75
+    import inspect
+    assert inspect.signature(DA.solve_gep).parameters["eps"].default == consts["rank_cutoff"]
+
+
+def test_end_to_end_n10_chain_vs_dense():
+    """N=10 mixed-field chain, 100 central eigenvalues, plain FP64: error <= 1e-9 * bandwidth."""
+    m = W.chain(10)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    psi = W.start_vectors(10, 4, seed=0)
+    emax = P.emax_bound(m, psi[:, 0])
+    assert emax >= np.abs(E).max()
+    mu = P.kpm_moments(m, psi[:, 0], emax, 256)
+    a = P.kpm_window(mu, 1 << 10, emax, 2.0 * 100)
+    n = P.basis_half_size(100, 4, d_ratio=2.0)
+    K = P.filter_order(emax, a)
+    r = DA.dacp(m, psi, emax, a, K, n, 100)
+    assert len(r["eigs"]) == 100
+    ex = MT.central_exact(E, 100)
+    bandwidth = E[-1] - E[0]
+    assert np.abs(r["eigs"] - ex).max() < 1e-9 * bandwidth
+
+
+def test_planted_sign_error_is_caught(small):
+    """A wrong sign in the evolution recurrence (2Gw + w_prev) breaks the moment pin."""
+    m, E, V, emax = small
+    psi = W.start_vectors(8, 1, seed=6)[:, 0]
+    psi /= np.linalg.norm(psi)
+    v0, v1 = psi, Hm.apply_h(m, psi) / emax
+    for _ in range(2, 11):
+        v0, v1 = v1, 2 * Hm.apply_h(m, v1) / emax + v0
+    c = V.T @ psi
+    ref = c @ (C.cheb_closed(10, E / emax) * c)
+    assert abs(float(psi @ v1) - float(ref)) > 1e-3

@@ -1,0 +1,115 @@
+"""Pins for the oracle's Hamiltonian (matrix-free apply and dense builder).
+
+The bit-flip apply and the Kronecker-product builder are two independent
+constructions; on top of their agreement, closed forms (N=1, N=2), trace
+identities and symmetry-sector structure pin both against the mathematics.
+"""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hamiltonian as Hm
+from tests.conftest import read_golden
+
+
+def test_apply_matches_kronecker_dense():
+    m = W.random_model(7, seed=3)
+    x = np.random.default_rng(1).standard_normal((1 << 7, 3))
+    y = Hm.apply_h(m, x)
+    ref = Hm.dense_h(m) @ x
+    assert np.abs(y - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_single_spin_closed_form():
+    m = {"N": 1, "J": np.zeros((1, 1)), "h": np.array([0.7]), "gamma": np.array([1.3])}
+    ev = np.linalg.eigvalsh(Hm.dense_h(m))
+    r = np.hypot(0.7, 1.3)
+    assert np.allclose(ev, [-r, r], atol=1e-15)
+    # matrix-free: H^2 = (Gamma^2 + h^2) I
+    x = np.array([0.3, -1.1])
+    assert np.allclose(Hm.apply_h(m, Hm.apply_h(m, x)), r * r * x, atol=1e-14)
+
+
+def test_two_spin_chain_golden():
+    m = W.chain(2, J=1.0, hx=1.0, hz=0.0)
+    ev = np.linalg.eigvalsh(Hm.dense_h(m))
+    gold = np.array([float(r[0]) for r in read_golden("n2_chain_spectrum.txt")])
+    assert np.allclose(ev, gold, atol=1e-14)
+
+
+def test_traces():
+    m = W.random_model(8, seed=5)
+    H = Hm.dense_h(m)
+    D = H.shape[0]
+    assert abs(np.trace(H)) < 1e-11
+    assert abs(np.trace(H @ H) / D - Hm.trace_h2_per_state(m)) < 1e-11
+    assert abs(Hm.diagonal(m).sum()) < 1e-11
+
+
+def test_symmetric_operator():
+    m = W.random_model(9, seed=11)
+    rng = np.random.default_rng(2)
+    u, v = rng.standard_normal((2, 1 << 9))
+    assert abs(u @ Hm.apply_h(m, v) - Hm.apply_h(m, u) @ v) < 1e-11
+
+
+def _sector_spectra(H, P):
+    """Eigenvalues of H restricted to the +1 and -1 eigenspaces of an involution P."""
+    w, V = np.linalg.eigh(P)
+    out = []
+    for sgn in (1.0, -1.0):
+        B = V[:, np.isclose(w, sgn)]
+        out.append((B.shape[1], np.linalg.eigvalsh(B.T @ H @ B)))
+    return out
+
+
+def test_parity_sectors_h0():
+    m = W.spin_glass_shard(8, seed=4)        # h = 0 -> global spin flip is a symmetry
+    H = Hm.dense_h(m)
+    D = H.shape[0]
+    P = np.zeros((D, D))
+    P[np.arange(D) ^ (D - 1), np.arange(D)] = 1.0
+    assert np.abs(P @ H - H @ P).max() < 1e-12
+    (d1, e1), (d2, e2) = _sector_spectra(H, P)
+    assert d1 == d2 == D // 2
+    assert np.allclose(np.sort(np.concatenate([e1, e2])), np.linalg.eigvalsh(H), atol=1e-11)
+
+
+def test_reflection_sectors_uniform_chain():
+    N = 10
+    m = W.chain(N)
+    H = Hm.dense_h(m)
+    D = 1 << N
+    s = np.arange(D)
+    rev = np.zeros(D, dtype=np.int64)
+    for i in range(N):
+        rev |= ((s >> i) & 1) << (N - 1 - i)
+    R = np.zeros((D, D))
+    R[rev, s] = 1.0
+    assert np.abs(R @ H - H @ R).max() < 1e-12
+    (dp, ep), (dm, em) = _sector_spectra(H, R)
+    assert (dp, dm) == (528, 496)             # (2^N +- 2^ceil(N/2)) / 2
+    assert np.allclose(np.sort(np.concatenate([ep, em])), np.linalg.eigvalsh(H), atol=1e-10)
+
+
+def test_pauli_bound_holds():
+    for seed in range(5):
+        m = W.random_model(7, seed=seed)
+        assert np.abs(np.linalg.eigvalsh(Hm.dense_h(m))).max() <= Hm.pauli_norm_bound(m) + 1e-12
+
+
+def test_dense_limit():
+    with pytest.raises(ValueError):
+        Hm.dense_h(W.chain(13))
+
+
+def test_planted_mistake_is_caught():
+    """A transposed coupling (J_ji used as if it were J_ij+1) breaks the dense agreement."""
+    m = W.random_model(6, seed=8)
+    bad = dict(m)
+    Jb = m["J"].copy()
+    Jb[0, 2], Jb[1, 2] = Jb[1, 2], Jb[0, 2]
+    bad["J"] = Jb
+    x = np.random.default_rng(3).standard_normal(1 << 6)
+    assert np.abs(Hm.apply_h(bad, x) - Hm.dense_h(m) @ x).max() > 1e-3

@@ -1,0 +1,71 @@
+"""Pins for the oracle's parameter selection (E_max bound, KPM window)."""
+
+import math
+
+import numpy as np
+
+import workloads as W
+from oracle import chebyshev as C
+from oracle import hamiltonian as Hm
+from oracle import params as P
+
+
+def test_lanczos_complete_krylov_is_exact():
+    m = W.random_model(3, seed=2)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    v0 = np.random.default_rng(0).standard_normal(8)
+    al, be = P.lanczos_tridiagonal(m, v0, steps=8)
+    k = len(al)
+    T = np.diag(al) + np.diag(be[:k - 1], 1) + np.diag(be[:k - 1], -1)
+    th = np.linalg.eigvalsh(T)
+    assert abs(th[0] - E[0]) < 1e-9 and abs(th[-1] - E[-1]) < 1e-9
+
+
+def test_emax_is_an_upper_bound():
+    for seed in range(8):
+        m = W.random_model(8, seed=100 + seed)
+        E = np.linalg.eigvalsh(Hm.dense_h(m))
+        v0 = W.start_vectors(8, 1, seed=seed)[:, 0]
+        bnd = P.emax_bound(m, v0)
+        assert np.abs(E).max() <= bnd <= Hm.pauli_norm_bound(m) + 1e-12
+
+
+def test_kpm_moments_from_spectrum():
+    m = W.random_model(8, seed=7)
+    E, V = np.linalg.eigh(Hm.dense_h(m))
+    emax = Hm.pauli_norm_bound(m)
+    r = W.start_vectors(8, 1, seed=9)[:, 0]
+    mu = P.kpm_moments(m, r, emax, 64)
+    w = (V.T @ (r / np.linalg.norm(r))) ** 2
+    for k in (0, 1, 5, 63):
+        assert abs(mu[k] - w @ C.cheb_closed(k, E / emax)) < 1e-12
+
+
+def test_jackson_and_count_identities():
+    g = P.jackson(64)
+    assert abs(g[0] - 1.0) < 1e-12 and np.all(np.diff(g) < 0)
+    # A flat moment sequence (mu_0 = 1, others 0) is the Chebyshev weight
+    # 1/(pi sqrt(1-x^2)); its mass in [-a, a] is (pi - 2 acos a)/pi.
+    mu = np.zeros(32)
+    mu[0] = 1.0
+    for ar in (0.1, 0.5, 0.9):
+        assert abs(P.kpm_count(mu, 1, ar) - (math.pi - 2 * math.acos(ar)) / math.pi) < 1e-12
+
+
+def test_kpm_count_converges_to_weighted_count():
+    m = W.chain(10)
+    E, V = np.linalg.eigh(Hm.dense_h(m))
+    emax = P.emax_bound(m, W.start_vectors(10, 1, 0)[:, 0])
+    r = W.start_vectors(10, 1, seed=3)[:, 0]
+    w = (V.T @ (r / np.linalg.norm(r))) ** 2
+    mu = P.kpm_moments(m, r, emax, 2048)
+    a = 2.0
+    exact = 1024 * w[np.abs(E) <= a].sum()
+    assert abs(P.kpm_count(mu, 1024, a / emax) - exact) < 0.05 * exact
+    a_found = P.kpm_window(mu, 1024, emax, exact)
+    assert abs(a_found - a) < 0.1 * a
+
+
+def test_filter_order_and_basis():
+    assert P.filter_order(10.0, 1.0) == 180
+    assert P.basis_half_size(100, 4, d_ratio=2.0) == 37     # 4(2n+1) = 300
