@@ -1,0 +1,179 @@
+/*
+ * dacp.h -- C ABI of the GB300 implementation of DACP ("dual application of
+ * Chebyshev polynomial", Guan & Zhang, arXiv 2011.02107): thousands of central
+ * eigenvalues of spin-1/2 Hamiltonians
+ *
+ *     H = sum_{i<j} J_ij Z_i Z_j + sum_i h_i Z_i + sum_i Gamma_i X_i
+ *
+ * on 2^N-dimensional real state vectors, matrix-free (Sec. II intro; the
+ * paper's sigma^x sigma^x + sigma^z models of Sec. III are this form after a
+ * global Hadamard rotation). Z_i acts on bit i of the basis-state index.
+ *
+ * Conventions for every entry point
+ *   - Return a dacp_status; nothing throws across the ABI. On failure the
+ *     handle keeps a message readable with dacp_last_error().
+ *   - All host arrays are owned by the caller and only read or written during
+ *     the call. The library owns every device buffer it allocates.
+ *   - Work is ordered on the handle's CUDA stream (the `stream` given to
+ *     dacp_create, NULL = legacy default stream). Calls that return host data
+ *     synchronise that stream before returning.
+ *   - A handle is not thread-safe; separate handles are independent.
+ *   - Calling out of order (e.g. dacp_central_eigs before dacp_basis_moments)
+ *     returns DACP_ERR_STATE.
+ *   - Per-realization failures inside a batch are reported through n_found[r]
+ *     = -status, so one bad realization does not fail the batch.
+ */
+#ifndef DACP_H
+#define DACP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dacp_ctx* dacp_handle;
+
+typedef enum {
+    DACP_OK = 0,
+    DACP_ERR_ARG = 1,          /* bad argument (sizes, NULL, range)            */
+    DACP_ERR_CUDA = 2,         /* CUDA runtime error                            */
+    DACP_ERR_NOMEM = 3,        /* device allocation failed                      */
+    DACP_ERR_NUMERIC = 4,      /* NaN/Inf, or E_max is not a bound (|mu_k|>mu_0)*/
+    DACP_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                 */
+    DACP_ERR_STATE = 6,        /* call out of order                             */
+    DACP_ERR_NOT_CONVERGED = 7,/* eigensolver reported failure                  */
+    DACP_ERR_LIBRARY = 8       /* cuSOLVER / cuBLAS error                       */
+} dacp_status;
+
+typedef enum {
+    DACP_FP64 = 0,             /* float64 vectors, float64 moments (plain DACP) */
+    DACP_FP32 = 1              /* float32 vectors, float64 moments and solve    */
+} dacp_precision;
+
+/*
+ * dacp_create -- build a batch of n_real independent problems ("realizations").
+ *
+ *   n_spins[r]   N_r, 1 <= N_r <= 26.
+ *   J            concatenated row-major N_r x N_r zz couplings; only i<j read.
+ *                Realization r starts at sum_{r'<r} N_r'^2.
+ *   h, gamma     concatenated z-fields and x-fields, N_r each.
+ *   block_b      start vectors per realization (block filter, Sec. III):
+ *                1, 2, 4, 8 or 16.
+ *   precision    dacp_precision.
+ *   psi0         start vectors, float64, realization r at sum_{r'<r} 2^N_r' * b,
+ *                layout [state][column]. The paper draws them at random
+ *                (Sec. II intro); the caller supplies them.
+ *   stream       cudaStream_t or NULL.
+ * Errors: DACP_ERR_ARG for bad sizes, DACP_ERR_NOMEM if device memory runs out
+ * (nothing is leaked; *out stays NULL).
+ */
+dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins,
+                        const double* J, const double* h, const double* gamma,
+                        int block_b, int precision, const double* psi0, void* stream);
+
+/*
+ * dacp_set_params -- explicit per-realization parameters (arrays of n_real).
+ *   emax  bound on |E| (E_min = -E_max, Sec. II A); must be a true bound.
+ *   a     window half-width, 0 < a < emax (Sec. II A).
+ *   K     filter order (Eq. target; the paper uses K = 18 E_max / a). K >= 0.
+ *   n     basis half-size: b(2n+1) basis vectors (Eq. set / set2). n >= 1.
+ * Resets any filter or moment results. Errors: DACP_ERR_ARG.
+ */
+dacp_status dacp_set_params(dacp_handle hd, const double* emax, const double* a,
+                            const int* K, const int* n);
+
+/*
+ * dacp_choose_params -- the parameter heuristic of Sec. III on the GPU:
+ *   E_max: Lanczos upper-bound estimator (lanczos_steps steps on column 0 of
+ *          psi0, bound = max|Ritz| + residual norm, x(1+1e-3), clamped to the
+ *          Pauli 1-norm);
+ *   a:     kernel-polynomial DOS estimate from kpm_moments Chebyshev moments of
+ *          the same vector; [-a, a] holds d = d_ratio * n_eigs levels;
+ *   n:     b(2n+1) >= basis_ratio * d (Sec. II B: 2n+1 = 1.5 d);
+ *   K:     ceil(c_order * E_max / a) (Sec. II A: c_order = 18).
+ * Errors: DACP_ERR_ARG, DACP_ERR_CUDA.
+ */
+dacp_status dacp_choose_params(dacp_handle hd, int n_eigs, double d_ratio,
+                               double basis_ratio, double c_order,
+                               int lanczos_steps, int kpm_moments);
+
+/* dacp_get_params -- copy the parameters in use (each pointer may be NULL);
+ * kn[r] = k_n = floor(n pi / a_r), the last basis order (Eq. set2). */
+dacp_status dacp_get_params(dacp_handle hd, double* emax, double* a, int* K,
+                            int* n, int* kn);
+
+/*
+ * dacp_filter -- the exp-semicircle filter (Sec. II A, Eqs. F, chevo, target):
+ * psi_E = T_K(F) psi0 / norm, F = (H^2 - E_c)/E_0, per column, by the
+ * three-term recurrence (two fused H.v sweeps per order). Requires params.
+ */
+dacp_status dacp_filter(dacp_handle hd);
+
+/*
+ * dacp_basis_moments -- the Chebyshev evolution (Sec. II B, Appendix C):
+ * w_{k+1} = 2 G w_k - w_{k-1}, G = H/E_max, w_0 = psi_E, for k = 0..k_n,
+ * accumulating the float64 moment blocks
+ *   mu_j^{pq} = <psi_E^p| T_j(G) |psi_E^q>,  j = 0 .. 2 k_n + 1,
+ * through T_2k = 2 T_k^2 - 1 and T_{2k+1} = 2 T_{k+1} T_k - T_1. The basis
+ * vectors themselves are never stored (Appendix C). Requires dacp_filter.
+ * Errors: DACP_ERR_NUMERIC when a realization's |mu_j| exceeds mu_0 (E_max
+ * was not a bound) -- reported per realization by dacp_central_eigs.
+ */
+dacp_status dacp_basis_moments(dacp_handle hd);
+
+/*
+ * dacp_central_eigs -- assemble S and H from the moments (Appendix C,
+ * S_ij = (mu_{x_i+x_j} + mu_{|x_i-x_j|})/2 and the same with
+ * nu_k = E_max (mu_{k+1} + mu_{|k-1|})/2 for H), solve H B = S B Lambda
+ * (Eq. gep) after dropping eigenvalues of S below eps * lambda_max(S)
+ * (eps <= 0 -> 1e-12, Sec. II C), and return up to n_eigs eigenvalues of
+ * smallest |E| inside [-window, window] (window <= 0 -> a) in ascending order.
+ *   eigs     n_real * n_eigs doubles; realization r at r * n_eigs.
+ *   n_found  n_real ints: count written for r, or -dacp_status on failure.
+ *   rank     n_real ints (may be NULL): m, the retained rank of S.
+ */
+dacp_status dacp_central_eigs(dacp_handle hd, int n_eigs, double window, double eps,
+                              double* eigs, int* n_found, int* rank);
+
+/*
+ * dacp_get_moments -- copy realization r's moments mu[j][p][q], j = 0..2k_n+1
+ * (float64, (2 k_n + 2) b^2 values) into mu (capacity cap doubles).
+ * *count receives the number of doubles. Test hook.
+ */
+dacp_status dacp_get_moments(dacp_handle hd, int r, double* mu, int64_t cap, int64_t* count);
+
+/* dacp_get_filtered -- copy realization r's psi_E (2^N_r x b, float64) into
+ * psi (capacity cap doubles). Test hook. */
+dacp_status dacp_get_filtered(dacp_handle hd, int r, double* psi, int64_t cap);
+
+/*
+ * dacp_apply_h -- one matrix-free H.v of realization r (Sec. II intro):
+ * y = H x for the b columns of x. x_dev, y_dev: device pointers to 2^N_r * b
+ * values of the handle's precision (float64 or float32), layout
+ * [state][column], 16-byte aligned, not overlapping. Test hook.
+ */
+dacp_status dacp_apply_h(dacp_handle hd, int r, const void* x_dev, void* y_dev);
+
+/*
+ * dacp_get_timings -- milliseconds of the last filter, evolution and subspace
+ * solve (T_F, T_E, T_D of Sec. III, Fig. 4), measured with CUDA events on the
+ * handle's stream: ms[0] = T_F, ms[1] = T_E, ms[2] = T_D.
+ */
+dacp_status dacp_get_timings(dacp_handle hd, double* ms);
+
+/* dacp_last_error -- message of the last failure on this handle (owned by
+ * the handle, valid until the next call on it). */
+const char* dacp_last_error(dacp_handle hd);
+
+/* dacp_status_string -- static name of a status code. */
+const char* dacp_status_string(int status);
+
+/* dacp_destroy -- free every device buffer of the handle. NULL is allowed. */
+void dacp_destroy(dacp_handle hd);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DACP_H */

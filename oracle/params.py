@@ -14,7 +14,11 @@ Readings (the paper only cites these estimators):
   * DOS: kernel polynomial method -- Chebyshev moments of the same start
     vector under G = H/E_max with the Jackson kernel; the expected count in
     [-a, a] is integrated in closed form and a found by bisection so that it
-    equals d = d_ratio * n_eigs (d_ratio = 1.25 by default).
+    equals d = d_ratio * n_eigs. d_ratio = 2 by default: with K = 18 E_max/a
+    and the 1e-12 cut-off only levels with |E| below about 0.8 a survive the
+    rank removal, and the accuracy falls off toward the window edge (the
+    "inverted filter shape" of Fig. 2), so the window holds twice the levels
+    that are returned.
 ``kpm_window`` is a heuristic: parity unpinned beyond the count identity and
 the large-M convergence tested in tests/test_oracle_params.py.
 """
@@ -52,7 +56,7 @@ def lanczos_tridiagonal(model, v0, steps: int = 20, diag=None):
 
 def emax_bound(model, v0, steps: int = 20, safety: float = 1e-3, diag=None) -> float:
     """Upper bound on max |E|: Lanczos extreme Ritz values plus the residual norm."""
-    al, be = lanczos_tridiagonal(model, v0, steps, diag)
+    al, be = lanczos_tridiagonal(model, v0, min(steps, 1 << model["N"]), diag)
     k = len(al)
     T = np.diag(al) + np.diag(be[:k - 1], 1) + np.diag(be[:k - 1], -1)
     th = np.linalg.eigvalsh(T)
@@ -104,9 +108,9 @@ def kpm_count(mu, D: int, a_r: float) -> float:
 
 def kpm_window(mu, D: int, emax: float, d_target: float, iters: int = 100) -> float:
     """Window half-width a with kpm_count(a/E_max) = d_target, by bisection on a_r."""
-    lo, hi = 0.0, 1.0
-    if kpm_count(mu, D, 1.0) <= d_target:
-        return emax
+    lo, hi = 0.0, 0.999          # a < E_max keeps E_0 = (E_max^2 - a^2)/2 > 0
+    if kpm_count(mu, D, hi) <= d_target:
+        return hi * emax
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
         if kpm_count(mu, D, mid) < d_target:
@@ -116,7 +120,7 @@ def kpm_window(mu, D: int, emax: float, d_target: float, iters: int = 100) -> fl
     return 0.5 * (lo + hi) * emax
 
 
-def basis_half_size(n_eigs: int, b: int, d_ratio: float = 1.25, basis_ratio: float = 1.5) -> int:
+def basis_half_size(n_eigs: int, b: int, d_ratio: float = 2.0, basis_ratio: float = 1.5) -> int:
     """n with b(2n+1) >= basis_ratio * d, d = d_ratio * n_eigs (Sec. II B: 2n+1 = 1.5 d)."""
     d = d_ratio * n_eigs
     return max(1, int(math.ceil((basis_ratio * d / b - 1.0) / 2.0)))

@@ -1,0 +1,247 @@
+"""Python binding of the DACP C ABI (include/dacp.h), argument marshalling only.
+
+DACP -- dual application of Chebyshev polynomial (arXiv 2011.02107) -- finds
+thousands of central eigenvalues of spin-1/2 Hamiltonians
+H = sum J_ij Z_i Z_j + sum h_i Z_i + sum Gamma_i X_i. Every step runs in the
+CUDA library libdacp.so built in-tree by ``paper_2011_02107_gb300.build``;
+importing this module fails loudly when that library is missing. There is no
+CPU fallback.
+
+The module-level functions carry the C names (``dacp_create``,
+``dacp_filter``, ...); ``Dacp`` bundles them around one handle.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdacp.so")
+
+DACP_FP64 = 0
+DACP_FP32 = 1
+
+_STATUS = {0: "DACP_OK", 1: "DACP_ERR_ARG", 2: "DACP_ERR_CUDA", 3: "DACP_ERR_NOMEM", 4: "DACP_ERR_NUMERIC",
+           5: "DACP_ERR_TIMEOUT", 6: "DACP_ERR_STATE", 7: "DACP_ERR_NOT_CONVERGED", 8: "DACP_ERR_LIBRARY"}
+
+EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_params", "dacp_filter",
+           "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered",
+           "dacp_apply_h", "dacp_get_timings", "dacp_last_error", "dacp_status_string", "dacp_destroy"]
+
+
+class DacpError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libdacp.so not found at {LIB_PATH}: build it first with "
+            "`python -c \"import __graft_entry__ as g; g.build()\"` (the CUDA library is required; "
+            "there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    L = ctypes.c_int64
+    sig = {
+        "dacp_create": [ctypes.POINTER(P), I, P, P, P, P, I, I, P, P],
+        "dacp_set_params": [P, P, P, P, P],
+        "dacp_choose_params": [P, I, D, D, D, I, I],
+        "dacp_get_params": [P, P, P, P, P, P],
+        "dacp_filter": [P],
+        "dacp_basis_moments": [P],
+        "dacp_central_eigs": [P, I, D, D, P, P, P],
+        "dacp_get_moments": [P, I, P, L, ctypes.POINTER(L)],
+        "dacp_get_filtered": [P, I, P, L],
+        "dacp_apply_h": [P, I, P, P],
+        "dacp_get_timings": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = I
+    lib.dacp_last_error.argtypes = [P]
+    lib.dacp_last_error.restype = ctypes.c_char_p
+    lib.dacp_status_string.argtypes = [I]
+    lib.dacp_status_string.restype = ctypes.c_char_p
+    lib.dacp_destroy.argtypes = [P]
+    lib.dacp_destroy.restype = None
+    return lib
+
+
+_lib = _load()
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _check(h, status):
+    if status != 0:
+        msg = _lib.dacp_last_error(h).decode() if h else ""
+        raise DacpError(status, msg)
+
+
+# ---- C-named functions -----------------------------------------------------
+
+def dacp_create(n_spins, J, h, gamma, block_b, precision, psi0, stream=None):
+    n_spins = np.ascontiguousarray(n_spins, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    psi0 = np.ascontiguousarray(psi0, dtype=np.float64)
+    out = ctypes.c_void_p()
+    st = _lib.dacp_create(ctypes.byref(out), len(n_spins), _ptr(n_spins), _ptr(J), _ptr(h), _ptr(gamma),
+                          int(block_b), int(precision), _ptr(psi0),
+                          ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
+    return out.value
+
+
+def dacp_set_params(hd, emax, a, K, n):
+    emax = np.ascontiguousarray(emax, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    _check(hd, _lib.dacp_set_params(hd, _ptr(emax), _ptr(a), _ptr(K), _ptr(n)))
+
+
+def dacp_choose_params(hd, n_eigs, d_ratio=2.0, basis_ratio=1.5, c_order=18.0, lanczos_steps=20,
+                       kpm_moments=256):
+    _check(hd, _lib.dacp_choose_params(hd, int(n_eigs), float(d_ratio), float(basis_ratio), float(c_order),
+                                       int(lanczos_steps), int(kpm_moments)))
+
+
+def dacp_get_params(hd, R):
+    emax = np.zeros(R)
+    a = np.zeros(R)
+    K = np.zeros(R, dtype=np.int32)
+    n = np.zeros(R, dtype=np.int32)
+    kn = np.zeros(R, dtype=np.int32)
+    _check(hd, _lib.dacp_get_params(hd, _ptr(emax), _ptr(a), _ptr(K), _ptr(n), _ptr(kn)))
+    return {"emax": emax, "a": a, "K": K, "n": n, "kn": kn}
+
+
+def dacp_filter(hd):
+    _check(hd, _lib.dacp_filter(hd))
+
+
+def dacp_basis_moments(hd):
+    _check(hd, _lib.dacp_basis_moments(hd))
+
+
+def dacp_central_eigs(hd, R, n_eigs, window=0.0, eps=0.0):
+    eigs = np.zeros(R * n_eigs)
+    nf = np.zeros(R, dtype=np.int32)
+    rank = np.zeros(R, dtype=np.int32)
+    _check(hd, _lib.dacp_central_eigs(hd, int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(nf),
+                                      _ptr(rank)))
+    return eigs.reshape(R, n_eigs), nf, rank
+
+
+def dacp_get_moments(hd, r, cap):
+    mu = np.zeros(cap)
+    cnt = ctypes.c_int64(0)
+    _check(hd, _lib.dacp_get_moments(hd, int(r), _ptr(mu), int(cap), ctypes.byref(cnt)))
+    return mu[:cnt.value]
+
+
+def dacp_get_filtered(hd, r, n):
+    out = np.zeros(n)
+    _check(hd, _lib.dacp_get_filtered(hd, int(r), _ptr(out), int(n)))
+    return out
+
+
+def dacp_apply_h(hd, r, x_dev_ptr, y_dev_ptr):
+    _check(hd, _lib.dacp_apply_h(hd, int(r), ctypes.c_void_p(x_dev_ptr), ctypes.c_void_p(y_dev_ptr)))
+
+
+def dacp_get_timings(hd):
+    ms = np.zeros(3)
+    _check(hd, _lib.dacp_get_timings(hd, _ptr(ms)))
+    return ms
+
+
+def dacp_destroy(hd):
+    if hd:
+        _lib.dacp_destroy(hd)
+
+
+def dacp_last_error(hd):
+    return _lib.dacp_last_error(hd).decode() if hd else ""
+
+
+def dacp_status_string(s):
+    return _lib.dacp_status_string(int(s)).decode()
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class Dacp:
+    """One handle over a batch of realizations (models from ``workloads``)."""
+
+    def __init__(self, models, psi0_list, block_b=4, precision=DACP_FP64, stream=None):
+        self.models = list(models)
+        self.R = len(self.models)
+        self.b = int(block_b)
+        self.N = [m["N"] for m in self.models]
+        n_spins = np.array(self.N, dtype=np.int32)
+        J = np.concatenate([m["J"].ravel() for m in self.models])
+        h = np.concatenate([m["h"] for m in self.models])
+        g = np.concatenate([m["gamma"] for m in self.models])
+        psi0 = np.concatenate([np.ascontiguousarray(p, dtype=np.float64).ravel() for p in psi0_list])
+        self.handle = dacp_create(n_spins, J, h, g, block_b, precision, psi0, stream)
+
+    def set_params(self, emax, a, K, n):
+        R = self.R
+        dacp_set_params(self.handle, np.broadcast_to(emax, R), np.broadcast_to(a, R), np.broadcast_to(K, R),
+                        np.broadcast_to(n, R))
+
+    def choose_params(self, n_eigs, **kw):
+        dacp_choose_params(self.handle, n_eigs, **kw)
+
+    def params(self):
+        return dacp_get_params(self.handle, self.R)
+
+    def filter(self):
+        dacp_filter(self.handle)
+
+    def basis_moments(self):
+        dacp_basis_moments(self.handle)
+
+    def central_eigs(self, n_eigs, window=0.0, eps=0.0):
+        eigs, nf, rank = dacp_central_eigs(self.handle, self.R, n_eigs, window, eps)
+        return [eigs[r, :max(nf[r], 0)].copy() for r in range(self.R)], nf, rank
+
+    def moments(self, r):
+        p = self.params()
+        rows = 2 * int(p["kn"][r]) + 2
+        mu = dacp_get_moments(self.handle, r, rows * self.b * self.b)
+        return mu.reshape(rows, self.b, self.b)
+
+    def filtered(self, r):
+        n = (1 << self.N[r]) * self.b
+        return dacp_get_filtered(self.handle, r, n).reshape(1 << self.N[r], self.b)
+
+    def apply_h(self, r, x_ptr, y_ptr):
+        dacp_apply_h(self.handle, r, x_ptr, y_ptr)
+
+    def timings(self):
+        return dacp_get_timings(self.handle)
+
+    def close(self):
+        if self.handle:
+            dacp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,808 @@
+// C ABI of the DACP library: handle, parameter set-up, the two Chebyshev
+// recurrences (graph-replayed fused stencil launches) and the float64
+// subspace solve. Declarations and documentation: include/dacp.h.
+
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/dacp.h"
+#include "common.cuh"
+#include "ops.h"
+
+using namespace dacp;
+
+namespace {
+
+constexpr int kGraphOrders = 32;   // orders per captured graph
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int mode = -1;
+};
+
+}  // namespace
+
+struct dacp_ctx {
+    int R = 0, b = 1;
+    bool fp32 = false;
+    size_t esz = 8;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    std::vector<int> N;
+    std::vector<RealInfo> info;
+    std::vector<Item> items;
+    int64_t Dtot = 0;
+    int smem = 0;
+    std::vector<double> J_h, h_h, g_h;   // [R][kMaxSpins(^2)]
+    std::vector<double> pnorm;
+
+    // device
+    std::vector<void*> allocs;
+    RealInfo* info_d = nullptr;
+    Item* items_d = nullptr;
+    double *J_d = nullptr, *h_d = nullptr, *pnorm_d = nullptr;
+    void *gam_d = nullptr, *diag_d = nullptr;
+    void *psi0_d = nullptr, *A_d = nullptr, *B_d = nullptr, *U_d = nullptr, *psiE_d = nullptr;
+    double *coef_d = nullptr, *apply_coef_d = nullptr, *part_d = nullptr, *norms_d = nullptr;
+    unsigned *real_done_d = nullptr, *launch_done_d = nullptr;
+    int* step_ctr_d = nullptr;
+    double* mom_d = nullptr;
+    int64_t mom_cap = 0;
+
+    // parameters
+    std::vector<double> emax, a;
+    std::vector<int> K, n, kn;
+    int state = 0;                      // 0 created, 1 params, 2 filtered, 3 moments
+    std::vector<int> bad;               // per realization numeric failure after moments
+
+    // subspace workspace
+    cusolverDnHandle_t sol = nullptr;
+    cublasHandle_t blas = nullptr;
+    cusolverDnParams_t sp = nullptr;
+
+    Graph gf, ge;
+    cudaEvent_t ev[6] = {};
+    double t_ms[3] = {0, 0, 0};
+    std::string err;
+};
+
+namespace {
+
+dacp_status fail(dacp_ctx* c, dacp_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? DACP_ERR_NOMEM : DACP_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                             \
+    } while (0)
+
+#define CKS(call)                                                                                       \
+    do {                                                                                                \
+        cusolverStatus_t e_ = (call);                                                                   \
+        if (e_ != CUSOLVER_STATUS_SUCCESS)                                                              \
+            return fail(c, DACP_ERR_LIBRARY, "%s: cusolver status %d (%s:%d)", #call, (int)e_, __FILE__, __LINE__); \
+    } while (0)
+
+#define CKB(call)                                                                                       \
+    do {                                                                                                \
+        cublasStatus_t e_ = (call);                                                                     \
+        if (e_ != CUBLAS_STATUS_SUCCESS)                                                                \
+            return fail(c, DACP_ERR_LIBRARY, "%s: cublas status %d (%s:%d)", #call, (int)e_, __FILE__, __LINE__); \
+    } while (0)
+
+#define TRY(expr)                                 \
+    do {                                          \
+        dacp_status s_ = (expr);                  \
+        if (s_ != DACP_OK) return s_;             \
+    } while (0)
+
+dacp_status dalloc(dacp_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, DACP_ERR_NOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*p);
+    return DACP_OK;
+}
+
+template <typename T>
+dacp_status dalloc_t(dacp_ctx* c, T** p, size_t count) {
+    void* v = nullptr;
+    dacp_status s = dalloc(c, &v, count * sizeof(T));
+    *p = static_cast<T*>(v);
+    return s;
+}
+
+void dfree(dacp_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(p);
+}
+
+StepArgs base_args(dacp_ctx* c) {
+    StepArgs a;
+    memset(&a, 0, sizeof(a));
+    a.items = c->items_d;
+    a.real = c->info_d;
+    a.diag = c->diag_d;
+    a.gam = c->gam_d;
+    a.coef = c->coef_d;
+    a.bufA = c->A_d;
+    a.bufB = c->B_d;
+    a.bufU = c->U_d;
+    a.step_ctr = c->step_ctr_d;
+    a.launch_done = c->launch_done_d;
+    a.real_done = c->real_done_d;
+    a.part = c->part_d;
+    a.mom = c->mom_d;
+    return a;
+}
+
+// Launch `orders` Chebyshev orders of the filter (two stencil passes each) or of
+// the evolution (one pass each) on the handle stream. A graph of kGraphOrders
+// orders is captured once and replayed; realizations whose run is shorter
+// skip the surplus orders inside the kernel.
+dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
+    if (orders <= 0) return DACP_OK;
+    CK(cudaMemsetAsync(c->step_ctr_d, 0, sizeof(int), c->st));
+    const StepArgs a = base_args(c);
+    const int ni = static_cast<int>(c->items.size());
+    auto launch_order = [&]() -> cudaError_t {
+        cudaError_t e;
+        if (filter) {
+            if ((e = launch_step(c->fp32, c->b, kFilter1, a, 0, ni, c->smem, c->st)) != cudaSuccess) return e;
+            return launch_step(c->fp32, c->b, kFilter2, a, 0, ni, c->smem, c->st);
+        }
+        return launch_step(c->fp32, c->b, kEvolve, a, 0, ni, c->smem, c->st);
+    };
+    Graph& g = filter ? c->gf : c->ge;
+    if (!g.exec && orders >= kGraphOrders) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int i = 0; i < kGraphOrders && le == cudaSuccess; ++i) le = launch_order();
+        cudaError_t ee = cudaStreamEndCapture(c->st, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(c, DACP_ERR_CUDA, "stencil launch during capture: %s", cudaGetErrorString(le));
+        }
+        CK(ee);
+        cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ie);
+    }
+    int done = 0;
+    if (g.exec) {
+        for (; done + kGraphOrders <= orders; done += kGraphOrders) CK(cudaGraphLaunch(g.exec, c->st));
+    }
+    for (; done < orders; ++done) CK(launch_order());
+    return DACP_OK;
+}
+
+dacp_status check_handle(dacp_ctx* c) {
+    if (!c) return DACP_ERR_ARG;
+    c->err.clear();
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return fail(c, DACP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return DACP_OK;
+}
+
+// Apply explicit parameters: run lengths, moment storage.
+dacp_status apply_params(dacp_ctx* c) {
+    int64_t rows_total = 0;
+    for (int r = 0; r < c->R; ++r) {
+        const double ar = c->a[r] / c->emax[r];
+        c->kn[r] = static_cast<int>(floor(static_cast<double>(c->n[r]) * M_PI / ar));
+        c->info[r].nf = c->K[r];
+        c->info[r].ne = c->kn[r] + 1;
+        c->info[r].mom_off = rows_total;
+        rows_total += 2 * static_cast<int64_t>(c->kn[r]) + 2;
+    }
+    const int64_t need = rows_total * c->b * c->b;
+    if (need > c->mom_cap) {
+        dfree(c, c->mom_d);
+        c->mom_d = nullptr;
+        c->mom_cap = 0;
+        TRY(dalloc_t(c, &c->mom_d, static_cast<size_t>(need)));
+        c->mom_cap = need;
+    }
+    CK(cudaMemcpyAsync(c->info_d, c->info.data(), sizeof(RealInfo) * c->R, cudaMemcpyHostToDevice, c->st));
+    std::vector<double> coef(8 * static_cast<size_t>(c->R), 0.0);
+    for (int r = 0; r < c->R; ++r) {
+        const double em = c->emax[r], aa = c->a[r];
+        const double ec = (em * em + aa * aa) / 2.0, e0 = (em * em - aa * aa) / 2.0;
+        // filter: order 0 -> T_1(F) = F, then 2F w_k - w_{k-1}
+        coef[8 * r + 0] = 1.0 / e0;
+        coef[8 * r + 1] = -ec / e0;
+        coef[8 * r + 2] = 0.0;
+        coef[8 * r + 3] = 2.0 / e0;
+        coef[8 * r + 4] = -2.0 * ec / e0;
+        coef[8 * r + 5] = -1.0;
+    }
+    CK(cudaMemcpyAsync(c->coef_d, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->bad.assign(c->R, 0);
+    c->state = 1;
+    return DACP_OK;
+}
+
+dacp_status set_evolution_coef(dacp_ctx* c, const std::vector<double>& emax) {
+    std::vector<double> coef(8 * static_cast<size_t>(c->R), 0.0);
+    for (int r = 0; r < c->R; ++r) {
+        coef[8 * r + 0] = 1.0 / emax[r];
+        coef[8 * r + 1] = 0.0;
+        coef[8 * r + 3] = 2.0 / emax[r];
+        coef[8 * r + 4] = -1.0;
+    }
+    CK(cudaMemcpyAsync(c->coef_d, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    return DACP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dacp_status_string(int s) {
+    switch (s) {
+        case DACP_OK: return "DACP_OK";
+        case DACP_ERR_ARG: return "DACP_ERR_ARG";
+        case DACP_ERR_CUDA: return "DACP_ERR_CUDA";
+        case DACP_ERR_NOMEM: return "DACP_ERR_NOMEM";
+        case DACP_ERR_NUMERIC: return "DACP_ERR_NUMERIC";
+        case DACP_ERR_TIMEOUT: return "DACP_ERR_TIMEOUT";
+        case DACP_ERR_STATE: return "DACP_ERR_STATE";
+        case DACP_ERR_NOT_CONVERGED: return "DACP_ERR_NOT_CONVERGED";
+        case DACP_ERR_LIBRARY: return "DACP_ERR_LIBRARY";
+    }
+    return "DACP_ERR_UNKNOWN";
+}
+
+const char* dacp_last_error(dacp_handle c) { return c ? c->err.c_str() : "NULL handle"; }
+
+void dacp_destroy(dacp_handle c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->st) cudaStreamSynchronize(c->st);
+    if (c->gf.exec) cudaGraphExecDestroy(c->gf.exec);
+    if (c->ge.exec) cudaGraphExecDestroy(c->ge.exec);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->sp) cusolverDnDestroyParams(c->sp);
+    if (c->sol) cusolverDnDestroy(c->sol);
+    if (c->blas) cublasDestroy(c->blas);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const double* J, const double* h,
+                        const double* gamma, int block_b, int precision, const double* psi0, void* stream) {
+    if (!out) return DACP_ERR_ARG;
+    *out = nullptr;
+    if (n_real <= 0 || !n_spins || !J || !h || !gamma || !psi0) return DACP_ERR_ARG;
+    if (!(block_b == 1 || block_b == 2 || block_b == 4)) return DACP_ERR_ARG;
+    if (precision != DACP_FP64 && precision != DACP_FP32) return DACP_ERR_ARG;
+    for (int r = 0; r < n_real; ++r)
+        if (n_spins[r] < 1 || n_spins[r] > kMaxSpins) return DACP_ERR_ARG;
+
+    dacp_ctx* c = new dacp_ctx();
+    auto bail = [&](dacp_status s) {
+        dacp_destroy(c);
+        return s;
+    };
+    cudaGetDevice(&c->device);
+    c->R = n_real;
+    c->b = block_b;
+    c->fp32 = precision == DACP_FP32;
+    c->esz = c->fp32 ? 4 : 8;
+    if (stream) {
+        c->st = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) return bail(DACP_ERR_CUDA);
+        c->own_stream = true;
+    }
+    c->N.assign(n_spins, n_spins + n_real);
+    c->info.resize(n_real);
+    c->J_h.assign(static_cast<size_t>(n_real) * kMaxSpins * kMaxSpins, 0.0);
+    c->h_h.assign(static_cast<size_t>(n_real) * kMaxSpins, 0.0);
+    c->g_h.assign(static_cast<size_t>(n_real) * kMaxSpins, 0.0);
+    c->pnorm.assign(n_real, 0.0);
+    // tile: at most kTileBytes of the vector per CTA
+    int tb_cap = 0;
+    while ((static_cast<int64_t>(2) << tb_cap) * block_b * static_cast<int64_t>(c->esz) <= kTileBytes) ++tb_cap;
+    int64_t jo = 0, ho = 0, off = 0;
+    int max_tstates = 1;
+    for (int r = 0; r < n_real; ++r) {
+        const int Nr = n_spins[r];
+        RealInfo& R = c->info[r];
+        R.N = Nr;
+        R.tbits = std::min(Nr, tb_cap);
+        R.off = off;
+        R.item_begin = static_cast<int>(c->items.size());
+        R.item_count = 1 << (Nr - R.tbits);
+        R.nf = 0;
+        R.ne = 0;
+        R.mom_off = 0;
+        for (int t = 0; t < R.item_count; ++t) c->items.push_back(Item{r, t});
+        max_tstates = std::max(max_tstates, 1 << R.tbits);
+        double pn = 0.0;
+        for (int i = 0; i < Nr; ++i) {
+            for (int j = 0; j < Nr; ++j) {
+                const double v = J[jo + static_cast<int64_t>(i) * Nr + j];
+                if (j > i) {
+                    c->J_h[static_cast<size_t>(r) * kMaxSpins * kMaxSpins + i * kMaxSpins + j] = v;
+                    pn += fabs(v);
+                }
+            }
+            const double hv = h[ho + i], gv = gamma[ho + i];
+            if (!isfinite(hv) || !isfinite(gv)) return bail(fail(c, DACP_ERR_ARG, "non-finite field"));
+            c->h_h[static_cast<size_t>(r) * kMaxSpins + i] = hv;
+            c->g_h[static_cast<size_t>(r) * kMaxSpins + i] = gv;
+            pn += fabs(hv) + fabs(gv);
+        }
+        if (!isfinite(pn)) {
+            dacp_destroy(c);
+            return DACP_ERR_ARG;
+        }
+        c->pnorm[r] = pn;
+        jo += static_cast<int64_t>(Nr) * Nr;
+        ho += Nr;
+        off += static_cast<int64_t>(1) << Nr;
+    }
+    c->Dtot = off;
+    c->smem = static_cast<int>(max_tstates * block_b * c->esz);
+    c->emax.assign(n_real, 0.0);
+    c->a.assign(n_real, 0.0);
+    c->K.assign(n_real, 0);
+    c->n.assign(n_real, 0);
+    c->kn.assign(n_real, 0);
+    c->bad.assign(n_real, 0);
+
+    const size_t vec_bytes = static_cast<size_t>(c->Dtot) * block_b * c->esz;
+    const int ni = static_cast<int>(c->items.size());
+    dacp_status s;
+#define ALLOC(expr) if ((s = (expr)) != DACP_OK) return bail(s)
+    ALLOC(dalloc_t(c, &c->info_d, n_real));
+    ALLOC(dalloc_t(c, &c->items_d, ni));
+    ALLOC(dalloc_t(c, &c->J_d, c->J_h.size()));
+    ALLOC(dalloc_t(c, &c->h_d, c->h_h.size()));
+    ALLOC(dalloc_t(c, &c->pnorm_d, n_real));
+    ALLOC(dalloc(c, &c->gam_d, c->g_h.size() * c->esz));
+    ALLOC(dalloc(c, &c->diag_d, static_cast<size_t>(c->Dtot) * c->esz));
+    ALLOC(dalloc(c, &c->psi0_d, vec_bytes));
+    ALLOC(dalloc(c, &c->A_d, vec_bytes));
+    ALLOC(dalloc(c, &c->B_d, vec_bytes));
+    ALLOC(dalloc(c, &c->U_d, vec_bytes));
+    ALLOC(dalloc(c, &c->psiE_d, vec_bytes));
+    ALLOC(dalloc_t(c, &c->coef_d, 8 * static_cast<size_t>(n_real)));
+    ALLOC(dalloc_t(c, &c->apply_coef_d, 8 * static_cast<size_t>(n_real)));
+    ALLOC(dalloc_t(c, &c->part_d, static_cast<size_t>(ni) * 2 * block_b * block_b + 64));
+    ALLOC(dalloc_t(c, &c->norms_d, static_cast<size_t>(n_real) * block_b));
+    ALLOC(dalloc_t(c, &c->real_done_d, n_real));
+    ALLOC(dalloc_t(c, &c->launch_done_d, 1));
+    ALLOC(dalloc_t(c, &c->step_ctr_d, 1));
+#undef ALLOC
+
+    auto ck = [&](cudaError_t e) { return e == cudaSuccess; };
+    bool ok = ck(cudaMemcpyAsync(c->info_d, c->info.data(), sizeof(RealInfo) * n_real, cudaMemcpyHostToDevice, c->st)) &&
+              ck(cudaMemcpyAsync(c->items_d, c->items.data(), sizeof(Item) * ni, cudaMemcpyHostToDevice, c->st)) &&
+              ck(cudaMemcpyAsync(c->J_d, c->J_h.data(), c->J_h.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
+              ck(cudaMemcpyAsync(c->h_d, c->h_h.data(), c->h_h.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
+              ck(cudaMemcpyAsync(c->pnorm_d, c->pnorm.data(), n_real * 8, cudaMemcpyHostToDevice, c->st)) &&
+              ck(cudaMemsetAsync(c->real_done_d, 0, sizeof(unsigned) * n_real, c->st)) &&
+              ck(cudaMemsetAsync(c->launch_done_d, 0, sizeof(unsigned), c->st));
+    if (!ok) return bail(fail(c, DACP_ERR_CUDA, "upload failed"));
+    // x-fields in the vector precision
+    {
+        double* tmp = nullptr;
+        if ((s = dalloc_t(c, &tmp, c->g_h.size())) != DACP_OK) return bail(s);
+        ok = ck(cudaMemcpyAsync(tmp, c->g_h.data(), c->g_h.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
+             ck(launch_convert(c->fp32, tmp, c->gam_d, static_cast<int64_t>(c->g_h.size()), c->st));
+        // start vectors: host float64 -> device, converted in place of psi0
+        double* tmp2 = nullptr;
+        const int64_t nv = c->Dtot * block_b;
+        if (ok && (s = dalloc_t(c, &tmp2, static_cast<size_t>(nv))) != DACP_OK) return bail(s);
+        ok = ok && ck(cudaMemcpyAsync(tmp2, psi0, static_cast<size_t>(nv) * 8, cudaMemcpyHostToDevice, c->st)) &&
+             ck(launch_convert(c->fp32, tmp2, c->psi0_d, nv, c->st));
+        for (int r = 0; ok && r < n_real; ++r) ok = ck(launch_diag(c->fp32, c->info_d, r, c->N[r], c->J_d, c->h_d, c->diag_d, c->st));
+        std::vector<double> ac(8 * static_cast<size_t>(n_real), 0.0);
+        for (int r = 0; r < n_real; ++r) ac[8 * r] = 1.0;
+        ok = ok && ck(cudaMemcpyAsync(c->apply_coef_d, ac.data(), ac.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
+             ck(cudaStreamSynchronize(c->st));
+        dfree(c, tmp);
+        dfree(c, tmp2);
+        if (!ok) return bail(fail(c, DACP_ERR_CUDA, "set-up kernels failed: %s", cudaGetErrorString(cudaGetLastError())));
+    }
+    // b-column stencil for the recurrences, 1-column stencil for the Lanczos / KPM pre-pass
+    if (prepare_step(c->fp32, block_b, c->smem) != cudaSuccess || prepare_step(c->fp32, 1, c->smem) != cudaSuccess)
+        return bail(DACP_ERR_CUDA);
+    for (auto& e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(DACP_ERR_CUDA);
+    if (cusolverDnCreate(&c->sol) != CUSOLVER_STATUS_SUCCESS || cusolverDnSetStream(c->sol, c->st) != CUSOLVER_STATUS_SUCCESS ||
+        cusolverDnCreateParams(&c->sp) != CUSOLVER_STATUS_SUCCESS)
+        return bail(DACP_ERR_LIBRARY);
+    if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS || cublasSetStream(c->blas, c->st) != CUBLAS_STATUS_SUCCESS)
+        return bail(DACP_ERR_LIBRARY);
+    *out = c;
+    return DACP_OK;
+}
+
+dacp_status dacp_set_params(dacp_handle c, const double* emax, const double* a, const int* K, const int* n) {
+    TRY(check_handle(c));
+    if (!emax || !a || !K || !n) return fail(c, DACP_ERR_ARG, "NULL parameter array");
+    for (int r = 0; r < c->R; ++r) {
+        if (!(emax[r] > 0.0) || !(a[r] > 0.0) || !(a[r] < emax[r]) || K[r] < 0 || n[r] < 1 || !isfinite(emax[r]))
+            return fail(c, DACP_ERR_ARG, "bad parameters for realization %d", r);
+        const double kn = floor(static_cast<double>(n[r]) * M_PI / (a[r] / emax[r]));
+        if (kn > 2.0e8) return fail(c, DACP_ERR_ARG, "k_n too large for realization %d", r);
+    }
+    c->emax.assign(emax, emax + c->R);
+    c->a.assign(a, a + c->R);
+    c->K.assign(K, K + c->R);
+    c->n.assign(n, n + c->R);
+    return apply_params(c);
+}
+
+dacp_status dacp_choose_params(dacp_handle c, int n_eigs, double d_ratio, double basis_ratio, double c_order,
+                               int lanczos_steps, int kpm_moments) {
+    TRY(check_handle(c));
+    if (n_eigs < 1 || !(d_ratio > 0) || !(basis_ratio > 0) || !(c_order > 0) || lanczos_steps < 2 ||
+        lanczos_steps > 64 || kpm_moments < 2 || (kpm_moments & 1))
+        return fail(c, DACP_ERR_ARG, "bad heuristic arguments");
+    int minN = kMaxSpins;
+    for (int r = 0; r < c->R; ++r) minN = std::min(minN, c->N[r]);
+    const int steps = static_cast<int>(std::min<int64_t>(lanczos_steps, static_cast<int64_t>(1) << minN));
+    const int R = c->R;
+    const int ni = static_cast<int>(c->items.size());
+    const size_t sv = static_cast<size_t>(c->Dtot) * c->esz;   // one column
+    void *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *kA = nullptr, *kB = nullptr;
+    double *lmom = nullptr, *beta2 = nullptr, *emax_d = nullptr, *a_d = nullptr, *kp = nullptr;
+    int *K_d = nullptr, *n_d = nullptr;
+    auto cleanup = [&]() {
+        for (void* p : {v0, v1, v2, kA, kB, static_cast<void*>(lmom), static_cast<void*>(beta2),
+                        static_cast<void*>(emax_d), static_cast<void*>(a_d), static_cast<void*>(kp),
+                        static_cast<void*>(K_d), static_cast<void*>(n_d)})
+            dfree(c, p);
+    };
+    dacp_status s = DACP_OK;
+    auto run = [&]() -> dacp_status {
+        TRY(dalloc(c, &v0, sv));
+        TRY(dalloc(c, &v1, sv));
+        TRY(dalloc(c, &v2, sv));
+        TRY(dalloc(c, &kA, sv));
+        TRY(dalloc(c, &kB, sv));
+        const int rows = 2 * steps;
+        TRY(dalloc_t(c, &lmom, static_cast<size_t>(R) * rows));
+        TRY(dalloc_t(c, &beta2, static_cast<size_t>(R) * steps));
+        TRY(dalloc_t(c, &emax_d, R));
+        TRY(dalloc_t(c, &a_d, R));
+        TRY(dalloc_t(c, &kp, static_cast<size_t>(R) * kpm_moments));
+        TRY(dalloc_t(c, &K_d, R));
+        TRY(dalloc_t(c, &n_d, R));
+        // v = column 0 of psi0, normalised; kept in kA for the KPM run
+        CK(launch_extract_col(c->fp32, c->b, c->psi0_d, v2, c->Dtot, c->st));
+        CK(launch_normalize(c->fp32, 1, c->items_d, c->info_d, ni, v2, v2, 0, c->part_d, c->real_done_d,
+                            c->norms_d, v1, kA, c->st));
+        // Lanczos: w = H v - beta v_prev; alpha = <w, v>; w -= alpha v; beta = |w|
+        std::vector<double> lc(8 * static_cast<size_t>(R), 0.0);
+        for (int r = 0; r < R; ++r) lc[8 * r] = 1.0;
+        CK(cudaMemcpyAsync(c->apply_coef_d, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice, c->st));
+        void* vp = v0;   // v_{j-1}
+        void* vc = v1;   // v_j
+        void* w = v2;
+        CK(cudaMemsetAsync(vp, 0, sv, c->st));
+        for (int j = 0; j < steps; ++j) {
+            StepArgs a = base_args(c);
+            a.coef = c->apply_coef_d;
+            a.x = vc;
+            a.y1 = vp;
+            a.out = w;
+            a.apply_moments = 1;
+            a.apply_row = j;
+            a.mom = lmom;
+            a.mom_rows_fixed = rows;
+            CK(launch_step(c->fp32, 1, kApply, a, 0, ni, c->smem, c->st));
+            CK(launch_lanczos_orth(c->fp32, c->items_d, c->info_d, ni, vc, w, lmom, rows, j, c->part_d,
+                                   c->real_done_d, beta2, steps, c->st));
+            CK(launch_lanczos_scale(c->fp32, c->items_d, c->info_d, ni, w, beta2, j, steps, c->apply_coef_d, R, c->st));
+            void* t = vp;
+            vp = vc;
+            vc = w;
+            w = t;
+        }
+        CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax_d, c->st));
+        // reset the apply coefficients of the test hook
+        for (int r = 0; r < R; ++r) lc[8 * r + 1] = 0.0;
+        CK(cudaMemcpyAsync(c->apply_coef_d, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice, c->st));
+        std::vector<double> em(R);
+        CK(cudaMemcpyAsync(em.data(), emax_d, R * 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        // KPM moments of the normalised start vector under G = H / E_max
+        TRY(set_evolution_coef(c, em));
+        StepArgs a = base_args(c);
+        a.bufA = kA;
+        a.bufB = kB;
+        a.mom = kp;
+        a.mom_rows_fixed = kpm_moments;
+        a.nsteps_override = kpm_moments / 2;
+        CK(cudaMemsetAsync(c->step_ctr_d, 0, sizeof(int), c->st));
+        for (int k = 0; k < kpm_moments / 2; ++k) CK(launch_step(c->fp32, 1, kEvolve, a, 0, ni, c->smem, c->st));
+        CK(launch_kpm_window(R, c->info_d, kp, kpm_moments, emax_d, d_ratio * n_eigs, c_order, basis_ratio, c->b,
+                             a_d, K_d, n_d, c->st));
+        std::vector<double> av(R);
+        std::vector<int> Kv(R), nv(R);
+        CK(cudaMemcpyAsync(av.data(), a_d, R * 8, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(Kv.data(), K_d, R * 4, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(nv.data(), n_d, R * 4, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        c->emax = em;
+        c->a = av;
+        c->K = Kv;
+        c->n = nv;
+        return apply_params(c);
+    };
+    s = run();
+    cleanup();
+    return s;
+}
+
+dacp_status dacp_get_params(dacp_handle c, double* emax, double* a, int* K, int* n, int* kn) {
+    TRY(check_handle(c));
+    if (c->state < 1) return fail(c, DACP_ERR_STATE, "no parameters set");
+    for (int r = 0; r < c->R; ++r) {
+        if (emax) emax[r] = c->emax[r];
+        if (a) a[r] = c->a[r];
+        if (K) K[r] = c->K[r];
+        if (n) n[r] = c->n[r];
+        if (kn) kn[r] = c->kn[r];
+    }
+    return DACP_OK;
+}
+
+dacp_status dacp_filter(dacp_handle c) {
+    TRY(check_handle(c));
+    if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_filter before parameters");
+    const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
+    int maxK = 0;
+    for (int r = 0; r < c->R; ++r) maxK = std::max(maxK, c->K[r]);
+    CK(cudaEventRecord(c->ev[0], c->st));
+    CK(cudaMemcpyAsync(c->A_d, c->psi0_d, vec_bytes, cudaMemcpyDeviceToDevice, c->st));
+    TRY(run_orders(c, true, maxK));
+    // psi_E = w_K / |w_K| per column; w_K sits in A (K even) or B (K odd); also w_0 of the evolution
+    CK(launch_normalize(c->fp32, c->b, c->items_d, c->info_d, static_cast<int>(c->items.size()), c->A_d, c->B_d, 1,
+                        c->part_d, c->real_done_d, c->norms_d, c->psiE_d, nullptr, c->st));
+    CK(cudaEventRecord(c->ev[1], c->st));
+    CK(cudaStreamSynchronize(c->st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+    c->t_ms[0] = ms;
+    c->state = 2;
+    return DACP_OK;
+}
+
+dacp_status dacp_basis_moments(dacp_handle c) {
+    TRY(check_handle(c));
+    if (c->state < 2) return fail(c, DACP_ERR_STATE, "dacp_basis_moments before dacp_filter");
+    const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
+    int maxE = 0;
+    for (int r = 0; r < c->R; ++r) maxE = std::max(maxE, c->info[r].ne);
+    TRY(set_evolution_coef(c, c->emax));
+    CK(cudaEventRecord(c->ev[2], c->st));
+    CK(cudaMemcpyAsync(c->A_d, c->psiE_d, vec_bytes, cudaMemcpyDeviceToDevice, c->st));
+    TRY(run_orders(c, false, maxE));
+    CK(cudaEventRecord(c->ev[3], c->st));
+    CK(cudaStreamSynchronize(c->st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    c->t_ms[1] = ms;
+    // restore the filter coefficients for a later dacp_filter
+    TRY(apply_params(c));
+    c->state = 3;
+    return DACP_OK;
+}
+
+dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double eps, double* eigs, int* n_found,
+                              int* rank) {
+    TRY(check_handle(c));
+    if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_central_eigs before dacp_basis_moments");
+    if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
+    if (!(eps > 0.0)) eps = 1e-12;
+    const int b = c->b;
+    int Mmax = 0;
+    int64_t rows_max = 0;
+    for (int r = 0; r < c->R; ++r) {
+        Mmax = std::max(Mmax, b * (2 * c->n[r] + 1));
+        rows_max = std::max<int64_t>(rows_max, 2 * static_cast<int64_t>(c->kn[r]) + 2);
+    }
+    double *S = nullptr, *H = nullptr, *W = nullptr, *Ht = nullptr, *lam = nullptr, *lamt = nullptr, *mus = nullptr,
+           *nus = nullptr, *sel = nullptr;
+    int *orders = nullptr, *mi = nullptr, *bad = nullptr, *info = nullptr, *nf = nullptr;
+    void* work = nullptr;
+    std::vector<char> work_h;
+    auto cleanup = [&]() {
+        for (void* p : {static_cast<void*>(S), static_cast<void*>(H), static_cast<void*>(W), static_cast<void*>(Ht),
+                        static_cast<void*>(lam), static_cast<void*>(lamt), static_cast<void*>(mus),
+                        static_cast<void*>(nus), static_cast<void*>(sel), static_cast<void*>(orders),
+                        static_cast<void*>(mi), static_cast<void*>(bad), static_cast<void*>(info),
+                        static_cast<void*>(nf), work})
+            dfree(c, p);
+    };
+    auto run = [&]() -> dacp_status {
+        const size_t MM = static_cast<size_t>(Mmax) * Mmax;
+        TRY(dalloc_t(c, &S, MM));
+        TRY(dalloc_t(c, &H, MM));
+        TRY(dalloc_t(c, &W, MM));
+        TRY(dalloc_t(c, &Ht, MM));
+        TRY(dalloc_t(c, &lam, Mmax));
+        TRY(dalloc_t(c, &lamt, Mmax));
+        TRY(dalloc_t(c, &mus, static_cast<size_t>(rows_max) * b * b));
+        TRY(dalloc_t(c, &nus, static_cast<size_t>(rows_max) * b * b));
+        TRY(dalloc_t(c, &sel, static_cast<size_t>(n_eigs)));
+        TRY(dalloc_t(c, &orders, Mmax));
+        TRY(dalloc_t(c, &mi, 4));
+        TRY(dalloc_t(c, &bad, 1));
+        TRY(dalloc_t(c, &info, 1));
+        TRY(dalloc_t(c, &nf, 1));
+        size_t dbytes = 0, hbytes = 0;
+        CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, Mmax,
+                                        CUDA_R_64F, S, Mmax, CUDA_R_64F, lam, CUDA_R_64F, &dbytes, &hbytes));
+        TRY(dalloc(c, &work, dbytes));
+        work_h.resize(std::max<size_t>(hbytes, 1));
+        CK(cudaEventRecord(c->ev[4], c->st));
+        for (int r = 0; r < c->R; ++r) {
+            const int L = 2 * c->n[r] + 1;
+            const int M = b * L;
+            const int rows = 2 * c->kn[r] + 2;
+            double* out = eigs + static_cast<size_t>(r) * n_eigs;
+            CK(cudaMemsetAsync(bad, 0, sizeof(int), c->st));
+            CK(launch_orders(L, c->a[r] / c->emax[r], orders, c->st));
+            CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], mus, nus, bad, c->st));
+            CK(launch_assemble(L, b, orders, mus, nus, S, H, c->st));
+            // S = V Lam_s V^T (in place), ascending
+            CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, S, M,
+                                 CUDA_R_64F, lam, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, info));
+            CK(launch_cutoff(lam, M, eps, 0, S, mi, c->st));
+            int hv[3] = {0, 0, 0};
+            CK(cudaMemcpyAsync(&hv[0], mi, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(&hv[1], bad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(&hv[2], info, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            const int m = hv[0];
+            if (rank) rank[r] = m;
+            if (hv[1]) {
+                n_found[r] = -DACP_ERR_NUMERIC;
+                continue;
+            }
+            if (hv[2] != 0 || m < 1) {
+                n_found[r] = -DACP_ERR_NOT_CONVERGED;
+                continue;
+            }
+            const double* U = S + static_cast<size_t>(M - m) * M;
+            const double one = 1.0, zero = 0.0;
+            // W = H U (M x m); Ht = U^T W (m x m)
+            CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m, M, &one, H, M, U, M, &zero, W, M));
+            CKB(cublasDgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, M, &one, U, M, W, M, &zero, Ht, m));
+            CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, Ht,
+                                 m, CUDA_R_64F, lamt, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, info));
+            const double w = window > 0.0 ? window : c->a[r];
+            CK(launch_select(lamt, m, n_eigs, w, sel, nf, c->st));
+            int cnt = 0;
+            CK(cudaMemcpyAsync(&cnt, nf, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(&hv[2], info, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            if (hv[2] != 0) {
+                n_found[r] = -DACP_ERR_NOT_CONVERGED;
+                continue;
+            }
+            CK(cudaMemcpyAsync(out, sel, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
+            n_found[r] = cnt;
+        }
+        CK(cudaEventRecord(c->ev[5], c->st));
+        CK(cudaStreamSynchronize(c->st));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+        c->t_ms[2] = ms;
+        return DACP_OK;
+    };
+    dacp_status s = run();
+    cleanup();
+    return s;
+}
+
+dacp_status dacp_get_moments(dacp_handle c, int r, double* mu, int64_t cap, int64_t* count) {
+    TRY(check_handle(c));
+    if (c->state < 3) return fail(c, DACP_ERR_STATE, "no moments yet");
+    if (r < 0 || r >= c->R || !mu) return fail(c, DACP_ERR_ARG, "bad realization or buffer");
+    const int b = c->b;
+    const int rows = 2 * c->kn[r] + 2;
+    const int64_t nvals = static_cast<int64_t>(rows) * b * b;
+    if (count) *count = nvals;
+    if (cap < nvals) return fail(c, DACP_ERR_ARG, "capacity %lld < %lld", (long long)cap, (long long)nvals);
+    double *mus = nullptr, *nus = nullptr;
+    int* bad = nullptr;
+    auto run = [&]() -> dacp_status {
+        TRY(dalloc_t(c, &mus, static_cast<size_t>(nvals)));
+        TRY(dalloc_t(c, &nus, static_cast<size_t>(nvals)));
+        TRY(dalloc_t(c, &bad, 1));
+        CK(cudaMemsetAsync(bad, 0, sizeof(int), c->st));
+        CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], mus, nus, bad, c->st));
+        CK(cudaMemcpyAsync(mu, mus, sizeof(double) * nvals, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        return DACP_OK;
+    };
+    dacp_status s = run();
+    dfree(c, mus);
+    dfree(c, nus);
+    dfree(c, bad);
+    return s;
+}
+
+dacp_status dacp_get_filtered(dacp_handle c, int r, double* psi, int64_t cap) {
+    TRY(check_handle(c));
+    if (c->state < 2) return fail(c, DACP_ERR_STATE, "no filtered vectors yet");
+    if (r < 0 || r >= c->R || !psi) return fail(c, DACP_ERR_ARG, "bad realization or buffer");
+    const int64_t n = (static_cast<int64_t>(1) << c->N[r]) * c->b;
+    if (cap < n) return fail(c, DACP_ERR_ARG, "capacity too small");
+    double* tmp = nullptr;
+    auto run = [&]() -> dacp_status {
+        TRY(dalloc_t(c, &tmp, static_cast<size_t>(n)));
+        const char* src = static_cast<const char*>(c->psiE_d) + static_cast<size_t>(c->info[r].off) * c->b * c->esz;
+        CK(launch_to_double(c->fp32, src, tmp, n, c->st));
+        CK(cudaMemcpyAsync(psi, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        return DACP_OK;
+    };
+    dacp_status s = run();
+    dfree(c, tmp);
+    return s;
+}
+
+dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
+    TRY(check_handle(c));
+    if (r < 0 || r >= c->R || !x_dev || !y_dev || x_dev == y_dev) return fail(c, DACP_ERR_ARG, "bad arguments");
+    if ((reinterpret_cast<uintptr_t>(x_dev) & 15) || (reinterpret_cast<uintptr_t>(y_dev) & 15))
+        return fail(c, DACP_ERR_ARG, "x and y must be 16-byte aligned");
+    StepArgs a = base_args(c);
+    a.coef = c->apply_coef_d;
+    // the kernel indexes x and y by the batch offset of realization r
+    const size_t shift = static_cast<size_t>(c->info[r].off) * c->b * c->esz;
+    a.x = static_cast<const char*>(x_dev) - shift;
+    a.y1 = nullptr;
+    a.out = static_cast<char*>(y_dev) - shift;
+    CK(launch_step(c->fp32, c->b, kApply, a, c->info[r].item_begin, c->info[r].item_count, c->smem, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return DACP_OK;
+}
+
+dacp_status dacp_get_timings(dacp_handle c, double* ms) {
+    TRY(check_handle(c));
+    if (!ms) return DACP_ERR_ARG;
+    for (int i = 0; i < 3; ++i) ms[i] = c->t_ms[i];
+    return DACP_OK;
+}
+
+}  // extern "C"

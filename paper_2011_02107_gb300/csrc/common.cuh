@@ -1,0 +1,58 @@
+// Shared definitions of the DACP CUDA library (device kernels and host driver).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dacp {
+
+constexpr int kThreads = 256;       // threads per CTA of the stencil kernels
+constexpr int kMaxSpins = 26;       // N limit (2^26 states per realization)
+constexpr int kTileBytes = 65536;   // shared-memory tile of one stencil CTA
+
+// Per-realization geometry and run lengths, read by every stencil CTA.
+struct RealInfo {
+    int N;            // spins
+    int tbits;        // log2(states per tile), tbits <= N
+    int64_t off;      // first state of this realization in the batch vectors
+    int item_begin;   // first work item (tile) of this realization
+    int item_count;   // tiles of this realization = 2^(N - tbits)
+    int nf;           // filter orders K to run
+    int ne;           // evolution launches = k_n + 1
+    int64_t mom_off;  // first moment row (of b*b doubles) of this realization
+};
+
+// One work item = one tile of one realization.
+struct Item {
+    int r;
+    int tile;
+};
+
+enum StepMode { kApply = 0, kFilter1 = 1, kFilter2 = 2, kEvolve = 3 };
+
+// Arguments of one stencil launch. Vectors are [state][b] in precision T.
+struct StepArgs {
+    const Item* items;
+    const RealInfo* real;
+    const void* diag;        // T per state: diagonal of H
+    const void* gam;         // T [R][kMaxSpins]: x-fields
+    const double* coef;      // [R][8]: {c_h, c_1, c_2} at order 0, then steady
+    void* bufA;              // rotating vectors (filter / evolution)
+    void* bufB;
+    void* bufU;              // u = H w_k between the two filter passes
+    // kApply: explicit vectors
+    const void* x;
+    const void* y1;
+    void* out;
+    int apply_row;           // kApply with moments: moment row pair 2*row, 2*row+1
+    int apply_moments;       // kApply: accumulate moments
+    int* step_ctr;           // device step counter (order k) for graph replay
+    unsigned* launch_done;   // CTAs finished in this launch
+    unsigned* real_done;     // [R] CTAs of each realization finished
+    double* part;            // [items][2 b^2] per-tile moment partials
+    double* mom;             // moment rows
+    int nsteps_override;     // > 0: run this many orders instead of RealInfo.nf / ne
+    int mom_rows_fixed;      // > 0: realization r's rows start at r * mom_rows_fixed
+};
+
+}  // namespace dacp

@@ -1,0 +1,218 @@
+// Parameter heuristic on the GPU (Sec. III): Lanczos upper bound on |E|
+// (the "upper-bound-estimator" the paper cites: largest |Ritz value| plus the
+// residual norm), and the window a from a kernel-polynomial estimate of the
+// density of states built from Chebyshev moments of the same start vector.
+// The H.v steps reuse the fused stencil kernel; these kernels do the vector
+// updates, the small tridiagonal eigenproblem and the window search.
+
+#include <math.h>
+
+#include "common.cuh"
+#include "ops.h"
+
+namespace dacp {
+
+__device__ __forceinline__ double warp_sum_p(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// w -= alpha_r v (alpha_r = moment row 2j+1 of realization r), then ||w||^2 per
+// realization into beta2[r * steps + j] (deterministic last-CTA reduction).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) lanczos_orth_kernel(const Item* __restrict__ items,
+                                                                const RealInfo* __restrict__ real, const T* v,
+                                                                T* w, const double* __restrict__ lmom,
+                                                                int rows, int j, double* part,
+                                                                unsigned* real_done, double* beta2, int steps) {
+    __shared__ double red_s[kThreads / 32];
+    __shared__ int last_s;
+    const int tid = threadIdx.x;
+    const Item it = items[blockIdx.x];
+    const RealInfo R = real[it.r];
+    const double alpha = lmom[static_cast<int64_t>(it.r) * rows + 2 * j + 1];
+    const T al = static_cast<T>(alpha);
+    const int tstates = 1 << R.tbits;
+    const int64_t base = R.off + (static_cast<int64_t>(it.tile) << R.tbits);
+    double acc = 0.0;
+    for (int sl = tid; sl < tstates; sl += kThreads) {
+        const T nv = w[base + sl] - al * v[base + sl];
+        w[base + sl] = nv;
+        acc = fma(static_cast<double>(nv), static_cast<double>(nv), acc);
+    }
+    acc = warp_sum_p(acc);
+    if ((tid & 31) == 0) red_s[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) s += red_s[i];
+        part[blockIdx.x] = s;
+        __threadfence();
+        last_s = (atomicAdd(&real_done[it.r], 1u) == static_cast<unsigned>(R.item_count - 1));
+    }
+    __syncthreads();
+    if (last_s && tid == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (int i = 0; i < R.item_count; ++i) s += __ldcg(part + R.item_begin + i);
+        beta2[it.r * steps + j] = s;
+        real_done[it.r] = 0u;
+    }
+}
+
+// w /= beta_{j+1}; a zero residual (invariant subspace) leaves w = 0.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) lanczos_scale_kernel(const Item* __restrict__ items,
+                                                                 const RealInfo* __restrict__ real, T* w,
+                                                                 const double* __restrict__ beta2, int j,
+                                                                 int steps) {
+    const Item it = items[blockIdx.x];
+    const RealInfo R = real[it.r];
+    const double b2 = beta2[it.r * steps + j];
+    const T sc = b2 > 0.0 ? static_cast<T>(1.0 / sqrt(b2)) : T(0);
+    const int tstates = 1 << R.tbits;
+    const int64_t base = R.off + (static_cast<int64_t>(it.tile) << R.tbits);
+    for (int sl = threadIdx.x; sl < tstates; sl += kThreads) w[base + sl] *= sc;
+}
+
+// coef[r] = {1, -beta_{j+1}, 0} for the next Lanczos apply.
+__global__ void lanczos_coef_kernel(int R, const double* __restrict__ beta2, int j, int steps, double* coef) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    coef[8 * r + 0] = 1.0;
+    coef[8 * r + 1] = -sqrt(beta2[r * steps + j]);
+    coef[8 * r + 2] = 0.0;
+}
+
+// Number of eigenvalues of the k x k tridiagonal (alpha, beta) below x (Sturm count).
+__device__ int sturm_count(const double* al, const double* b2, int k, double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+        const double off = i > 0 ? b2[i - 1] : 0.0;          // beta_{i}^2
+        d = (al[i] - x) - (i > 0 ? off / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+// Extreme Ritz values by bisection; bound = max(|theta_min|, |theta_max|) + beta_{k+1},
+// times (1 + safety), clamped to the Pauli 1-norm pnorm[r].
+__global__ void lanczos_bound_kernel(int R, const double* __restrict__ lmom, int rows,
+                                     const double* __restrict__ beta2, int steps,
+                                     const double* __restrict__ pnorm, double safety, double* emax) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double al[64], b2[64];
+    const int k = steps;
+    double gmax = 0.0;
+    for (int i = 0; i < k; ++i) {
+        al[i] = lmom[static_cast<int64_t>(r) * rows + 2 * i + 1];
+        b2[i] = beta2[r * steps + i];
+    }
+    for (int i = 0; i < k; ++i) {
+        const double bl = i > 0 ? sqrt(b2[i - 1]) : 0.0;
+        const double br = i < k - 1 ? sqrt(b2[i]) : 0.0;
+        gmax = fmax(gmax, fabs(al[i]) + bl + br);
+    }
+    double lo = -gmax - 1.0, hi = gmax + 1.0;
+    for (int it = 0; it < 200; ++it) {          // theta_min: count(x) >= 1
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(al, b2, k, mid) >= 1) hi = mid; else lo = mid;
+    }
+    const double tmin = 0.5 * (lo + hi);
+    lo = -gmax - 1.0; hi = gmax + 1.0;
+    for (int it = 0; it < 200; ++it) {          // theta_max: count(x) >= k
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(al, b2, k, mid) >= k) hi = mid; else lo = mid;
+    }
+    const double tmax = 0.5 * (lo + hi);
+    const double bound = (fmax(fabs(tmin), fabs(tmax)) + sqrt(b2[k - 1])) * (1.0 + safety);
+    emax[r] = fmin(bound, pnorm[r]);
+}
+
+// Kernel-polynomial window: mu_j = 2 P_j - P_{j mod 2} (j < M) of the
+// normalised start vector under G = H/E_max; Jackson damping; expected count
+// in [-a_r, a_r] = D [g_0 mu_0 (pi - 2 phi)/pi + 2 sum g_j mu_j (sin(j(pi-phi)) - sin(j phi))/(pi j)],
+// phi = acos(a_r); bisection for count = d_target. Then K = ceil(c E_max / a)
+// and n = ceil((basis_ratio d / b - 1) / 2).
+__global__ void kpm_window_kernel(int R, const RealInfo* __restrict__ real, const double* __restrict__ P,
+                                  int M, const double* __restrict__ emax, double d_target, double c_order,
+                                  double basis_ratio, int b, double* a_out, int* K_out, int* n_out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const double D = ldexp(1.0, real[r].N);
+    const double* Pr = P + static_cast<int64_t>(r) * M;
+    const double q = M_PI / (M + 1);
+    const double cq = 1.0 / tan(q);
+    auto count = [&](double ar) {
+        const double phi = acos(ar);
+        double tot = Pr[0] * (M_PI - 2.0 * phi) / M_PI;           // g_0 = 1, mu_0 = P_0
+        for (int j = 1; j < M; ++j) {
+            const double g = ((M - j + 1) * cos(q * j) + sin(q * j) * cq) / (M + 1);
+            const double mu = 2.0 * Pr[j] - Pr[j & 1];
+            tot += 2.0 * g * mu * (sin(j * (M_PI - phi)) - sin(j * phi)) / (M_PI * j);
+        }
+        return D * tot;
+    };
+    const double em = emax[r];
+    double a;
+    if (count(0.999) <= d_target) {           // a < E_max keeps E_0 > 0
+        a = 0.999 * em;
+    } else {
+        double lo = 0.0, hi = 0.999;
+        for (int it = 0; it < 100; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (count(mid) < d_target) lo = mid; else hi = mid;
+        }
+        a = 0.5 * (lo + hi) * em;
+    }
+    a_out[r] = a;
+    K_out[r] = static_cast<int>(ceil(c_order * em / a));
+    const double n = ceil((basis_ratio * d_target / b - 1.0) / 2.0);
+    n_out[r] = n < 1.0 ? 1 : static_cast<int>(n);
+}
+
+cudaError_t launch_lanczos_orth(bool fp32, const Item* items, const RealInfo* real, int n_items, const void* v,
+                                void* w, const double* lmom, int rows, int j, double* part, unsigned* real_done,
+                                double* beta2, int steps, cudaStream_t st) {
+    if (fp32)
+        lanczos_orth_kernel<float><<<n_items, kThreads, 0, st>>>(items, real, static_cast<const float*>(v),
+                                                                  static_cast<float*>(w), lmom, rows, j, part,
+                                                                  real_done, beta2, steps);
+    else
+        lanczos_orth_kernel<double><<<n_items, kThreads, 0, st>>>(items, real, static_cast<const double*>(v),
+                                                                   static_cast<double*>(w), lmom, rows, j, part,
+                                                                   real_done, beta2, steps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_scale(bool fp32, const Item* items, const RealInfo* real, int n_items, void* w,
+                                 const double* beta2, int j, int steps, double* coef, int R, cudaStream_t st) {
+    if (fp32)
+        lanczos_scale_kernel<float><<<n_items, kThreads, 0, st>>>(items, real, static_cast<float*>(w), beta2, j, steps);
+    else
+        lanczos_scale_kernel<double><<<n_items, kThreads, 0, st>>>(items, real, static_cast<double*>(w), beta2, j, steps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lanczos_coef_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, beta2, j, steps, coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps,
+                                 const double* pnorm, double safety, double* emax, cudaStream_t st) {
+    lanczos_bound_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, lmom, rows, beta2, steps, pnorm, safety, emax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kpm_window(int R, const RealInfo* real, const double* P, int M, const double* emax,
+                              double d_target, double c_order, double basis_ratio, int b, double* a_out,
+                              int* K_out, int* n_out, cudaStream_t st) {
+    kpm_window_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, real, P, M, emax, d_target, c_order, basis_ratio, b, a_out,
+                                                    K_out, n_out);
+    return cudaGetLastError();
+}
+
+}  // namespace dacp

@@ -1,0 +1,479 @@
+// Fused matrix-free H.v stencil + Chebyshev three-term recurrence + moments.
+//
+// One CTA owns one tile of 2^tbits consecutive basis states of one
+// realization. The tile of the vector H acts on is staged in shared memory;
+// a bit flip s -> s ^ 2^i with i < tbits reads the partner from the tile,
+// with i >= tbits from the partner tile in global memory (L2 resident when the
+// vector is). The diagonal (sum J_ij z_i z_j + sum h_i z_i) is read per state.
+//
+//   kApply   out = c_h H x + c_1 y1                       (test hook, Lanczos)
+//   kFilter1 u = H w_k                                     (Sec. II A, F = (H^2-E_c)/E_0)
+//   kFilter2 w_{k+1} = c_h H u + c_1 w_k + c_2 w_{k-1}     c_h = 2/E_0, c_1 = -2E_c/E_0, c_2 = -1
+//   kEvolve  w_{k+1} = c_h H w_k + c_1 w_{k-1}             c_h = 2/E_max, c_1 = -1 (Sec. II B)
+// Order 0 uses its own coefficients (T_1 = x): 1/E_0, -E_c/E_0, 0 and 1/E_max, 0.
+//
+// kEvolve also emits the moment rows P_2k = <w_k, w_k> and P_{2k+1} =
+// <w_{k+1}, w_k> (b x b blocks, float64). With T_2k = 2T_k^2 - 1 and
+// T_{2k+1} = 2T_{k+1}T_k - T_1, mu_j = 2 P_j - P_{j mod 2} (Appendix C moments
+// without a second pass). Per-tile partials are reduced by the last CTA of
+// each realization in tile order, so the result does not depend on scheduling.
+//
+// The order k is read from a device counter that the last CTA of a launch
+// advances, so the same launch can be captured once and replayed in a CUDA
+// graph; the two vector buffers swap roles by the parity of k and the write of
+// w_{k+1} goes in place over w_{k-1} (each element is read and written by the
+// same thread; partners are only read from w_k).
+
+#include "common.cuh"
+#include "ops.h"
+
+namespace dacp {
+
+template <typename T> struct MomAcc { using type = double; };
+template <> struct MomAcc<float> { using type = float; };   // short per-thread runs, then float64
+
+template <typename T, int B>
+__device__ __forceinline__ void load_vals(const T* __restrict__ p, T (&v)[B]) {
+#pragma unroll
+    for (int q = 0; q < B; ++q) v[q] = p[q];
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void load_vals_ro(const T* __restrict__ p, T (&v)[B]) {
+#pragma unroll
+    for (int q = 0; q < B; ++q) v[q] = __ldg(p + q);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T, int B, int MODE>
+__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int item_base) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    __shared__ T gam_s[kMaxSpins];
+    __shared__ double red_s[kThreads / 32][2 * B * B];
+    __shared__ int last_s;
+
+    const int tid = threadIdx.x;
+    const int item = item_base + blockIdx.x;
+    const Item it = a.items[item];
+    const RealInfo R = a.real[it.r];
+    int step = 0;
+    if (MODE != kApply) step = *a.step_ctr;
+    int nsteps = (MODE == kEvolve) ? R.ne : (MODE == kApply ? 1 : R.nf);
+    if (MODE != kApply && a.nsteps_override > 0) nsteps = a.nsteps_override;
+    const bool active = step < nsteps;
+    const bool want_mom = (MODE == kEvolve) || (MODE == kApply && a.apply_moments);
+
+    using Acc = typename MomAcc<T>::type;
+    Acc xx[B][B], ox[B][B];
+#pragma unroll
+    for (int p = 0; p < B; ++p)
+#pragma unroll
+        for (int q = 0; q < B; ++q) { xx[p][q] = Acc(0); ox[p][q] = Acc(0); }
+
+    if (active) {
+        T* wA = static_cast<T*>(a.bufA);
+        T* wB = static_cast<T*>(a.bufB);
+        T* wk = (step & 1) ? wB : wA;      // w_k
+        T* wo = (step & 1) ? wA : wB;      // w_{k-1}, overwritten by w_{k+1}
+        const T* x;
+        const T* y1 = nullptr;
+        const T* y2 = nullptr;
+        T* out;
+        double c_h, c_1 = 0.0, c_2 = 0.0;
+        const double* cf = a.coef + 8 * it.r + (step == 0 ? 0 : 3);
+        if (MODE == kApply) {
+            x = static_cast<const T*>(a.x); y1 = static_cast<const T*>(a.y1); out = static_cast<T*>(a.out);
+            c_h = cf[0]; c_1 = cf[1];
+        } else if (MODE == kFilter1) {
+            x = wk; out = static_cast<T*>(a.bufU); c_h = 1.0;
+        } else if (MODE == kFilter2) {
+            x = static_cast<const T*>(a.bufU); y1 = wk; y2 = wo; out = wo;
+            c_h = cf[0]; c_1 = cf[1]; c_2 = cf[2];
+        } else {
+            x = wk; y1 = wo; out = wo;
+            c_h = cf[0]; c_1 = cf[1];
+        }
+        const bool use1 = (c_1 != 0.0) && (y1 != nullptr);
+        const bool use2 = (c_2 != 0.0) && (y2 != nullptr);
+
+        const int tstates = 1 << R.tbits;
+        const int64_t tile0 = static_cast<int64_t>(it.tile) << R.tbits;   // first local state
+        const T* xg = x + R.off * B;
+        {
+            const int64_t nbytes = static_cast<int64_t>(tstates) * B * sizeof(T);
+            if ((nbytes & 15) == 0) {
+                const float4* src = reinterpret_cast<const float4*>(xg + tile0 * B);
+                float4* dst = reinterpret_cast<float4*>(smem_raw);
+                for (int64_t i = tid; i < nbytes / 16; i += kThreads) dst[i] = __ldg(src + i);
+            } else {
+                for (int i = tid; i < tstates * B; i += kThreads) tile[i] = xg[tile0 * B + i];
+            }
+        }
+        if (tid < R.N) gam_s[tid] = static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
+        __syncthreads();
+
+        const T* dg = static_cast<const T*>(a.diag) + R.off;
+        const T ch = static_cast<T>(c_h), c1 = static_cast<T>(c_1), c2 = static_cast<T>(c_2);
+        const int64_t gbase = R.off * B;
+        for (int sl = tid; sl < tstates; sl += kThreads) {
+            const int64_t s = tile0 + sl;
+            T xv[B], acc[B];
+            load_vals<T, B>(tile + sl * B, xv);
+            const T d = __ldg(dg + s);
+#pragma unroll
+            for (int p = 0; p < B; ++p) acc[p] = d * xv[p];
+            for (int i = 0; i < R.tbits; ++i) {
+                const T g = gam_s[i];
+                const T* q = tile + (sl ^ (1 << i)) * B;
+#pragma unroll
+                for (int p = 0; p < B; ++p) acc[p] = fma(g, q[p], acc[p]);
+            }
+            for (int i = R.tbits; i < R.N; ++i) {
+                const T g = gam_s[i];
+                T pv[B];
+                load_vals_ro<T, B>(xg + (s ^ (static_cast<int64_t>(1) << i)) * B, pv);
+#pragma unroll
+                for (int p = 0; p < B; ++p) acc[p] = fma(g, pv[p], acc[p]);
+            }
+            T o[B];
+#pragma unroll
+            for (int p = 0; p < B; ++p) o[p] = ch * acc[p];
+            if (use1) {
+                T v[B];
+                load_vals<T, B>(y1 + gbase + s * B, v);
+#pragma unroll
+                for (int p = 0; p < B; ++p) o[p] = fma(c1, v[p], o[p]);
+            }
+            if (use2) {
+                T v[B];
+                load_vals<T, B>(y2 + gbase + s * B, v);
+#pragma unroll
+                for (int p = 0; p < B; ++p) o[p] = fma(c2, v[p], o[p]);
+            }
+            T* op = out + gbase + s * B;
+#pragma unroll
+            for (int p = 0; p < B; ++p) op[p] = o[p];
+            if (want_mom) {
+#pragma unroll
+                for (int p = 0; p < B; ++p)
+#pragma unroll
+                    for (int q = 0; q < B; ++q) {
+                        xx[p][q] = fma(static_cast<Acc>(xv[p]), static_cast<Acc>(xv[q]), xx[p][q]);
+                        ox[p][q] = fma(static_cast<Acc>(o[p]), static_cast<Acc>(xv[q]), ox[p][q]);
+                    }
+            }
+        }
+    }
+
+    if (want_mom && active) {
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int p = 0; p < B; ++p)
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                const double v1 = warp_sum(static_cast<double>(xx[p][q]));
+                const double v2 = warp_sum(static_cast<double>(ox[p][q]));
+                if (lane == 0) { red_s[warp][p * B + q] = v1; red_s[warp][B * B + p * B + q] = v2; }
+            }
+        __syncthreads();
+        if (tid < 2 * B * B) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) s += red_s[w][tid];
+            a.part[static_cast<int64_t>(item) * 2 * B * B + tid] = s;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&a.real_done[it.r], 1u);
+            last_s = (prev == static_cast<unsigned>(R.item_count - 1));
+        }
+        __syncthreads();
+        if (last_s) {
+            __threadfence();
+            if (tid < 2 * B * B) {
+                double s = 0.0;
+                for (int j = 0; j < R.item_count; ++j)
+                    s += __ldcg(a.part + static_cast<int64_t>(R.item_begin + j) * 2 * B * B + tid);
+                const int row = (MODE == kEvolve) ? 2 * step : 2 * a.apply_row;
+                const int64_t row0 = a.mom_rows_fixed > 0
+                                         ? static_cast<int64_t>(it.r) * a.mom_rows_fixed : R.mom_off;
+                a.mom[(row0 + row) * B * B + tid] = s;
+            }
+            if (tid == 0) a.real_done[it.r] = 0u;
+        }
+    }
+
+    if (MODE == kFilter2 || MODE == kEvolve) {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(a.launch_done, 1u);
+            if (prev == gridDim.x - 1) {
+                *a.launch_done = 0u;
+                __threadfence();
+                atomicAdd(a.step_ctr, 1);
+            }
+        }
+    }
+}
+
+template <typename T, int B, int MODE>
+static cudaError_t launch_one(const StepArgs& a, int item_base, int n_items, int smem, cudaStream_t st) {
+    step_kernel<T, B, MODE><<<n_items, kThreads, smem, st>>>(a, item_base);
+    return cudaGetLastError();
+}
+
+template <typename T, int B>
+static cudaError_t prepare_tb(int smem) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(step_kernel<T, B, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(step_kernel<T, B, kFilter1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(step_kernel<T, B, kFilter2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_kernel<T, B, kEvolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// Allow the dynamic shared-memory tile for every mode of (precision, b);
+// called once per handle, outside any stream capture.
+cudaError_t prepare_step(bool fp32, int b, int smem) {
+    if (fp32) {
+        if (b == 1) return prepare_tb<float, 1>(smem);
+        if (b == 2) return prepare_tb<float, 2>(smem);
+        if (b == 4) return prepare_tb<float, 4>(smem);
+    } else {
+        if (b == 1) return prepare_tb<double, 1>(smem);
+        if (b == 2) return prepare_tb<double, 2>(smem);
+        if (b == 4) return prepare_tb<double, 4>(smem);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int B>
+static cudaError_t launch_mode(int mode, const StepArgs& a, int item_base, int n_items, int smem,
+                               cudaStream_t st) {
+    switch (mode) {
+        case kApply: return launch_one<T, B, kApply>(a, item_base, n_items, smem, st);
+        case kFilter1: return launch_one<T, B, kFilter1>(a, item_base, n_items, smem, st);
+        case kFilter2: return launch_one<T, B, kFilter2>(a, item_base, n_items, smem, st);
+        case kEvolve: return launch_one<T, B, kEvolve>(a, item_base, n_items, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t launch_b(int b, int mode, const StepArgs& a, int item_base, int n_items, int smem,
+                            cudaStream_t st) {
+    switch (b) {
+        case 1: return launch_mode<T, 1>(mode, a, item_base, n_items, smem, st);
+        case 2: return launch_mode<T, 2>(mode, a, item_base, n_items, smem, st);
+        case 4: return launch_mode<T, 4>(mode, a, item_base, n_items, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(bool fp32, int b, int mode, const StepArgs& a, int item_base, int n_items,
+                        int smem, cudaStream_t st) {
+    return fp32 ? launch_b<float>(b, mode, a, item_base, n_items, smem, st)
+                : launch_b<double>(b, mode, a, item_base, n_items, smem, st);
+}
+
+// ---------------------------------------------------------------------------
+// Set-up kernels: diagonal, precision conversion, column norms, normalisation.
+
+// diag(s) = sum_{i<j} J_ij z_i z_j + sum_i h_i z_i, z_i = 1 - 2 bit_i(s), in float64.
+template <typename T>
+__global__ void diag_kernel(const RealInfo* __restrict__ real, int r, const double* __restrict__ J,
+                            const double* __restrict__ h, T* __restrict__ diag) {
+    const RealInfo R = real[r];
+    const int64_t D = static_cast<int64_t>(1) << R.N;
+    const double* Jr = J + static_cast<int64_t>(r) * kMaxSpins * kMaxSpins;
+    const double* hr = h + static_cast<int64_t>(r) * kMaxSpins;
+    for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < D;
+         s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double d = 0.0;
+        for (int i = 0; i < R.N; ++i) {
+            const double zi = ((s >> i) & 1) ? -1.0 : 1.0;
+            d += hr[i] * zi;
+            for (int j = i + 1; j < R.N; ++j) {
+                const double zj = ((s >> j) & 1) ? -1.0 : 1.0;
+                d += Jr[i * kMaxSpins + j] * zi * zj;
+            }
+        }
+        diag[R.off + s] = static_cast<T>(d);
+    }
+}
+
+template <typename T>
+__global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[i] = static_cast<T>(src[i]);
+}
+
+template <typename T>
+__global__ void extract_col_kernel(const T* __restrict__ src, T* __restrict__ dst, int b, int64_t states) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < states;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[i] = src[i * b];
+}
+
+template <typename T>
+__global__ void to_double_kernel(const T* __restrict__ src, double* __restrict__ dst, int64_t n) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[i] = static_cast<double>(src[i]);
+}
+
+// Squared column norms of each realization's vector; src is chosen per
+// realization by the parity of its filter order (w_K lives in A when K is even).
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads) colnorm_kernel(const Item* __restrict__ items,
+                                                           const RealInfo* __restrict__ real,
+                                                           const T* A, const T* Bv, int by_parity,
+                                                           double* part, unsigned* real_done,
+                                                           double* norms) {
+    __shared__ double red_s[kThreads / 32][B];
+    __shared__ int last_s;
+    const int tid = threadIdx.x;
+    const Item it = items[blockIdx.x];
+    const RealInfo R = real[it.r];
+    const T* src = (by_parity && (R.nf & 1)) ? Bv : A;
+    const int tstates = 1 << R.tbits;
+    const int64_t tile0 = static_cast<int64_t>(it.tile) << R.tbits;
+    double acc[B];
+#pragma unroll
+    for (int p = 0; p < B; ++p) acc[p] = 0.0;
+    for (int sl = tid; sl < tstates; sl += kThreads) {
+        const T* q = src + (R.off + tile0 + sl) * B;
+#pragma unroll
+        for (int p = 0; p < B; ++p) {
+            const double v = static_cast<double>(q[p]);
+            acc[p] = fma(v, v, acc[p]);
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int p = 0; p < B; ++p) {
+        const double v = warp_sum(acc[p]);
+        if (lane == 0) red_s[warp][p] = v;
+    }
+    __syncthreads();
+    if (tid < B) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += red_s[w][tid];
+        part[static_cast<int64_t>(blockIdx.x) * B + tid] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last_s = (atomicAdd(&real_done[it.r], 1u) == static_cast<unsigned>(R.item_count - 1));
+    __syncthreads();
+    if (last_s) {
+        __threadfence();
+        if (tid < B) {
+            double s = 0.0;
+            for (int j = 0; j < R.item_count; ++j) s += __ldcg(part + static_cast<int64_t>(R.item_begin + j) * B + tid);
+            norms[it.r * B + tid] = s;
+        }
+        if (tid == 0) real_done[it.r] = 0u;
+    }
+}
+
+// psi_E = w_K / ||w_K|| per column (Eq. target), written to dst and dst2.
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads) normalize_kernel(const Item* __restrict__ items,
+                                                             const RealInfo* __restrict__ real,
+                                                             const T* A, const T* Bv, int by_parity,
+                                                             const double* __restrict__ norms,
+                                                             T* dst, T* dst2) {
+    const int tid = threadIdx.x;
+    const Item it = items[blockIdx.x];
+    const RealInfo R = real[it.r];
+    const T* src = (by_parity && (R.nf & 1)) ? Bv : A;
+    const int tstates = 1 << R.tbits;
+    const int64_t tile0 = static_cast<int64_t>(it.tile) << R.tbits;
+    T sc[B];
+#pragma unroll
+    for (int p = 0; p < B; ++p) sc[p] = static_cast<T>(1.0 / sqrt(norms[it.r * B + p]));
+    for (int sl = tid; sl < tstates; sl += kThreads) {
+        const int64_t e = (R.off + tile0 + sl) * B;
+#pragma unroll
+        for (int p = 0; p < B; ++p) {
+            const T v = src[e + p] * sc[p];
+            dst[e + p] = v;
+            if (dst2) dst2[e + p] = v;
+        }
+    }
+}
+
+cudaError_t launch_diag(bool fp32, const RealInfo* real, int r, int N, const double* J, const double* h,
+                        void* diag, cudaStream_t st) {
+    const int64_t D = static_cast<int64_t>(1) << N;
+    const int grid = static_cast<int>((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096);
+    if (fp32) diag_kernel<float><<<grid, 256, 0, st>>>(real, r, J, h, static_cast<float*>(diag));
+    else diag_kernel<double><<<grid, 256, 0, st>>>(real, r, J, h, static_cast<double*>(diag));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(bool fp32, const double* src, void* dst, int64_t n, cudaStream_t st) {
+    const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+    if (n == 0) return cudaSuccess;
+    if (fp32) convert_kernel<float><<<grid, 256, 0, st>>>(src, static_cast<float*>(dst), n);
+    else convert_kernel<double><<<grid, 256, 0, st>>>(src, static_cast<double*>(dst), n);
+    return cudaGetLastError();
+}
+
+// dst[s] = src[s][0]: column 0 of a [state][b] vector.
+cudaError_t launch_extract_col(bool fp32, int b, const void* src, void* dst, int64_t states, cudaStream_t st) {
+    const int grid = static_cast<int>((states + 255) / 256 < 8192 ? (states + 255) / 256 : 8192);
+    if (fp32) extract_col_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(src), static_cast<float*>(dst), b, states);
+    else extract_col_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(src), static_cast<double*>(dst), b, states);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_double(bool fp32, const void* src, double* dst, int64_t n, cudaStream_t st) {
+    const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+    if (n == 0) return cudaSuccess;
+    if (fp32) to_double_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(src), dst, n);
+    else to_double_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(src), dst, n);
+    return cudaGetLastError();
+}
+
+template <typename T, int B>
+static cudaError_t norm_and_scale(const Item* items, const RealInfo* real, int n_items, const void* A,
+                                  const void* Bv, int by_parity, double* part, unsigned* real_done,
+                                  double* norms, void* dst, void* dst2, cudaStream_t st) {
+    colnorm_kernel<T, B><<<n_items, kThreads, 0, st>>>(items, real, static_cast<const T*>(A),
+                                                        static_cast<const T*>(Bv), by_parity, part,
+                                                        real_done, norms);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    normalize_kernel<T, B><<<n_items, kThreads, 0, st>>>(items, real, static_cast<const T*>(A),
+                                                          static_cast<const T*>(Bv), by_parity, norms,
+                                                          static_cast<T*>(dst), static_cast<T*>(dst2));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(bool fp32, int b, const Item* items, const RealInfo* real, int n_items,
+                             const void* A, const void* Bv, int by_parity, double* part,
+                             unsigned* real_done, double* norms, void* dst, void* dst2, cudaStream_t st) {
+#define DACP_NS(T, BB) return norm_and_scale<T, BB>(items, real, n_items, A, Bv, by_parity, part, real_done, norms, dst, dst2, st)
+    if (fp32) {
+        if (b == 1) DACP_NS(float, 1);
+        if (b == 2) DACP_NS(float, 2);
+        if (b == 4) DACP_NS(float, 4);
+    } else {
+        if (b == 1) DACP_NS(double, 1);
+        if (b == 2) DACP_NS(double, 2);
+        if (b == 4) DACP_NS(double, 4);
+    }
+#undef DACP_NS
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dacp

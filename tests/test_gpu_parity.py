@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path through the C ABI against the float64 CPU oracle.
+
+Inputs are seeded and synthetic (``workloads``). Tolerances:
+  * H.v, float64: 1e-13 of max|y| (same summation order, FMA contraction only);
+    float32: 2e-6 of max|y| (inputs and couplings rounded to float32, N terms);
+  * filtered vectors, float64: 1e-9 of max|psi_E| after K ~ 10^2..10^3 orders;
+  * moments, float64: 1e-9 (|mu_j| <= mu_0 = 1; the CUDA path uses the doubling
+    identities, the oracle records every order directly, so this also checks
+    T_2k = 2 T_k^2 - 1 and T_{2k+1} = 2 T_{k+1} T_k - T_1 at run time);
+  * central eigenvalues, float64: 1e-9 of the spectral width (the target).
+"""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dacp as DA
+from oracle import hamiltonian as Hm
+from oracle import metrics as MT
+from oracle import params as OP
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2011_02107_gb300")
+
+
+def _dev(x, fp32):
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32 if fp32 else np.float64))
+    return t.cuda()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_apply_h_uneven_batch(fp32, b):
+    # N spans: below one warp, exactly one tile, several tiles with out-of-tile bits
+    Ns = [1, 3, 9, 13, 15, 16]
+    models = [W.random_model(N, seed=40 + N) for N in Ns]
+    psi = [W.start_vectors(N, b, seed=1, r=i) for i, N in enumerate(Ns)]
+    d = P.Dacp(models, psi, block_b=b, precision=P.DACP_FP32 if fp32 else P.DACP_FP64)
+    try:
+        for r, m in enumerate(models):
+            x = W.start_vectors(m["N"], b, seed=7, r=r)
+            xd = _dev(x, fp32)
+            yd = torch.zeros_like(xd)
+            d.apply_h(r, xd.data_ptr(), yd.data_ptr())
+            torch.cuda.synchronize()
+            y = yd.double().cpu().numpy()
+            ref = Hm.apply_h(m, x.astype(np.float32).astype(np.float64) if fp32 else x)
+            tol = (2e-6 if fp32 else 1e-13) * np.abs(ref).max()
+            assert np.abs(y - ref).max() <= tol, (m["N"], np.abs(y - ref).max(), tol)
+    finally:
+        d.close()
+
+
+def _c1_params(m, psi, n_eigs, b):
+    emax = OP.emax_bound(m, psi[:, 0])
+    mu = OP.kpm_moments(m, psi[:, 0], emax, 256)
+    a = OP.kpm_window(mu, 1 << m["N"], emax, 2.0 * n_eigs)
+    return emax, a, OP.filter_order(emax, a), OP.basis_half_size(n_eigs, b)
+
+
+@pytest.fixture(scope="module")
+def c1_run():
+    """N=10 mixed-field chain, b=4, plain float64, the oracle's parameters."""
+    m = W.chain(10)
+    psi = W.start_vectors(10, 4, seed=0)
+    emax, a, K, n = _c1_params(m, psi, 100, 4)
+    d = P.Dacp([m], [psi], block_b=4, precision=P.DACP_FP64)
+    d.set_params(emax, a, K, n)
+    d.filter()
+    d.basis_moments()
+    eigs, nf, rank = d.central_eigs(100)
+    ref = DA.dacp(m, psi, emax, a, K, n, 100)
+    out = {"m": m, "psi": psi, "emax": emax, "a": a, "K": K, "n": n, "d": d, "eigs": eigs[0], "nf": nf,
+           "rank": rank, "ref": ref, "psiE": d.filtered(0), "mu": d.moments(0), "params": d.params()}
+    yield out
+    d.close()
+
+
+def test_c1_filtered_state(c1_run):
+    ref = c1_run["ref"]["psi_E"]
+    got = c1_run["psiE"]
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_c1_moments_vs_direct(c1_run):
+    mu_ref = c1_run["ref"]["mu"]          # (2 k_n + 1, b, b) directly recorded
+    mu = c1_run["mu"]                     # (2 k_n + 2, b, b) from the doubling identities
+    assert c1_run["params"]["kn"][0] == c1_run["ref"]["kn"]
+    k = mu_ref.shape[0]
+    musym = 0.5 * (mu_ref + np.transpose(mu_ref, (0, 2, 1)))
+    assert np.abs(mu[:k] - musym).max() < 1e-9
+
+
+def test_c1_eigenvalues_vs_oracle_and_dense(c1_run):
+    E = np.linalg.eigvalsh(Hm.dense_h(c1_run["m"]))
+    width = E[-1] - E[0]
+    assert c1_run["nf"][0] == 100
+    assert np.abs(c1_run["eigs"] - c1_run["ref"]["eigs"]).max() < 1e-9 * width
+    assert np.abs(c1_run["eigs"] - MT.central_exact(E, 100)).max() < 1e-9 * width
+    assert abs(int(c1_run["rank"][0]) - c1_run["ref"]["rank"]) <= 2
+
+
+def test_heuristic_parameters_match_oracle():
+    models = [W.chain(10), W.spin_glass_shard(9, seed=3), W.random_model(8, seed=5)]
+    psis = [W.start_vectors(m["N"], 2, seed=11, r=i) for i, m in enumerate(models)]
+    d = P.Dacp(models, psis, block_b=2, precision=P.DACP_FP64)
+    try:
+        d.choose_params(60, d_ratio=2.0, basis_ratio=1.5, c_order=18.0, lanczos_steps=20, kpm_moments=256)
+        p = d.params()
+        for r, m in enumerate(models):
+            em = OP.emax_bound(m, psis[r][:, 0], steps=20)
+            mu = OP.kpm_moments(m, psis[r][:, 0], em, 256)
+            a = OP.kpm_window(mu, 1 << m["N"], em, 2.0 * 60)
+            assert abs(p["emax"][r] - em) <= 1e-9 * em
+            assert abs(p["a"][r] - a) <= 1e-7 * a
+            assert p["K"][r] == OP.filter_order(em, a)
+            assert p["n"][r] == OP.basis_half_size(60, 2, d_ratio=2.0)
+            assert p["emax"][r] >= np.abs(np.linalg.eigvalsh(Hm.dense_h(m))).max()
+    finally:
+        d.close()
+
+
+def test_batched_uneven_end_to_end_fp64():
+    """Three realizations of different N in one handle; each against dense eigh."""
+    models = [W.spin_glass_shard(8, seed=1), W.chain(9), W.random_model(10, seed=2)]
+    psis = [W.start_vectors(m["N"], 4, seed=5, r=i) for i, m in enumerate(models)]
+    d = P.Dacp(models, psis, block_b=4, precision=P.DACP_FP64)
+    try:
+        d.choose_params(40)
+        d.filter()
+        d.basis_moments()
+        eigs, nf, rank = d.central_eigs(40)
+        for r, m in enumerate(models):
+            E = np.linalg.eigvalsh(Hm.dense_h(m))
+            assert nf[r] == 40
+            assert np.abs(eigs[r] - MT.central_exact(E, 40)).max() < 1e-9 * (E[-1] - E[0])
+    finally:
+        d.close()
+
+
+def test_fp32_vectors_fp64_moments_small_batch():
+    """Float32 recurrence with float64 moments and solve: error in local level spacings."""
+    models = [W.spin_glass_shard(10, seed=s) for s in range(4)]
+    psis = [W.start_vectors(10, 4, seed=9, r=i) for i in range(4)]
+    d = P.Dacp(models, psis, block_b=4, precision=P.DACP_FP32)
+    try:
+        d.choose_params(60)
+        d.filter()
+        d.basis_moments()
+        eigs, nf, rank = d.central_eigs(60)
+        for r, m in enumerate(models):
+            E = np.linalg.eigvalsh(Hm.dense_h(m))
+            assert nf[r] == 60
+            mt = MT.match(eigs[r], E)
+            assert mt["n_unmatched"] == 0
+            assert mt["spacing_err"].max() < 1e-2
+    finally:
+        d.close()
+
+
+def test_integrable_n16_against_jordan_wigner():
+    """N=16 h_z=0 chain (J=1, h_x=1), 1000 central eigenvalues, plain float64, vs the closed form."""
+    from oracle import jordan_wigner as JW
+    m = W.chain(16, J=1.0, hx=1.0, hz=0.0)
+    psi = W.start_vectors(16, 4, seed=0)
+    d = P.Dacp([m], [psi], block_b=4, precision=P.DACP_FP64)
+    try:
+        d.choose_params(1000)
+        d.filter()
+        d.basis_moments()
+        eigs, nf, rank = d.central_eigs(1000)
+        E = JW.spectrum(m)
+        assert nf[0] == 1000
+        mt = MT.match(eigs[0], E)
+        # integrable chain: clustered levels; report misses, require the rest exact
+        good = mt["abs_err"] < 1e-9 * (E[-1] - E[0])
+        assert good.mean() > 0.97, (good.mean(), mt["n_unmatched"])
+    finally:
+        d.close()
+
+
+def test_state_and_argument_errors():
+    m = W.chain(6)
+    d = P.Dacp([m], [W.start_vectors(6, 1, seed=0)], block_b=1)
+    try:
+        with pytest.raises(P.DacpError) as e:
+            d.filter()
+        assert e.value.status == 6
+        with pytest.raises(P.DacpError) as e:
+            d.set_params(5.0, 6.0, 10, 3)          # a >= E_max
+        assert e.value.status == 1
+        d.set_params(20.0, 1.0, 10, 3)
+        with pytest.raises(P.DacpError) as e:
+            d.central_eigs(5)
+        assert e.value.status == 6
+    finally:
+        d.close()
+
+
+def test_emax_not_a_bound_is_reported():
+    """E_max below the true spectral radius: |mu_j| grows past mu_0 and the realization is flagged."""
+    m = W.chain(8)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    bad_emax = 0.7 * np.abs(E).max()
+    d = P.Dacp([m], [W.start_vectors(8, 1, seed=0)], block_b=1)
+    try:
+        d.set_params(bad_emax, 0.3, 0, 40)
+        d.filter()
+        d.basis_moments()
+        eigs, nf, rank = d.central_eigs(10)
+        assert nf[0] == -4                          # -DACP_ERR_NUMERIC
+    finally:
+        d.close()
