@@ -14,9 +14,9 @@
  *     handle keeps a message readable with dacp_last_error().
  *   - All host arrays are owned by the caller and only read or written during
  *     the call. The library owns every device buffer it allocates.
- *   - Work is ordered on the handle's CUDA stream (the `stream` given to
- *     dacp_create, NULL = legacy default stream). Calls that return host data
- *     synchronise that stream before returning.
+ *   - Work is ordered on the handle's CUDA stream: the `stream` given to
+ *     dacp_create, or a private non-blocking stream when it is NULL. Every
+ *     call has finished its device work when it returns.
  *   - A handle is not thread-safe; separate handles are independent.
  *   - Calling out of order (e.g. dacp_central_eigs before dacp_basis_moments)
  *     returns DACP_ERR_STATE.
@@ -59,7 +59,7 @@ typedef enum {
  *                Realization r starts at sum_{r'<r} N_r'^2.
  *   h, gamma     concatenated z-fields and x-fields, N_r each.
  *   block_b      start vectors per realization (block filter, Sec. III):
- *                1, 2, 4, 8 or 16.
+ *                1, 2 or 4.
  *   precision    dacp_precision.
  *   psi0         start vectors, float64, realization r at sum_{r'<r} 2^N_r' * b,
  *                layout [state][column]. The paper draws them at random
@@ -91,7 +91,9 @@ dacp_status dacp_set_params(dacp_handle hd, const double* emax, const double* a,
  *   a:     kernel-polynomial DOS estimate from kpm_moments Chebyshev moments of
  *          the same vector; [-a, a] holds d = d_ratio * n_eigs levels;
  *   n:     b(2n+1) >= basis_ratio * d (Sec. II B: 2n+1 = 1.5 d);
- *   K:     ceil(c_order * E_max / a) (Sec. II A: c_order = 18).
+ *   K:     ceil(c_order * E_max / a) (Sec. II A: c_order = 18). c_order <= 0
+ *          picks the precision default: 18 for DACP_FP64, 6 for DACP_FP32
+ *          (float32 moments resolve a dynamic range of about e^12).
  * Errors: DACP_ERR_ARG, DACP_ERR_CUDA.
  */
 dacp_status dacp_choose_params(dacp_handle hd, int n_eigs, double d_ratio,
@@ -127,7 +129,8 @@ dacp_status dacp_basis_moments(dacp_handle hd);
  * S_ij = (mu_{x_i+x_j} + mu_{|x_i-x_j|})/2 and the same with
  * nu_k = E_max (mu_{k+1} + mu_{|k-1|})/2 for H), solve H B = S B Lambda
  * (Eq. gep) after dropping eigenvalues of S below eps * lambda_max(S)
- * (eps <= 0 -> 1e-12, Sec. II C), and return up to n_eigs eigenvalues of
+ * (eps <= 0 -> 1e-12 for DACP_FP64 as in Sec. II C, 1e-6 for DACP_FP32,
+ * whose moments carry float32 round-off), and return up to n_eigs eigenvalues of
  * smallest |E| inside [-window, window] (window <= 0 -> a) in ascending order.
  *   eigs     n_real * n_eigs doubles; realization r at r * n_eigs.
  *   n_found  n_real ints: count written for r, or -dacp_status on failure.
@@ -161,6 +164,70 @@ dacp_status dacp_apply_h(dacp_handle hd, int r, const void* x_dev, void* y_dev);
  * handle's stream: ms[0] = T_F, ms[1] = T_E, ms[2] = T_D.
  */
 dacp_status dacp_get_timings(dacp_handle hd, double* ms);
+
+/*
+ * dacp_get_launch_count -- number of this library's own CUDA kernels launched
+ * on the handle since dacp_create (kernels inside cuSOLVER / cuBLAS calls are
+ * not counted). A graph replay counts each kernel node it runs.
+ */
+dacp_status dacp_get_launch_count(dacp_handle hd, int64_t* count);
+
+/* ---- learned parameter predictor ------------------------------------------
+ * A small float32 MLP (project extension; the paper picks a, K and n by hand,
+ * Sec. III). Input: kFeatures = 40 features per realization -- N,
+ * log(n_eigs / 2^N), mean/std of the x-fields, of the nonzero zz couplings and
+ * of the z-fields, and mu_1..mu_32 of a normalised random vector under
+ * G = H / E_max. Output: 3 knobs -- log of the window ratio d / n_eigs, the
+ * filter-order constant c (K = c E_max / a) and the basis ratio b(2n+1) / d.
+ * Layers: affine + ReLU for the hidden layers, affine output; loss
+ * sum (y - t)^2 / (2B) on standardised inputs and targets; Adam.
+ * Weights are one flat float32 vector: for each layer W (out x in, row-major)
+ * then b. */
+typedef struct dacp_mlp_ctx* dacp_mlp;
+
+/* dacp_mlp_create -- layers n_in -> hidden_layers x n_hidden -> n_out.
+ * weights: initial flat weights, or NULL for He-uniform weights from seed.
+ * stream: cudaStream_t or NULL (private stream). */
+dacp_status dacp_mlp_create(dacp_mlp* out, int n_in, int n_hidden, int hidden_layers, int n_out,
+                            const float* weights, uint64_t seed, void* stream);
+/* dacp_mlp_set_normalization -- feature and target standardisation:
+ * z = (x - in_mean) / in_std into the network, y = z_out * out_std + out_mean. */
+dacp_status dacp_mlp_set_normalization(dacp_mlp m, const float* in_mean, const float* in_std,
+                                       const float* out_mean, const float* out_std);
+/* dacp_mlp_get_weights / dacp_mlp_set_weights -- the flat float32 weights
+ * (set also resets the Adam state). *count receives the number of weights. */
+dacp_status dacp_mlp_get_weights(dacp_mlp m, float* w, int64_t cap, int64_t* count);
+dacp_status dacp_mlp_set_weights(dacp_mlp m, const float* w, int64_t count);
+/* dacp_mlp_forward -- y[batch][n_out] (denormalised) from host x[batch][n_in]. */
+dacp_status dacp_mlp_forward(dacp_mlp m, const float* x, int batch, float* y);
+/* dacp_mlp_gradients -- gradient of the loss w.r.t. the flat weights for one
+ * batch of host (x, t) (targets in raw units), and the loss. Test hook. */
+dacp_status dacp_mlp_gradients(dacp_mlp m, const float* x, const float* t, int batch, float* grad,
+                               double* loss);
+/* dacp_mlp_train -- Adam (lr, beta = 0.9 / 0.999, eps = 1e-8) on shuffled
+ * minibatches for `epochs` passes over n_samples host samples; the data is
+ * copied to the device once. *final_loss = loss of the last minibatch. */
+dacp_status dacp_mlp_train(dacp_mlp m, const float* x, const float* t, int n_samples, int batch,
+                           int epochs, float lr, uint64_t seed, double* final_loss);
+dacp_status dacp_mlp_get_launch_count(dacp_mlp m, int64_t* count);
+const char* dacp_mlp_last_error(dacp_mlp m);
+void dacp_mlp_destroy(dacp_mlp m);
+
+/*
+ * dacp_choose_params_mlp -- parameters from the network: the same Lanczos
+ * bound and KPM moments as dacp_choose_params, then the features, one forward
+ * pass over all realizations on the device, and the window / order / basis
+ * from the predicted knobs (clamped to window ratio [1, 4], c [3, 24],
+ * basis ratio [0.6, 3]). The network must have 40 inputs and 3 outputs.
+ * Callers fall back to dacp_choose_params for realizations whose
+ * dacp_central_eigs count comes back short.
+ */
+dacp_status dacp_choose_params_mlp(dacp_handle hd, dacp_mlp m, int n_eigs, int lanczos_steps,
+                                   int kpm_moments);
+
+/* dacp_get_features -- the 40 network features of every realization
+ * (float32, [n_real][40]) from the last parameter choice. */
+dacp_status dacp_get_features(dacp_handle hd, float* feats, int64_t cap);
 
 /* dacp_last_error -- message of the last failure on this handle (owned by
  * the handle, valid until the next call on it). */

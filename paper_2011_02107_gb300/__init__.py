@@ -29,7 +29,14 @@ _STATUS = {0: "DACP_OK", 1: "DACP_ERR_ARG", 2: "DACP_ERR_CUDA", 3: "DACP_ERR_NOM
 
 EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_params", "dacp_filter",
            "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered",
-           "dacp_apply_h", "dacp_get_timings", "dacp_last_error", "dacp_status_string", "dacp_destroy"]
+           "dacp_apply_h", "dacp_get_timings", "dacp_get_launch_count", "dacp_last_error", "dacp_status_string",
+           "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_get_weights",
+           "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
+           "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
+           "dacp_get_features"]
+
+N_FEATURES = 40
+N_KNOBS = 3
 
 
 class DacpError(RuntimeError):
@@ -61,6 +68,17 @@ def _load():
         "dacp_get_filtered": [P, I, P, L],
         "dacp_apply_h": [P, I, P, P],
         "dacp_get_timings": [P, P],
+        "dacp_get_launch_count": [P, ctypes.POINTER(L)],
+        "dacp_mlp_create": [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64, P],
+        "dacp_mlp_set_normalization": [P, P, P, P, P],
+        "dacp_mlp_get_weights": [P, P, L, ctypes.POINTER(L)],
+        "dacp_mlp_set_weights": [P, P, L],
+        "dacp_mlp_forward": [P, P, I, P],
+        "dacp_mlp_gradients": [P, P, P, I, P, ctypes.POINTER(D)],
+        "dacp_mlp_train": [P, P, P, I, I, I, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(D)],
+        "dacp_mlp_get_launch_count": [P, ctypes.POINTER(L)],
+        "dacp_choose_params_mlp": [P, P, I, I, I],
+        "dacp_get_features": [P, P, L],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -72,6 +90,10 @@ def _load():
     lib.dacp_status_string.restype = ctypes.c_char_p
     lib.dacp_destroy.argtypes = [P]
     lib.dacp_destroy.restype = None
+    lib.dacp_mlp_last_error.argtypes = [P]
+    lib.dacp_mlp_last_error.restype = ctypes.c_char_p
+    lib.dacp_mlp_destroy.argtypes = [P]
+    lib.dacp_mlp_destroy.restype = None
     return lib
 
 
@@ -112,7 +134,7 @@ def dacp_set_params(hd, emax, a, K, n):
     _check(hd, _lib.dacp_set_params(hd, _ptr(emax), _ptr(a), _ptr(K), _ptr(n)))
 
 
-def dacp_choose_params(hd, n_eigs, d_ratio=2.0, basis_ratio=1.5, c_order=18.0, lanczos_steps=20,
+def dacp_choose_params(hd, n_eigs, d_ratio=2.0, basis_ratio=1.5, c_order=0.0, lanczos_steps=20,
                        kpm_moments=256):
     _check(hd, _lib.dacp_choose_params(hd, int(n_eigs), float(d_ratio), float(basis_ratio), float(c_order),
                                        int(lanczos_steps), int(kpm_moments)))
@@ -168,6 +190,12 @@ def dacp_get_timings(hd):
     return ms
 
 
+def dacp_get_launch_count(hd):
+    n = ctypes.c_int64(0)
+    _check(hd, _lib.dacp_get_launch_count(hd, ctypes.byref(n)))
+    return n.value
+
+
 def dacp_destroy(hd):
     if hd:
         _lib.dacp_destroy(hd)
@@ -179,6 +207,90 @@ def dacp_last_error(hd):
 
 def dacp_status_string(s):
     return _lib.dacp_status_string(int(s)).decode()
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _mcheck(m, status):
+    if status != 0:
+        raise DacpError(status, _lib.dacp_mlp_last_error(m).decode() if m else "")
+
+
+def dacp_mlp_create(n_in, n_hidden, hidden_layers, n_out, weights=None, seed=0, stream=None):
+    out = ctypes.c_void_p()
+    w = _f32(weights) if weights is not None else None
+    st = _lib.dacp_mlp_create(ctypes.byref(out), int(n_in), int(n_hidden), int(hidden_layers), int(n_out),
+                              _ptr(w), int(seed), ctypes.c_void_p(stream) if stream else None)
+    _mcheck(None, st)
+    return out.value
+
+
+def dacp_mlp_set_normalization(m, in_mean, in_std, out_mean, out_std):
+    a, b, c_, d = _f32(in_mean), _f32(in_std), _f32(out_mean), _f32(out_std)
+    _mcheck(m, _lib.dacp_mlp_set_normalization(m, _ptr(a), _ptr(b), _ptr(c_), _ptr(d)))
+
+
+def dacp_mlp_get_weights(m):
+    cnt = ctypes.c_int64(0)
+    _lib.dacp_mlp_get_weights(m, None, 0, ctypes.byref(cnt))
+    w = np.zeros(cnt.value, dtype=np.float32)
+    _mcheck(m, _lib.dacp_mlp_get_weights(m, _ptr(w), cnt.value, ctypes.byref(cnt)))
+    return w
+
+
+def dacp_mlp_set_weights(m, w):
+    w = _f32(w)
+    _mcheck(m, _lib.dacp_mlp_set_weights(m, _ptr(w), w.size))
+
+
+def dacp_mlp_forward(m, x, n_out):
+    x = _f32(x)
+    y = np.zeros((x.shape[0], n_out), dtype=np.float32)
+    _mcheck(m, _lib.dacp_mlp_forward(m, _ptr(x), x.shape[0], _ptr(y)))
+    return y
+
+
+def dacp_mlp_gradients(m, x, t, n_weights):
+    x, t = _f32(x), _f32(t)
+    g = np.zeros(n_weights, dtype=np.float32)
+    loss = ctypes.c_double(0)
+    _mcheck(m, _lib.dacp_mlp_gradients(m, _ptr(x), _ptr(t), x.shape[0], _ptr(g), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def dacp_mlp_train(m, x, t, batch=64, epochs=100, lr=1e-3, seed=0):
+    x, t = _f32(x), _f32(t)
+    loss = ctypes.c_double(0)
+    _mcheck(m, _lib.dacp_mlp_train(m, _ptr(x), _ptr(t), x.shape[0], int(batch), int(epochs), float(lr), int(seed),
+                                   ctypes.byref(loss)))
+    return loss.value
+
+
+def dacp_mlp_get_launch_count(m):
+    n = ctypes.c_int64(0)
+    _mcheck(m, _lib.dacp_mlp_get_launch_count(m, ctypes.byref(n)))
+    return n.value
+
+
+def dacp_mlp_last_error(m):
+    return _lib.dacp_mlp_last_error(m).decode() if m else ""
+
+
+def dacp_mlp_destroy(m):
+    if m:
+        _lib.dacp_mlp_destroy(m)
+
+
+def dacp_choose_params_mlp(hd, m, n_eigs, lanczos_steps=20, kpm_moments=256):
+    _check(hd, _lib.dacp_choose_params_mlp(hd, m, int(n_eigs), int(lanczos_steps), int(kpm_moments)))
+
+
+def dacp_get_features(hd, R):
+    f = np.zeros((R, N_FEATURES), dtype=np.float32)
+    _check(hd, _lib.dacp_get_features(hd, _ptr(f), f.size))
+    return f
 
 
 # ---- convenience wrapper ---------------------------------------------------
@@ -205,6 +317,12 @@ class Dacp:
 
     def choose_params(self, n_eigs, **kw):
         dacp_choose_params(self.handle, n_eigs, **kw)
+
+    def choose_params_mlp(self, mlp, n_eigs, **kw):
+        dacp_choose_params_mlp(self.handle, mlp, n_eigs, **kw)
+
+    def features(self):
+        return dacp_get_features(self.handle, self.R)
 
     def params(self):
         return dacp_get_params(self.handle, self.R)
@@ -234,6 +352,9 @@ class Dacp:
 
     def timings(self):
         return dacp_get_timings(self.handle)
+
+    def launch_count(self):
+        return dacp_get_launch_count(self.handle)
 
     def close(self):
         if self.handle:

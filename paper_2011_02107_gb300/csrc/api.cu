@@ -22,6 +22,16 @@ using namespace dacp;
 namespace {
 
 constexpr int kGraphOrders = 32;   // orders per captured graph
+constexpr int kMaxLanes = 16;      // concurrent subspace solves
+constexpr double kLaneBytes = 24e9;  // device memory budget of the lanes
+// Float32 vectors: round-off in the recurrence leaves a noise floor near
+// 1e-5 of the largest moment, so the rank cut-off rises to 1e-6 (relative)
+// and the filter order constant drops from 18 to 6: e^{2c} then matches the
+// dynamic range float32 moments resolve, and the requested levels keep
+// weights above the noise (measured on N=10..14 shards against dense eigh).
+constexpr double kEpsFp32 = 1e-6;
+constexpr double kCOrderFp32 = 6.0;
+constexpr double kCOrderFp64 = 18.0;
 
 struct Graph {
     cudaGraphExec_t exec = nullptr;
@@ -29,6 +39,25 @@ struct Graph {
 };
 
 }  // namespace
+
+// One concurrent subspace-solve lane: its own stream, library handles and
+// workspace, so that independent realizations' eigensolves overlap.
+struct Lane {
+    cudaStream_t st = nullptr;
+    cusolverDnHandle_t sol = nullptr;
+    cublasHandle_t blas = nullptr;
+    cudaEvent_t done = nullptr;
+    double *S = nullptr, *H = nullptr, *W = nullptr, *Ht = nullptr, *lam = nullptr, *lamt = nullptr;
+    double *mus = nullptr, *nus = nullptr, *sel = nullptr;
+    int *orders = nullptr, *mi = nullptr, *bad = nullptr, *info = nullptr, *nf = nullptr;
+    void* work = nullptr;
+    size_t dbytes = 0, hbytes = 0;
+    std::vector<char> work_h;
+    std::vector<double> out_h;
+    int hv[3] = {0, 0, 0};
+    int cnt = -1;
+    int r = -1;
+};
 
 struct dacp_ctx {
     int R = 0, b = 1;
@@ -49,7 +78,8 @@ struct dacp_ctx {
     std::vector<void*> allocs;
     RealInfo* info_d = nullptr;
     Item* items_d = nullptr;
-    double *J_d = nullptr, *h_d = nullptr, *pnorm_d = nullptr;
+    double *J_d = nullptr, *h_d = nullptr, *g64_d = nullptr, *pnorm_d = nullptr;
+    float* feats_d = nullptr;
     void *gam_d = nullptr, *diag_d = nullptr;
     void *psi0_d = nullptr, *A_d = nullptr, *B_d = nullptr, *U_d = nullptr, *psiE_d = nullptr;
     double *coef_d = nullptr, *apply_coef_d = nullptr, *part_d = nullptr, *norms_d = nullptr;
@@ -69,9 +99,14 @@ struct dacp_ctx {
     cublasHandle_t blas = nullptr;
     cusolverDnParams_t sp = nullptr;
 
+    std::vector<Lane> lanes;
+    int lane_M = 0, lane_neigs = 0;
+    int64_t lane_rows = 0;
+
     Graph gf, ge;
     cudaEvent_t ev[6] = {};
     double t_ms[3] = {0, 0, 0};
+    int64_t launches = 0;               // kernels of this library launched so far
     std::string err;
 };
 
@@ -143,6 +178,68 @@ void dfree(dacp_ctx* c, void* p) {
     cudaFree(p);
 }
 
+void free_lanes(dacp_ctx* c) {
+    for (auto& L : c->lanes) {
+        if (L.st) cudaStreamSynchronize(L.st);
+        for (void* p : {static_cast<void*>(L.S), static_cast<void*>(L.H), static_cast<void*>(L.W),
+                        static_cast<void*>(L.Ht), static_cast<void*>(L.lam), static_cast<void*>(L.lamt),
+                        static_cast<void*>(L.mus), static_cast<void*>(L.nus), static_cast<void*>(L.sel),
+                        static_cast<void*>(L.orders), static_cast<void*>(L.mi), static_cast<void*>(L.bad),
+                        static_cast<void*>(L.info), static_cast<void*>(L.nf), L.work})
+            dfree(c, p);
+        if (L.sol) cusolverDnDestroy(L.sol);
+        if (L.blas) cublasDestroy(L.blas);
+        if (L.done) cudaEventDestroy(L.done);
+        if (L.st) cudaStreamDestroy(L.st);
+    }
+    c->lanes.clear();
+    c->lane_M = 0;
+    c->lane_rows = 0;
+    c->lane_neigs = 0;
+}
+
+// Lanes able to solve problems of order <= M with <= rows moment rows.
+dacp_status ensure_lanes(dacp_ctx* c, int M, int64_t rows, int n_eigs) {
+    if (!c->lanes.empty() && M <= c->lane_M && rows <= c->lane_rows && n_eigs <= c->lane_neigs) return DACP_OK;
+    free_lanes(c);
+    const double per_lane = 4.0 * 8.0 * M * static_cast<double>(M) + 2.0 * 8.0 * rows * c->b * c->b;
+    int nl = std::min(c->R, kMaxLanes);
+    nl = std::max(1, std::min(nl, static_cast<int>(kLaneBytes / std::max(per_lane, 1.0))));
+    c->lanes.resize(nl);
+    const size_t MM = static_cast<size_t>(M) * M;
+    for (auto& L : c->lanes) {
+        CK(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+        CKS(cusolverDnCreate(&L.sol));
+        CKS(cusolverDnSetStream(L.sol, L.st));
+        CKB(cublasCreate(&L.blas));
+        CKB(cublasSetStream(L.blas, L.st));
+        TRY(dalloc_t(c, &L.S, MM));
+        TRY(dalloc_t(c, &L.H, MM));
+        TRY(dalloc_t(c, &L.W, MM));
+        TRY(dalloc_t(c, &L.Ht, MM));
+        TRY(dalloc_t(c, &L.lam, M));
+        TRY(dalloc_t(c, &L.lamt, M));
+        TRY(dalloc_t(c, &L.mus, static_cast<size_t>(rows) * c->b * c->b));
+        TRY(dalloc_t(c, &L.nus, static_cast<size_t>(rows) * c->b * c->b));
+        TRY(dalloc_t(c, &L.sel, static_cast<size_t>(std::max(n_eigs, 1))));
+        TRY(dalloc_t(c, &L.orders, M));
+        TRY(dalloc_t(c, &L.mi, 4));
+        TRY(dalloc_t(c, &L.bad, 1));
+        TRY(dalloc_t(c, &L.info, 1));
+        TRY(dalloc_t(c, &L.nf, 1));
+        CKS(cusolverDnXsyevd_bufferSize(L.sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
+                                        L.S, M, CUDA_R_64F, L.lam, CUDA_R_64F, &L.dbytes, &L.hbytes));
+        TRY(dalloc(c, &L.work, L.dbytes));
+        L.work_h.resize(std::max<size_t>(L.hbytes, 1));
+        L.out_h.resize(std::max(n_eigs, 1));
+    }
+    c->lane_M = M;
+    c->lane_rows = rows;
+    c->lane_neigs = n_eigs;
+    return DACP_OK;
+}
+
 StepArgs base_args(dacp_ctx* c) {
     StepArgs a;
     memset(&a, 0, sizeof(a));
@@ -197,9 +294,15 @@ dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
     }
     int done = 0;
     if (g.exec) {
-        for (; done + kGraphOrders <= orders; done += kGraphOrders) CK(cudaGraphLaunch(g.exec, c->st));
+        for (; done + kGraphOrders <= orders; done += kGraphOrders) {
+            CK(cudaGraphLaunch(g.exec, c->st));
+            c->launches += kGraphOrders * (filter ? 2 : 1);
+        }
     }
-    for (; done < orders; ++done) CK(launch_order());
+    for (; done < orders; ++done) {
+        CK(launch_order());
+        c->launches += filter ? 2 : 1;
+    }
     return DACP_OK;
 }
 
@@ -287,6 +390,7 @@ void dacp_destroy(dacp_handle c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->st) cudaStreamSynchronize(c->st);
+    free_lanes(c);
     if (c->gf.exec) cudaGraphExecDestroy(c->gf.exec);
     if (c->ge.exec) cudaGraphExecDestroy(c->ge.exec);
     for (auto& e : c->ev)
@@ -418,8 +522,8 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
     if (!ok) return bail(fail(c, DACP_ERR_CUDA, "upload failed"));
     // x-fields in the vector precision
     {
-        double* tmp = nullptr;
-        if ((s = dalloc_t(c, &tmp, c->g_h.size())) != DACP_OK) return bail(s);
+        if ((s = dalloc_t(c, &c->g64_d, c->g_h.size())) != DACP_OK) return bail(s);
+        double* tmp = c->g64_d;
         ok = ck(cudaMemcpyAsync(tmp, c->g_h.data(), c->g_h.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
              ck(launch_convert(c->fp32, tmp, c->gam_d, static_cast<int64_t>(c->g_h.size()), c->st));
         // start vectors: host float64 -> device, converted in place of psi0
@@ -429,11 +533,11 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         ok = ok && ck(cudaMemcpyAsync(tmp2, psi0, static_cast<size_t>(nv) * 8, cudaMemcpyHostToDevice, c->st)) &&
              ck(launch_convert(c->fp32, tmp2, c->psi0_d, nv, c->st));
         for (int r = 0; ok && r < n_real; ++r) ok = ck(launch_diag(c->fp32, c->info_d, r, c->N[r], c->J_d, c->h_d, c->diag_d, c->st));
+        c->launches += 2 + n_real;
         std::vector<double> ac(8 * static_cast<size_t>(n_real), 0.0);
         for (int r = 0; r < n_real; ++r) ac[8 * r] = 1.0;
         ok = ok && ck(cudaMemcpyAsync(c->apply_coef_d, ac.data(), ac.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
              ck(cudaStreamSynchronize(c->st));
-        dfree(c, tmp);
         dfree(c, tmp2);
         if (!ok) return bail(fail(c, DACP_ERR_CUDA, "set-up kernels failed: %s", cudaGetErrorString(cudaGetLastError())));
     }
@@ -467,12 +571,20 @@ dacp_status dacp_set_params(dacp_handle c, const double* emax, const double* a, 
     return apply_params(c);
 }
 
-dacp_status dacp_choose_params(dacp_handle c, int n_eigs, double d_ratio, double basis_ratio, double c_order,
-                               int lanczos_steps, int kpm_moments) {
-    TRY(check_handle(c));
+}  // extern "C"
+
+namespace {
+
+// Lanczos bound + KPM moments of column 0 of psi0, then the window, order and
+// basis size: from (d_ratio, basis_ratio, c_order) or from the network.
+dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ratio, double c_order,
+                        int lanczos_steps, int kpm_moments, dacp_mlp net) {
+    if (!(c_order > 0)) c_order = c->fp32 ? kCOrderFp32 : kCOrderFp64;
     if (n_eigs < 1 || !(d_ratio > 0) || !(basis_ratio > 0) || !(c_order > 0) || lanczos_steps < 2 ||
-        lanczos_steps > 64 || kpm_moments < 2 || (kpm_moments & 1))
+        lanczos_steps > 64 || kpm_moments < 2 * (kFeatureMoments + 1) || (kpm_moments & 1))
         return fail(c, DACP_ERR_ARG, "bad heuristic arguments");
+    if (net && (mlp_n_in(net) != kFeatures || mlp_n_out(net) != 3))
+        return fail(c, DACP_ERR_ARG, "the parameter network needs %d inputs and 3 outputs", kFeatures);
     int minN = kMaxSpins;
     for (int r = 0; r < c->R; ++r) minN = std::min(minN, c->N[r]);
     const int steps = static_cast<int>(std::min<int64_t>(lanczos_steps, static_cast<int64_t>(1) << minN));
@@ -482,13 +594,13 @@ dacp_status dacp_choose_params(dacp_handle c, int n_eigs, double d_ratio, double
     void *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *kA = nullptr, *kB = nullptr;
     double *lmom = nullptr, *beta2 = nullptr, *emax_d = nullptr, *a_d = nullptr, *kp = nullptr;
     int *K_d = nullptr, *n_d = nullptr;
+    float* knobs = nullptr;
     auto cleanup = [&]() {
         for (void* p : {v0, v1, v2, kA, kB, static_cast<void*>(lmom), static_cast<void*>(beta2),
                         static_cast<void*>(emax_d), static_cast<void*>(a_d), static_cast<void*>(kp),
-                        static_cast<void*>(K_d), static_cast<void*>(n_d)})
+                        static_cast<void*>(K_d), static_cast<void*>(n_d), static_cast<void*>(knobs)})
             dfree(c, p);
     };
-    dacp_status s = DACP_OK;
     auto run = [&]() -> dacp_status {
         TRY(dalloc(c, &v0, sv));
         TRY(dalloc(c, &v1, sv));
@@ -503,8 +615,11 @@ dacp_status dacp_choose_params(dacp_handle c, int n_eigs, double d_ratio, double
         TRY(dalloc_t(c, &kp, static_cast<size_t>(R) * kpm_moments));
         TRY(dalloc_t(c, &K_d, R));
         TRY(dalloc_t(c, &n_d, R));
+        TRY(dalloc_t(c, &knobs, static_cast<size_t>(R) * 3));
+        if (!c->feats_d) TRY(dalloc_t(c, &c->feats_d, static_cast<size_t>(R) * kFeatures));
         // v = column 0 of psi0, normalised; kept in kA for the KPM run
         CK(launch_extract_col(c->fp32, c->b, c->psi0_d, v2, c->Dtot, c->st));
+        c->launches += 3 + 4 * static_cast<int64_t>(steps) + 1 + kpm_moments / 2 + 2;
         CK(launch_normalize(c->fp32, 1, c->items_d, c->info_d, ni, v2, v2, 0, c->part_d, c->real_done_d,
                             c->norms_d, v1, kA, c->st));
         // Lanczos: w = H v - beta v_prev; alpha = <w, v>; w -= alpha v; beta = |w|
@@ -551,23 +666,57 @@ dacp_status dacp_choose_params(dacp_handle c, int n_eigs, double d_ratio, double
         a.nsteps_override = kpm_moments / 2;
         CK(cudaMemsetAsync(c->step_ctr_d, 0, sizeof(int), c->st));
         for (int k = 0; k < kpm_moments / 2; ++k) CK(launch_step(c->fp32, 1, kEvolve, a, 0, ni, c->smem, c->st));
+        CK(launch_features(R, c->info_d, c->J_d, c->h_d, c->g64_d, kp, kpm_moments, n_eigs, c->feats_d, c->st));
+        if (net) {
+            CK(mlp_forward_device(net, c->feats_d, R, knobs, c->st, &c->launches));
+        }
         CK(launch_kpm_window(R, c->info_d, kp, kpm_moments, emax_d, d_ratio * n_eigs, c_order, basis_ratio, c->b,
-                             a_d, K_d, n_d, c->st));
+                             net ? knobs : nullptr, n_eigs, a_d, K_d, n_d, c->st));
         std::vector<double> av(R);
         std::vector<int> Kv(R), nv(R);
         CK(cudaMemcpyAsync(av.data(), a_d, R * 8, cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(Kv.data(), K_d, R * 4, cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(nv.data(), n_d, R * 4, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
+        for (int r = 0; r < R; ++r) {
+            const double kn = floor(static_cast<double>(nv[r]) * M_PI / (av[r] / em[r]));
+            if (!(av[r] > 0.0) || !(av[r] < em[r]) || kn > 2.0e8)
+                return fail(c, DACP_ERR_NUMERIC, "parameter choice failed for realization %d (a = %g)", r, av[r]);
+        }
         c->emax = em;
         c->a = av;
         c->K = Kv;
         c->n = nv;
         return apply_params(c);
     };
-    s = run();
+    dacp_status s = run();
     cleanup();
     return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+dacp_status dacp_choose_params(dacp_handle c, int n_eigs, double d_ratio, double basis_ratio, double c_order,
+                               int lanczos_steps, int kpm_moments) {
+    TRY(check_handle(c));
+    return choose_impl(c, n_eigs, d_ratio, basis_ratio, c_order, lanczos_steps, kpm_moments, nullptr);
+}
+
+dacp_status dacp_choose_params_mlp(dacp_handle c, dacp_mlp net, int n_eigs, int lanczos_steps, int kpm_moments) {
+    TRY(check_handle(c));
+    if (!net) return fail(c, DACP_ERR_ARG, "NULL network");
+    return choose_impl(c, n_eigs, 2.0, 1.5, 0.0, lanczos_steps, kpm_moments, net);
+}
+
+dacp_status dacp_get_features(dacp_handle c, float* feats, int64_t cap) {
+    TRY(check_handle(c));
+    if (!c->feats_d) return fail(c, DACP_ERR_STATE, "no parameter choice yet");
+    if (!feats || cap < static_cast<int64_t>(c->R) * kFeatures) return fail(c, DACP_ERR_ARG, "capacity too small");
+    CK(cudaMemcpyAsync(feats, c->feats_d, sizeof(float) * c->R * kFeatures, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return DACP_OK;
 }
 
 dacp_status dacp_get_params(dacp_handle c, double* emax, double* a, int* K, int* n, int* kn) {
@@ -593,6 +742,7 @@ dacp_status dacp_filter(dacp_handle c) {
     CK(cudaMemcpyAsync(c->A_d, c->psi0_d, vec_bytes, cudaMemcpyDeviceToDevice, c->st));
     TRY(run_orders(c, true, maxK));
     // psi_E = w_K / |w_K| per column; w_K sits in A (K even) or B (K odd); also w_0 of the evolution
+    c->launches += 2;
     CK(launch_normalize(c->fp32, c->b, c->items_d, c->info_d, static_cast<int>(c->items.size()), c->A_d, c->B_d, 1,
                         c->part_d, c->real_done_d, c->norms_d, c->psiE_d, nullptr, c->st));
     CK(cudaEventRecord(c->ev[1], c->st));
@@ -630,7 +780,7 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
     TRY(check_handle(c));
     if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_central_eigs before dacp_basis_moments");
     if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
-    if (!(eps > 0.0)) eps = 1e-12;
+    if (!(eps > 0.0)) eps = c->fp32 ? kEpsFp32 : 1e-12;
     const int b = c->b;
     int Mmax = 0;
     int64_t rows_max = 0;
@@ -638,99 +788,88 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
         Mmax = std::max(Mmax, b * (2 * c->n[r] + 1));
         rows_max = std::max<int64_t>(rows_max, 2 * static_cast<int64_t>(c->kn[r]) + 2);
     }
-    double *S = nullptr, *H = nullptr, *W = nullptr, *Ht = nullptr, *lam = nullptr, *lamt = nullptr, *mus = nullptr,
-           *nus = nullptr, *sel = nullptr;
-    int *orders = nullptr, *mi = nullptr, *bad = nullptr, *info = nullptr, *nf = nullptr;
-    void* work = nullptr;
-    std::vector<char> work_h;
-    auto cleanup = [&]() {
-        for (void* p : {static_cast<void*>(S), static_cast<void*>(H), static_cast<void*>(W), static_cast<void*>(Ht),
-                        static_cast<void*>(lam), static_cast<void*>(lamt), static_cast<void*>(mus),
-                        static_cast<void*>(nus), static_cast<void*>(sel), static_cast<void*>(orders),
-                        static_cast<void*>(mi), static_cast<void*>(bad), static_cast<void*>(info),
-                        static_cast<void*>(nf), work})
-            dfree(c, p);
-    };
-    auto run = [&]() -> dacp_status {
-        const size_t MM = static_cast<size_t>(Mmax) * Mmax;
-        TRY(dalloc_t(c, &S, MM));
-        TRY(dalloc_t(c, &H, MM));
-        TRY(dalloc_t(c, &W, MM));
-        TRY(dalloc_t(c, &Ht, MM));
-        TRY(dalloc_t(c, &lam, Mmax));
-        TRY(dalloc_t(c, &lamt, Mmax));
-        TRY(dalloc_t(c, &mus, static_cast<size_t>(rows_max) * b * b));
-        TRY(dalloc_t(c, &nus, static_cast<size_t>(rows_max) * b * b));
-        TRY(dalloc_t(c, &sel, static_cast<size_t>(n_eigs)));
-        TRY(dalloc_t(c, &orders, Mmax));
-        TRY(dalloc_t(c, &mi, 4));
-        TRY(dalloc_t(c, &bad, 1));
-        TRY(dalloc_t(c, &info, 1));
-        TRY(dalloc_t(c, &nf, 1));
-        size_t dbytes = 0, hbytes = 0;
-        CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, Mmax,
-                                        CUDA_R_64F, S, Mmax, CUDA_R_64F, lam, CUDA_R_64F, &dbytes, &hbytes));
-        TRY(dalloc(c, &work, dbytes));
-        work_h.resize(std::max<size_t>(hbytes, 1));
-        CK(cudaEventRecord(c->ev[4], c->st));
-        for (int r = 0; r < c->R; ++r) {
-            const int L = 2 * c->n[r] + 1;
-            const int M = b * L;
-            const int rows = 2 * c->kn[r] + 2;
-            double* out = eigs + static_cast<size_t>(r) * n_eigs;
-            CK(cudaMemsetAsync(bad, 0, sizeof(int), c->st));
-            CK(launch_orders(L, c->a[r] / c->emax[r], orders, c->st));
-            CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], mus, nus, bad, c->st));
-            CK(launch_assemble(L, b, orders, mus, nus, S, H, c->st));
-            // S = V Lam_s V^T (in place), ascending
-            CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, S, M,
-                                 CUDA_R_64F, lam, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, info));
-            CK(launch_cutoff(lam, M, eps, 0, S, mi, c->st));
-            int hv[3] = {0, 0, 0};
-            CK(cudaMemcpyAsync(&hv[0], mi, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-            CK(cudaMemcpyAsync(&hv[1], bad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-            CK(cudaMemcpyAsync(&hv[2], info, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-            CK(cudaStreamSynchronize(c->st));
-            const int m = hv[0];
-            if (rank) rank[r] = m;
-            if (hv[1]) {
-                n_found[r] = -DACP_ERR_NUMERIC;
-                continue;
-            }
-            if (hv[2] != 0 || m < 1) {
-                n_found[r] = -DACP_ERR_NOT_CONVERGED;
-                continue;
-            }
-            const double* U = S + static_cast<size_t>(M - m) * M;
-            const double one = 1.0, zero = 0.0;
-            // W = H U (M x m); Ht = U^T W (m x m)
-            CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m, M, &one, H, M, U, M, &zero, W, M));
-            CKB(cublasDgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, M, &one, U, M, W, M, &zero, Ht, m));
-            CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, Ht,
-                                 m, CUDA_R_64F, lamt, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, info));
-            const double w = window > 0.0 ? window : c->a[r];
-            CK(launch_select(lamt, m, n_eigs, w, sel, nf, c->st));
-            int cnt = 0;
-            CK(cudaMemcpyAsync(&cnt, nf, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-            CK(cudaMemcpyAsync(&hv[2], info, sizeof(int), cudaMemcpyDeviceToHost, c->st));
-            CK(cudaStreamSynchronize(c->st));
-            if (hv[2] != 0) {
-                n_found[r] = -DACP_ERR_NOT_CONVERGED;
-                continue;
-            }
-            CK(cudaMemcpyAsync(out, sel, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
-            n_found[r] = cnt;
-        }
-        CK(cudaEventRecord(c->ev[5], c->st));
-        CK(cudaStreamSynchronize(c->st));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
-        c->t_ms[2] = ms;
+    TRY(ensure_lanes(c, Mmax, rows_max, n_eigs));
+    const int nl = static_cast<int>(c->lanes.size());
+    CK(cudaEventRecord(c->ev[4], c->st));
+    for (auto& L : c->lanes) CK(cudaStreamWaitEvent(L.st, c->ev[4], 0));
+
+    // Phase A on lane r % nl: moments -> S, H; S = V Lam V^T; cut-off -> m (device).
+    auto phase_a = [&](int r, Lane& L) -> dacp_status {
+        const int Ln = 2 * c->n[r] + 1;
+        const int M = b * Ln;
+        const int rows = 2 * c->kn[r] + 2;
+        CK(cudaMemsetAsync(L.bad, 0, sizeof(int), L.st));
+        c->launches += 4;
+        CK(launch_orders(Ln, c->a[r] / c->emax[r], L.orders, L.st));
+        CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], L.mus, L.nus, L.bad, L.st));
+        CK(launch_assemble(Ln, b, L.orders, L.mus, L.nus, L.S, L.H, L.st));
+        CKS(cusolverDnXsyevd(L.sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, L.S, M,
+                             CUDA_R_64F, L.lam, CUDA_R_64F, L.work, L.dbytes, L.work_h.data(), L.hbytes, L.info));
+        CK(launch_cutoff(L.lam, M, eps, 0, L.S, L.mi, L.st));
+        CK(cudaMemcpyAsync(&L.hv[0], L.mi, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+        CK(cudaMemcpyAsync(&L.hv[1], L.bad, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+        CK(cudaMemcpyAsync(&L.hv[2], L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
         return DACP_OK;
     };
-    dacp_status s = run();
-    cleanup();
-    return s;
+    // Phase B: W = H U, Ht = U^T W, eigenvalues of Ht, central selection.
+    auto phase_b = [&](int r, Lane& L) -> dacp_status {
+        CK(cudaStreamSynchronize(L.st));
+        const int M = b * (2 * c->n[r] + 1);
+        const int m = L.hv[0];
+        if (rank) rank[r] = m;
+        L.cnt = -1;
+        if (L.hv[1]) { n_found[r] = -DACP_ERR_NUMERIC; return DACP_OK; }
+        if (L.hv[2] != 0 || m < 1) { n_found[r] = -DACP_ERR_NOT_CONVERGED; return DACP_OK; }
+        const double* U = L.S + static_cast<size_t>(M - m) * M;
+        const double one = 1.0, zero = 0.0;
+        CKB(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m, M, &one, L.H, M, U, M, &zero, L.W, M));
+        CKB(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, M, &one, U, M, L.W, M, &zero, L.Ht, m));
+        CKS(cusolverDnXsyevd(L.sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, L.Ht, m,
+                             CUDA_R_64F, L.lamt, CUDA_R_64F, L.work, L.dbytes, L.work_h.data(), L.hbytes, L.info));
+        const double w = window > 0.0 ? window : c->a[r];
+        CK(launch_select(L.lamt, m, n_eigs, w, L.sel, L.nf, L.st));
+        c->launches += 1;
+        CK(cudaMemcpyAsync(&L.cnt, L.nf, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+        CK(cudaMemcpyAsync(&L.hv[2], L.info, sizeof(int), cudaMemcpyDeviceToHost, L.st));
+        CK(cudaMemcpyAsync(L.out_h.data(), L.sel, sizeof(double) * n_eigs, cudaMemcpyDeviceToHost, L.st));
+        L.r = r;
+        return DACP_OK;
+    };
+    auto collect = [&](Lane& L) -> dacp_status {
+        if (L.r < 0) return DACP_OK;
+        CK(cudaStreamSynchronize(L.st));
+        if (L.cnt >= 0) {
+            if (L.hv[2] != 0) {
+                n_found[L.r] = -DACP_ERR_NOT_CONVERGED;
+            } else {
+                memcpy(eigs + static_cast<size_t>(L.r) * n_eigs, L.out_h.data(), sizeof(double) * L.cnt);
+                n_found[L.r] = L.cnt;
+            }
+        }
+        L.r = -1;
+        return DACP_OK;
+    };
+    for (auto& L : c->lanes) L.r = -1;
+    for (int r0 = 0; r0 < c->R; r0 += nl) {
+        const int r1 = std::min(c->R, r0 + nl);
+        for (int r = r0; r < r1; ++r) {
+            Lane& L = c->lanes[r - r0];
+            TRY(collect(L));
+            TRY(phase_a(r, L));
+        }
+        for (int r = r0; r < r1; ++r) TRY(phase_b(r, c->lanes[r - r0]));
+    }
+    for (auto& L : c->lanes) TRY(collect(L));
+    for (auto& L : c->lanes) {
+        CK(cudaEventRecord(L.done, L.st));
+        CK(cudaStreamWaitEvent(c->st, L.done, 0));
+    }
+    CK(cudaEventRecord(c->ev[5], c->st));
+    CK(cudaStreamSynchronize(c->st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+    c->t_ms[2] = ms;
+    return DACP_OK;
 }
 
 dacp_status dacp_get_moments(dacp_handle c, int r, double* mu, int64_t cap, int64_t* count) {
@@ -750,6 +889,7 @@ dacp_status dacp_get_moments(dacp_handle c, int r, double* mu, int64_t cap, int6
         TRY(dalloc_t(c, &bad, 1));
         CK(cudaMemsetAsync(bad, 0, sizeof(int), c->st));
         CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], mus, nus, bad, c->st));
+        c->launches += 1;
         CK(cudaMemcpyAsync(mu, mus, sizeof(double) * nvals, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
         return DACP_OK;
@@ -772,6 +912,7 @@ dacp_status dacp_get_filtered(dacp_handle c, int r, double* psi, int64_t cap) {
         TRY(dalloc_t(c, &tmp, static_cast<size_t>(n)));
         const char* src = static_cast<const char*>(c->psiE_d) + static_cast<size_t>(c->info[r].off) * c->b * c->esz;
         CK(launch_to_double(c->fp32, src, tmp, n, c->st));
+        c->launches += 1;
         CK(cudaMemcpyAsync(psi, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
         return DACP_OK;
@@ -794,7 +935,15 @@ dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
     a.y1 = nullptr;
     a.out = static_cast<char*>(y_dev) - shift;
     CK(launch_step(c->fp32, c->b, kApply, a, c->info[r].item_begin, c->info[r].item_count, c->smem, c->st));
+    c->launches += 1;
     CK(cudaStreamSynchronize(c->st));
+    return DACP_OK;
+}
+
+dacp_status dacp_get_launch_count(dacp_handle c, int64_t* count) {
+    TRY(check_handle(c));
+    if (!count) return DACP_ERR_ARG;
+    *count = c->launches;
     return DACP_OK;
 }
 

@@ -9,6 +9,8 @@ namespace dacp {
 constexpr int kThreads = 256;       // threads per CTA of the stencil kernels
 constexpr int kMaxSpins = 26;       // N limit (2^26 states per realization)
 constexpr int kTileBytes = 65536;   // shared-memory tile of one stencil CTA
+constexpr int kFeatureMoments = 32; // Chebyshev moments fed to the parameter network
+constexpr int kFeatures = 8 + kFeatureMoments;
 
 // Per-realization geometry and run lengths, read by every stencil CTA.
 struct RealInfo {

@@ -41,7 +41,19 @@ cudaError_t launch_lanczos_scale(bool fp32, const Item* items, const RealInfo* r
 cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps,
                                  const double* pnorm, double safety, double* emax, cudaStream_t st);
 cudaError_t launch_kpm_window(int R, const RealInfo* real, const double* P, int M, const double* emax,
-                              double d_target, double c_order, double basis_ratio, int b, double* a_out,
-                              int* K_out, int* n_out, cudaStream_t st);
+                              double d_target, double c_order, double basis_ratio, int b, const float* knobs,
+                              int n_eigs, double* a_out, int* K_out, int* n_out, cudaStream_t st);
+cudaError_t launch_features(int R, const RealInfo* real, const double* J, const double* h, const double* g,
+                            const double* P, int M, int n_eigs, float* out, cudaStream_t st);
 
+// mlp.cu
+}  // namespace dacp
+
+struct dacp_mlp_ctx;
+
+namespace dacp {
+cudaError_t mlp_forward_device(struct dacp_mlp_ctx* m, const float* feats, int B, float* out, cudaStream_t st,
+                               int64_t* launches);
+int mlp_n_in(struct dacp_mlp_ctx* m);
+int mlp_n_out(struct dacp_mlp_ctx* m);
 }  // namespace dacp

@@ -140,9 +140,17 @@ __global__ void lanczos_bound_kernel(int R, const double* __restrict__ lmom, int
 // and n = ceil((basis_ratio d / b - 1) / 2).
 __global__ void kpm_window_kernel(int R, const RealInfo* __restrict__ real, const double* __restrict__ P,
                                   int M, const double* __restrict__ emax, double d_target, double c_order,
-                                  double basis_ratio, int b, double* a_out, int* K_out, int* n_out) {
+                                  double basis_ratio, int b, const float* __restrict__ knobs, int n_eigs,
+                                  double* a_out, int* K_out, int* n_out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
+    if (knobs) {
+        // learned knobs per realization: log(window ratio), filter constant, basis ratio;
+        // clamped to the range the network was trained on
+        d_target = n_eigs * exp(fmin(fmax(static_cast<double>(knobs[3 * r + 0]), 0.0), log(4.0)));
+        c_order = fmin(fmax(static_cast<double>(knobs[3 * r + 1]), 3.0), 24.0);
+        basis_ratio = fmin(fmax(static_cast<double>(knobs[3 * r + 2]), 0.6), 3.0);
+    }
     const double D = ldexp(1.0, real[r].N);
     const double* Pr = P + static_cast<int64_t>(r) * M;
     const double q = M_PI / (M + 1);
@@ -208,10 +216,54 @@ cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const doub
 }
 
 cudaError_t launch_kpm_window(int R, const RealInfo* real, const double* P, int M, const double* emax,
-                              double d_target, double c_order, double basis_ratio, int b, double* a_out,
-                              int* K_out, int* n_out, cudaStream_t st) {
-    kpm_window_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, real, P, M, emax, d_target, c_order, basis_ratio, b, a_out,
-                                                    K_out, n_out);
+                              double d_target, double c_order, double basis_ratio, int b, const float* knobs,
+                              int n_eigs, double* a_out, int* K_out, int* n_out, cudaStream_t st) {
+    kpm_window_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, real, P, M, emax, d_target, c_order, basis_ratio, b, knobs,
+                                                    n_eigs, a_out, K_out, n_out);
+    return cudaGetLastError();
+}
+
+// Features of each realization for the parameter network (kFeatures floats):
+// N, log(n_eigs / 2^N), mean/std of the x-fields, mean/std of the nonzero zz
+// couplings, mean/std of the z-fields, and mu_1..mu_32 of the normalised
+// start vector under G = H / E_max (from the KPM rows P).
+__global__ void features_kernel(int R, const RealInfo* __restrict__ real, const double* __restrict__ J,
+                                const double* __restrict__ h, const double* __restrict__ g, const double* __restrict__ P,
+                                int M, int n_eigs, float* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int N = real[r].N;
+    float* o = out + static_cast<int64_t>(r) * kFeatures;
+    auto stats = [](const double* v, int stride, int n, float* dst) {
+        double s = 0.0, s2 = 0.0;
+        for (int i = 0; i < n; ++i) { s += v[i * stride]; s2 += v[i * stride] * v[i * stride]; }
+        const double mean = n > 0 ? s / n : 0.0;
+        dst[0] = static_cast<float>(mean);
+        dst[1] = static_cast<float>(n > 0 ? sqrt(fmax(s2 / n - mean * mean, 0.0)) : 0.0);
+    };
+    o[0] = static_cast<float>(N);
+    o[1] = static_cast<float>(log(static_cast<double>(n_eigs)) - N * log(2.0));
+    stats(g + static_cast<int64_t>(r) * kMaxSpins, 1, N, o + 2);
+    const double* Jr = J + static_cast<int64_t>(r) * kMaxSpins * kMaxSpins;
+    double s = 0.0, s2 = 0.0;
+    int cnt = 0;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            const double v = Jr[i * kMaxSpins + j];
+            if (v != 0.0) { s += v; s2 += v * v; ++cnt; }
+        }
+    const double jm = cnt ? s / cnt : 0.0;
+    o[4] = static_cast<float>(jm);
+    o[5] = static_cast<float>(cnt ? sqrt(fmax(s2 / cnt - jm * jm, 0.0)) : 0.0);
+    stats(h + static_cast<int64_t>(r) * kMaxSpins, 1, N, o + 6);
+    const double* Pr = P + static_cast<int64_t>(r) * M;
+    for (int j = 1; j <= kFeatureMoments; ++j)
+        o[7 + j] = j < M ? static_cast<float>(2.0 * Pr[j] - Pr[j & 1]) : 0.f;
+}
+
+cudaError_t launch_features(int R, const RealInfo* real, const double* J, const double* h, const double* g,
+                            const double* P, int M, int n_eigs, float* out, cudaStream_t st) {
+    features_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, real, J, h, g, P, M, n_eigs, out);
     return cudaGetLastError();
 }
 
