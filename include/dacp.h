@@ -166,6 +166,15 @@ dacp_status dacp_apply_h(dacp_handle hd, int r, const void* x_dev, void* y_dev);
 dacp_status dacp_get_timings(dacp_handle hd, double* ms);
 
 /*
+ * dacp_autotune -- pick the stencil tile size (8 to 128 KB of the vector per
+ * CTA) by timing `orders` evolution orders of this handle's own realizations
+ * for each candidate, keep the fastest, and cache the choice for the process,
+ * keyed by (sorted N list, b, precision). Needs parameters; resets filter and
+ * moment results (run dacp_filter again). *tile_bytes_out may be NULL.
+ */
+dacp_status dacp_autotune(dacp_handle hd, int orders, int* tile_bytes_out);
+
+/*
  * dacp_get_launch_count -- number of this library's own CUDA kernels launched
  * on the handle since dacp_create (kernels inside cuSOLVER / cuBLAS calls are
  * not counted). A graph replay counts each kernel node it runs.

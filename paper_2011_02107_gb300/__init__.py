@@ -33,7 +33,7 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_get_weights",
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
-           "dacp_get_features"]
+           "dacp_get_features", "dacp_autotune"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -79,6 +79,7 @@ def _load():
         "dacp_mlp_get_launch_count": [P, ctypes.POINTER(L)],
         "dacp_choose_params_mlp": [P, P, I, I, I],
         "dacp_get_features": [P, P, L],
+        "dacp_autotune": [P, I, ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -287,6 +288,12 @@ def dacp_choose_params_mlp(hd, m, n_eigs, lanczos_steps=20, kpm_moments=256):
     _check(hd, _lib.dacp_choose_params_mlp(hd, m, int(n_eigs), int(lanczos_steps), int(kpm_moments)))
 
 
+def dacp_autotune(hd, orders=64):
+    tb = ctypes.c_int(0)
+    _check(hd, _lib.dacp_autotune(hd, int(orders), ctypes.byref(tb)))
+    return tb.value
+
+
 def dacp_get_features(hd, R):
     f = np.zeros((R, N_FEATURES), dtype=np.float32)
     _check(hd, _lib.dacp_get_features(hd, _ptr(f), f.size))
@@ -320,6 +327,9 @@ class Dacp:
 
     def choose_params_mlp(self, mlp, n_eigs, **kw):
         dacp_choose_params_mlp(self.handle, mlp, n_eigs, **kw)
+
+    def autotune(self, orders=64):
+        return dacp_autotune(self.handle, orders)
 
     def features(self):
         return dacp_get_features(self.handle, self.R)

@@ -10,7 +10,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <atomic>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dacp.h"
@@ -22,6 +26,7 @@ using namespace dacp;
 namespace {
 
 constexpr int kGraphOrders = 32;   // orders per captured graph
+constexpr int kMinTileBytes = 8192; // smallest tile the autotuner tries
 constexpr int kMaxLanes = 16;      // concurrent subspace solves
 constexpr double kLaneBytes = 24e9;  // device memory budget of the lanes
 // Float32 vectors: round-off in the recurrence leaves a noise floor near
@@ -46,6 +51,7 @@ struct Lane {
     cudaStream_t st = nullptr;
     cusolverDnHandle_t sol = nullptr;
     cublasHandle_t blas = nullptr;
+    cusolverDnParams_t sp = nullptr;
     cudaEvent_t done = nullptr;
     double *S = nullptr, *H = nullptr, *W = nullptr, *Ht = nullptr, *lam = nullptr, *lamt = nullptr;
     double *mus = nullptr, *nus = nullptr, *sel = nullptr;
@@ -71,6 +77,7 @@ struct dacp_ctx {
     std::vector<Item> items;
     int64_t Dtot = 0;
     int smem = 0;
+    int tile_bytes = 0;
     std::vector<double> J_h, h_h, g_h;   // [R][kMaxSpins(^2)]
     std::vector<double> pnorm;
 
@@ -85,6 +92,7 @@ struct dacp_ctx {
     double *coef_d = nullptr, *apply_coef_d = nullptr, *part_d = nullptr, *norms_d = nullptr;
     unsigned *real_done_d = nullptr, *launch_done_d = nullptr;
     int* step_ctr_d = nullptr;
+    int* err_d = nullptr;               // set by a stencil CTA whose bounded wait gave up
     double* mom_d = nullptr;
     int64_t mom_cap = 0;
 
@@ -106,11 +114,13 @@ struct dacp_ctx {
     Graph gf, ge;
     cudaEvent_t ev[6] = {};
     double t_ms[3] = {0, 0, 0};
-    int64_t launches = 0;               // kernels of this library launched so far
+    std::atomic<int64_t> launches{0};   // kernels of this library launched so far
     std::string err;
 };
 
 namespace {
+
+std::mutex g_err_mu;   // lanes may report failures from several host threads
 
 dacp_status fail(dacp_ctx* c, dacp_status s, const char* fmt, ...) {
     char buf[512];
@@ -118,7 +128,10 @@ dacp_status fail(dacp_ctx* c, dacp_status s, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
-    if (c) c->err = buf;
+    if (c) {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        c->err = buf;
+    }
     return s;
 }
 
@@ -187,6 +200,7 @@ void free_lanes(dacp_ctx* c) {
                         static_cast<void*>(L.orders), static_cast<void*>(L.mi), static_cast<void*>(L.bad),
                         static_cast<void*>(L.info), static_cast<void*>(L.nf), L.work})
             dfree(c, p);
+        if (L.sp) cusolverDnDestroyParams(L.sp);
         if (L.sol) cusolverDnDestroy(L.sol);
         if (L.blas) cublasDestroy(L.blas);
         if (L.done) cudaEventDestroy(L.done);
@@ -212,6 +226,7 @@ dacp_status ensure_lanes(dacp_ctx* c, int M, int64_t rows, int n_eigs) {
         CK(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
         CKS(cusolverDnCreate(&L.sol));
         CKS(cusolverDnSetStream(L.sol, L.st));
+        CKS(cusolverDnCreateParams(&L.sp));
         CKB(cublasCreate(&L.blas));
         CKB(cublasSetStream(L.blas, L.st));
         TRY(dalloc_t(c, &L.S, MM));
@@ -228,7 +243,7 @@ dacp_status ensure_lanes(dacp_ctx* c, int M, int64_t rows, int n_eigs) {
         TRY(dalloc_t(c, &L.bad, 1));
         TRY(dalloc_t(c, &L.info, 1));
         TRY(dalloc_t(c, &L.nf, 1));
-        CKS(cusolverDnXsyevd_bufferSize(L.sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
+        CKS(cusolverDnXsyevd_bufferSize(L.sol, L.sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
                                         L.S, M, CUDA_R_64F, L.lam, CUDA_R_64F, &L.dbytes, &L.hbytes));
         TRY(dalloc(c, &L.work, L.dbytes));
         L.work_h.resize(std::max<size_t>(L.hbytes, 1));
@@ -256,6 +271,7 @@ StepArgs base_args(dacp_ctx* c) {
     a.real_done = c->real_done_d;
     a.part = c->part_d;
     a.mom = c->mom_d;
+    a.err_flag = c->err_d;
     return a;
 }
 
@@ -302,6 +318,65 @@ dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
     for (; done < orders; ++done) {
         CK(launch_order());
         c->launches += filter ? 2 : 1;
+    }
+    return DACP_OK;
+}
+
+// Work decomposition: tiles of at most tile_bytes of the vector per CTA.
+void tile_geometry(dacp_ctx* c, int tile_bytes) {
+    int tb_cap = 0;
+    while ((static_cast<int64_t>(2) << tb_cap) * c->b * static_cast<int64_t>(c->esz) <= tile_bytes) ++tb_cap;
+    c->items.clear();
+    int max_tstates = 1;
+    for (int r = 0; r < c->R; ++r) {
+        RealInfo& R = c->info[r];
+        R.tbits = std::min(R.N, tb_cap);
+        R.item_begin = static_cast<int>(c->items.size());
+        R.item_count = 1 << (R.N - R.tbits);
+        for (int t = 0; t < R.item_count; ++t) c->items.push_back(Item{r, t});
+        max_tstates = std::max(max_tstates, 1 << R.tbits);
+    }
+    c->smem = static_cast<int>(max_tstates * c->b * c->esz);
+    c->tile_bytes = tile_bytes;
+}
+
+// Partial-sum slots for the smallest tile the autotuner may pick.
+size_t part_capacity(const dacp_ctx* c) {
+    int64_t worst = 0;
+    for (int r = 0; r < c->R; ++r) {
+        int tb = 0;
+        while ((static_cast<int64_t>(2) << tb) * c->b * static_cast<int64_t>(c->esz) <= kMinTileBytes) ++tb;
+        worst += static_cast<int64_t>(1) << (c->info[r].N - std::min(c->info[r].N, tb));
+    }
+    return static_cast<size_t>(std::max<int64_t>(worst, 1)) * 2 * c->b * c->b + 64;
+}
+
+// Switch the handle to a new tile size: items, smem attribute, graphs.
+dacp_status retile(dacp_ctx* c, int tile_bytes) {
+    tile_geometry(c, tile_bytes);
+    if (prepare_step(c->fp32, c->b, c->smem) != cudaSuccess || prepare_step(c->fp32, 1, c->smem) != cudaSuccess)
+        return fail(c, DACP_ERR_CUDA, "shared-memory attribute for %d bytes", c->smem);
+    dfree(c, c->items_d);
+    c->items_d = nullptr;
+    TRY(dalloc_t(c, &c->items_d, c->items.size()));
+    CK(cudaMemcpyAsync(c->items_d, c->items.data(), sizeof(Item) * c->items.size(), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->info_d, c->info.data(), sizeof(RealInfo) * c->R, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (Graph* g : {&c->gf, &c->ge}) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    return DACP_OK;
+}
+
+// A stencil CTA whose bounded wait on its tile copy gave up sets err_d.
+dacp_status check_device_flag(dacp_ctx* c) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (e) {
+        CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+        return fail(c, DACP_ERR_TIMEOUT, "a tile copy did not complete within the wait limit");
     }
     return DACP_OK;
 }
@@ -435,24 +510,15 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
     c->h_h.assign(static_cast<size_t>(n_real) * kMaxSpins, 0.0);
     c->g_h.assign(static_cast<size_t>(n_real) * kMaxSpins, 0.0);
     c->pnorm.assign(n_real, 0.0);
-    // tile: at most kTileBytes of the vector per CTA
-    int tb_cap = 0;
-    while ((static_cast<int64_t>(2) << tb_cap) * block_b * static_cast<int64_t>(c->esz) <= kTileBytes) ++tb_cap;
     int64_t jo = 0, ho = 0, off = 0;
-    int max_tstates = 1;
     for (int r = 0; r < n_real; ++r) {
         const int Nr = n_spins[r];
         RealInfo& R = c->info[r];
         R.N = Nr;
-        R.tbits = std::min(Nr, tb_cap);
         R.off = off;
-        R.item_begin = static_cast<int>(c->items.size());
-        R.item_count = 1 << (Nr - R.tbits);
         R.nf = 0;
         R.ne = 0;
         R.mom_off = 0;
-        for (int t = 0; t < R.item_count; ++t) c->items.push_back(Item{r, t});
-        max_tstates = std::max(max_tstates, 1 << R.tbits);
         double pn = 0.0;
         for (int i = 0; i < Nr; ++i) {
             for (int j = 0; j < Nr; ++j) {
@@ -475,10 +541,10 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         c->pnorm[r] = pn;
         jo += static_cast<int64_t>(Nr) * Nr;
         ho += Nr;
-        off += static_cast<int64_t>(1) << Nr;
+        off += ((static_cast<int64_t>(1) << Nr) + 3) & ~static_cast<int64_t>(3);   // 16-byte aligned units
     }
     c->Dtot = off;
-    c->smem = static_cast<int>(max_tstates * block_b * c->esz);
+    tile_geometry(c, kTileBytes);
     c->emax.assign(n_real, 0.0);
     c->a.assign(n_real, 0.0);
     c->K.assign(n_real, 0);
@@ -504,11 +570,12 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
     ALLOC(dalloc(c, &c->psiE_d, vec_bytes));
     ALLOC(dalloc_t(c, &c->coef_d, 8 * static_cast<size_t>(n_real)));
     ALLOC(dalloc_t(c, &c->apply_coef_d, 8 * static_cast<size_t>(n_real)));
-    ALLOC(dalloc_t(c, &c->part_d, static_cast<size_t>(ni) * 2 * block_b * block_b + 64));
+    ALLOC(dalloc_t(c, &c->part_d, part_capacity(c)));
     ALLOC(dalloc_t(c, &c->norms_d, static_cast<size_t>(n_real) * block_b));
     ALLOC(dalloc_t(c, &c->real_done_d, n_real));
     ALLOC(dalloc_t(c, &c->launch_done_d, 1));
     ALLOC(dalloc_t(c, &c->step_ctr_d, 1));
+    ALLOC(dalloc_t(c, &c->err_d, 1));
 #undef ALLOC
 
     auto ck = [&](cudaError_t e) { return e == cudaSuccess; };
@@ -518,7 +585,8 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
               ck(cudaMemcpyAsync(c->h_d, c->h_h.data(), c->h_h.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
               ck(cudaMemcpyAsync(c->pnorm_d, c->pnorm.data(), n_real * 8, cudaMemcpyHostToDevice, c->st)) &&
               ck(cudaMemsetAsync(c->real_done_d, 0, sizeof(unsigned) * n_real, c->st)) &&
-              ck(cudaMemsetAsync(c->launch_done_d, 0, sizeof(unsigned), c->st));
+              ck(cudaMemsetAsync(c->launch_done_d, 0, sizeof(unsigned), c->st)) &&
+              ck(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
     if (!ok) return bail(fail(c, DACP_ERR_CUDA, "upload failed"));
     // x-fields in the vector precision
     {
@@ -530,8 +598,20 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         double* tmp2 = nullptr;
         const int64_t nv = c->Dtot * block_b;
         if (ok && (s = dalloc_t(c, &tmp2, static_cast<size_t>(nv))) != DACP_OK) return bail(s);
-        ok = ok && ck(cudaMemcpyAsync(tmp2, psi0, static_cast<size_t>(nv) * 8, cudaMemcpyHostToDevice, c->st)) &&
-             ck(launch_convert(c->fp32, tmp2, c->psi0_d, nv, c->st));
+        // the caller's layout is packed; the device layout pads each realization to 4 states
+        int64_t packed_total = 0;
+        for (int r = 0; r < n_real; ++r) packed_total += (static_cast<int64_t>(1) << c->N[r]) * block_b;
+        ok = ok && ck(cudaMemsetAsync(c->psi0_d, 0, static_cast<size_t>(nv) * c->esz, c->st)) &&
+             ck(cudaMemcpyAsync(tmp2, psi0, static_cast<size_t>(packed_total) * 8, cudaMemcpyHostToDevice, c->st));
+        int64_t src_off = 0;
+        for (int r = 0; ok && r < n_real; ++r) {
+            const int64_t len = (static_cast<int64_t>(1) << c->N[r]) * block_b;
+            ok = ck(launch_convert(c->fp32, tmp2 + src_off,
+                                   static_cast<char*>(c->psi0_d) + static_cast<size_t>(c->info[r].off) * block_b * c->esz,
+                                   len, c->st));
+            src_off += len;
+        }
+        c->launches += n_real - 1;
         for (int r = 0; ok && r < n_real; ++r) ok = ck(launch_diag(c->fp32, c->info_d, r, c->N[r], c->J_d, c->h_d, c->diag_d, c->st));
         c->launches += 2 + n_real;
         std::vector<double> ac(8 * static_cast<size_t>(n_real), 0.0);
@@ -668,7 +748,9 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
         for (int k = 0; k < kpm_moments / 2; ++k) CK(launch_step(c->fp32, 1, kEvolve, a, 0, ni, c->smem, c->st));
         CK(launch_features(R, c->info_d, c->J_d, c->h_d, c->g64_d, kp, kpm_moments, n_eigs, c->feats_d, c->st));
         if (net) {
-            CK(mlp_forward_device(net, c->feats_d, R, knobs, c->st, &c->launches));
+            int64_t nl = 0;
+            CK(mlp_forward_device(net, c->feats_d, R, knobs, c->st, &nl));
+            c->launches += nl;
         }
         CK(launch_kpm_window(R, c->info_d, kp, kpm_moments, emax_d, d_ratio * n_eigs, c_order, basis_ratio, c->b,
                              net ? knobs : nullptr, n_eigs, a_d, K_d, n_d, c->st));
@@ -683,6 +765,7 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
             if (!(av[r] > 0.0) || !(av[r] < em[r]) || kn > 2.0e8)
                 return fail(c, DACP_ERR_NUMERIC, "parameter choice failed for realization %d (a = %g)", r, av[r]);
         }
+        TRY(check_device_flag(c));
         c->emax = em;
         c->a = av;
         c->K = Kv;
@@ -747,6 +830,7 @@ dacp_status dacp_filter(dacp_handle c) {
                         c->part_d, c->real_done_d, c->norms_d, c->psiE_d, nullptr, c->st));
     CK(cudaEventRecord(c->ev[1], c->st));
     CK(cudaStreamSynchronize(c->st));
+    TRY(check_device_flag(c));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
     c->t_ms[0] = ms;
@@ -766,6 +850,7 @@ dacp_status dacp_basis_moments(dacp_handle c) {
     TRY(run_orders(c, false, maxE));
     CK(cudaEventRecord(c->ev[3], c->st));
     CK(cudaStreamSynchronize(c->st));
+    TRY(check_device_flag(c));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
     c->t_ms[1] = ms;
@@ -803,7 +888,7 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
         CK(launch_orders(Ln, c->a[r] / c->emax[r], L.orders, L.st));
         CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], L.mus, L.nus, L.bad, L.st));
         CK(launch_assemble(Ln, b, L.orders, L.mus, L.nus, L.S, L.H, L.st));
-        CKS(cusolverDnXsyevd(L.sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, L.S, M,
+        CKS(cusolverDnXsyevd(L.sol, L.sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, L.S, M,
                              CUDA_R_64F, L.lam, CUDA_R_64F, L.work, L.dbytes, L.work_h.data(), L.hbytes, L.info));
         CK(launch_cutoff(L.lam, M, eps, 0, L.S, L.mi, L.st));
         CK(cudaMemcpyAsync(&L.hv[0], L.mi, sizeof(int), cudaMemcpyDeviceToHost, L.st));
@@ -824,7 +909,7 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
         const double one = 1.0, zero = 0.0;
         CKB(cublasDgemm(L.blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m, M, &one, L.H, M, U, M, &zero, L.W, M));
         CKB(cublasDgemm(L.blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, M, &one, U, M, L.W, M, &zero, L.Ht, m));
-        CKS(cusolverDnXsyevd(L.sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, L.Ht, m,
+        CKS(cusolverDnXsyevd(L.sol, L.sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, L.Ht, m,
                              CUDA_R_64F, L.lamt, CUDA_R_64F, L.work, L.dbytes, L.work_h.data(), L.hbytes, L.info));
         const double w = window > 0.0 ? window : c->a[r];
         CK(launch_select(L.lamt, m, n_eigs, w, L.sel, L.nf, L.st));
@@ -849,17 +934,29 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
         L.r = -1;
         return DACP_OK;
     };
+    // One host thread per lane: cuSOLVER's syevd keeps part of its work on the
+    // host, so lanes driven from a single thread would serialise on it.
     for (auto& L : c->lanes) L.r = -1;
-    for (int r0 = 0; r0 < c->R; r0 += nl) {
-        const int r1 = std::min(c->R, r0 + nl);
-        for (int r = r0; r < r1; ++r) {
-            Lane& L = c->lanes[r - r0];
-            TRY(collect(L));
-            TRY(phase_a(r, L));
+    std::vector<dacp_status> lane_status(nl, DACP_OK);
+    auto worker = [&](int li) {
+        cudaSetDevice(c->device);
+        Lane& L = c->lanes[li];
+        for (int r = li; r < c->R; r += nl) {
+            dacp_status st = phase_a(r, L);
+            if (st == DACP_OK) st = phase_b(r, L);
+            if (st == DACP_OK) st = collect(L);
+            if (st != DACP_OK) {
+                lane_status[li] = st;
+                return;
+            }
         }
-        for (int r = r0; r < r1; ++r) TRY(phase_b(r, c->lanes[r - r0]));
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int li = 0; li < nl; ++li) pool.emplace_back(worker, li);
+        for (auto& t : pool) t.join();
     }
-    for (auto& L : c->lanes) TRY(collect(L));
+    for (dacp_status st : lane_status) TRY(st);
     for (auto& L : c->lanes) {
         CK(cudaEventRecord(L.done, L.st));
         CK(cudaStreamWaitEvent(c->st, L.done, 0));
@@ -937,6 +1034,55 @@ dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
     CK(launch_step(c->fp32, c->b, kApply, a, c->info[r].item_begin, c->info[r].item_count, c->smem, c->st));
     c->launches += 1;
     CK(cudaStreamSynchronize(c->st));
+    return check_device_flag(c);
+}
+
+// Tile sizes the autotuner tries, and its cache keyed by (sizes, b, precision).
+static const int kTileCandidates[] = {8192, 16384, 32768, 65536, 131072};
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+dacp_status dacp_autotune(dacp_handle c, int orders, int* tile_bytes_out) {
+    TRY(check_handle(c));
+    if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_autotune before parameters");
+    if (orders < 4 || orders > 100000) return fail(c, DACP_ERR_ARG, "orders out of range");
+    std::vector<int> ns = c->N;
+    std::sort(ns.begin(), ns.end());
+    std::string key = std::to_string(c->b) + (c->fp32 ? "f" : "d");
+    for (int v : ns) key += "," + std::to_string(v);
+    int best = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) best = it->second;
+    }
+    if (best < 0) {
+        const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
+        double best_ms = 1e300;
+        for (int tb : kTileCandidates) {
+            TRY(retile(c, tb));
+            TRY(set_evolution_coef(c, c->emax));
+            CK(cudaMemcpyAsync(c->A_d, c->psi0_d, vec_bytes, cudaMemcpyDeviceToDevice, c->st));
+            TRY(run_orders(c, false, kGraphOrders));         // warm-up; captures the graph
+            CK(cudaMemcpyAsync(c->A_d, c->psi0_d, vec_bytes, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaEventRecord(c->ev[0], c->st));
+            TRY(run_orders(c, false, orders));
+            CK(cudaEventRecord(c->ev[1], c->st));
+            CK(cudaStreamSynchronize(c->st));
+            TRY(check_device_flag(c));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = tb;
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    TRY(retile(c, best));
+    TRY(apply_params(c));          // filter coefficients back; results must be recomputed
+    if (tile_bytes_out) *tile_bytes_out = best;
     return DACP_OK;
 }
 

@@ -55,6 +55,7 @@ struct StepArgs {
     double* mom;             // moment rows
     int nsteps_override;     // > 0: run this many orders instead of RealInfo.nf / ne
     int mom_rows_fixed;      // > 0: realization r's rows start at r * mom_rows_fixed
+    int* err_flag;           // set to 1 when a bounded device wait gives up
 };
 
 }  // namespace dacp

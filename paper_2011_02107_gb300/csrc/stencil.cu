@@ -24,6 +24,8 @@
 // w_{k+1} goes in place over w_{k-1} (each element is read and written by the
 // same thread; partners are only read from w_k).
 
+#include <string.h>
+
 #include "common.cuh"
 #include "ops.h"
 
@@ -50,13 +52,96 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// 16-byte vector units: a unit holds kStates consecutive states x B columns
+// (float32: 4 states at b = 1, 2 at b = 2, 1 at b = 4; float64: 2 states at
+// b = 1, 1 at b = 2, one 32-byte state at b = 4). Bit flips inside a unit are
+// register permutations; flips inside the tile read shared memory; flips
+// beyond the tile read the partner unit from global memory (L2).
+template <typename T, int B>
+struct Unit {
+    static constexpr int kBytes = (B * static_cast<int>(sizeof(T)) >= 16) ? B * static_cast<int>(sizeof(T)) : 16;
+    static constexpr int kVals = kBytes / static_cast<int>(sizeof(T));
+    static constexpr int kStates = kVals / B;
+    static constexpr int kLog = kStates == 4 ? 2 : (kStates == 2 ? 1 : 0);
+    static constexpr int kVec = kBytes / 16;          // float4 per unit
+};
+
+template <typename T, int B>
+__device__ __forceinline__ void ld_unit(const T* p, T (&v)[Unit<T, B>::kVals]) {
+#pragma unroll
+    for (int q = 0; q < Unit<T, B>::kVec; ++q) {
+        const float4 f = reinterpret_cast<const float4*>(p)[q];
+        memcpy(reinterpret_cast<char*>(v) + 16 * q, &f, 16);
+    }
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void ld_unit_nc(const T* p, T (&v)[Unit<T, B>::kVals]) {
+#pragma unroll
+    for (int q = 0; q < Unit<T, B>::kVec; ++q) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(p) + q);
+        memcpy(reinterpret_cast<char*>(v) + 16 * q, &f, 16);
+    }
+}
+
+template <typename T, int B>
+__device__ __forceinline__ void st_unit(T* p, const T (&v)[Unit<T, B>::kVals]) {
+#pragma unroll
+    for (int q = 0; q < Unit<T, B>::kVec; ++q) {
+        float4 f;
+        memcpy(&f, reinterpret_cast<const char*>(v) + 16 * q, 16);
+        reinterpret_cast<float4*>(p)[q] = f;
+    }
+}
+
+// ---- TMA bulk copy of the tile into shared memory, with a bounded wait -----
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Spin on phase 0 of the barrier at most `limit` times; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+constexpr int kWaitLimit = 1 << 22;   // try_wait polls (each may suspend briefly): far beyond a 64 KB copy
+constexpr int kUnitsPerPass = 2;      // units per thread in flight
+
 template <typename T, int B, int MODE>
 __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int item_base) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using U = Unit<T, B>;
+    constexpr int VU = U::kVals, SU = U::kStates, LS = U::kLog, UP = kUnitsPerPass;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
     __shared__ T gam_s[kMaxSpins];
     __shared__ double red_s[kThreads / 32][2 * B * B];
     __shared__ int last_s;
+    __shared__ __align__(8) uint64_t bar_s;
 
     const int tid = threadIdx.x;
     const int item = item_base + blockIdx.x;
@@ -101,76 +186,163 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int it
         }
         const bool use1 = (c_1 != 0.0) && (y1 != nullptr);
         const bool use2 = (c_2 != 0.0) && (y2 != nullptr);
+        const T ch = static_cast<T>(c_h), c1 = static_cast<T>(c_1), c2 = static_cast<T>(c_2);
 
         const int tstates = 1 << R.tbits;
         const int64_t tile0 = static_cast<int64_t>(it.tile) << R.tbits;   // first local state
-        const T* xg = x + R.off * B;
-        {
-            const int64_t nbytes = static_cast<int64_t>(tstates) * B * sizeof(T);
-            if ((nbytes & 15) == 0) {
-                const float4* src = reinterpret_cast<const float4*>(xg + tile0 * B);
-                float4* dst = reinterpret_cast<float4*>(smem_raw);
-                for (int64_t i = tid; i < nbytes / 16; i += kThreads) dst[i] = __ldg(src + i);
-            } else {
-                for (int i = tid; i < tstates * B; i += kThreads) tile[i] = xg[tile0 * B + i];
-            }
-        }
-        if (tid < R.N) gam_s[tid] = static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
-        __syncthreads();
-
+        const int64_t gbase = R.off * B;                                  // first value of the realization
+        const T* xg = x + gbase;
         const T* dg = static_cast<const T*>(a.diag) + R.off;
-        const T ch = static_cast<T>(c_h), c1 = static_cast<T>(c_1), c2 = static_cast<T>(c_2);
-        const int64_t gbase = R.off * B;
-        for (int sl = tid; sl < tstates; sl += kThreads) {
-            const int64_t s = tile0 + sl;
-            T xv[B], acc[B];
-            load_vals<T, B>(tile + sl * B, xv);
-            const T d = __ldg(dg + s);
-#pragma unroll
-            for (int p = 0; p < B; ++p) acc[p] = d * xv[p];
-            for (int i = 0; i < R.tbits; ++i) {
-                const T g = gam_s[i];
-                const T* q = tile + (sl ^ (1 << i)) * B;
-#pragma unroll
-                for (int p = 0; p < B; ++p) acc[p] = fma(g, q[p], acc[p]);
+        if (tid < R.N) gam_s[tid] = static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
+
+        if (tstates >= SU) {
+            // ---- unit path: stage the tile with one bulk copy -------------------
+            const uint32_t nbytes = static_cast<uint32_t>(tstates) * B * sizeof(T);
+            if (tid == 0) {
+                mbar_init(&bar_s, 1);
+                bulk_load(tile, xg + tile0 * B, nbytes, &bar_s);
             }
-            for (int i = R.tbits; i < R.N; ++i) {
-                const T g = gam_s[i];
-                T pv[B];
-                load_vals_ro<T, B>(xg + (s ^ (static_cast<int64_t>(1) << i)) * B, pv);
-#pragma unroll
-                for (int p = 0; p < B; ++p) acc[p] = fma(g, pv[p], acc[p]);
+            __syncthreads();
+            const bool landed = mbar_wait(&bar_s, 0, kWaitLimit);
+            if (!landed) {
+                atomicExch(a.err_flag, 1);
+                mbar_wait(&bar_s, 0, kWaitLimit);        // let the copy land before the CTA exits
             }
-            T o[B];
+            __syncthreads();
+            if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar_s)) : "memory");
+            if (!landed) goto reduce;
+            const int nunits = tstates / SU;
+            const int tub = R.tbits - LS;                // unit bits inside the tile
+            for (int ub = 0; ub < nunits; ub += kThreads * UP) {
+                int uu[UP];
+                bool val[UP];
+                T xv[UP][VU], acc[UP][VU], yv[UP][VU], zv[UP][VU], dv[UP][SU];
 #pragma unroll
-            for (int p = 0; p < B; ++p) o[p] = ch * acc[p];
-            if (use1) {
-                T v[B];
-                load_vals<T, B>(y1 + gbase + s * B, v);
+                for (int k = 0; k < UP; ++k) {
+                    uu[k] = ub + k * kThreads + tid;
+                    val[k] = uu[k] < nunits;
+                    const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
+                    if (val[k]) {
+                        ld_unit<T, B>(tile + uu[k] * VU, xv[k]);
+                        if (use1) ld_unit<T, B>(y1 + gbase + s0 * B, yv[k]);
+                        if (use2) ld_unit<T, B>(y2 + gbase + s0 * B, zv[k]);
 #pragma unroll
-                for (int p = 0; p < B; ++p) o[p] = fma(c1, v[p], o[p]);
-            }
-            if (use2) {
-                T v[B];
-                load_vals<T, B>(y2 + gbase + s * B, v);
-#pragma unroll
-                for (int p = 0; p < B; ++p) o[p] = fma(c2, v[p], o[p]);
-            }
-            T* op = out + gbase + s * B;
-#pragma unroll
-            for (int p = 0; p < B; ++p) op[p] = o[p];
-            if (want_mom) {
-#pragma unroll
-                for (int p = 0; p < B; ++p)
-#pragma unroll
-                    for (int q = 0; q < B; ++q) {
-                        xx[p][q] = fma(static_cast<Acc>(xv[p]), static_cast<Acc>(xv[q]), xx[p][q]);
-                        ox[p][q] = fma(static_cast<Acc>(o[p]), static_cast<Acc>(xv[q]), ox[p][q]);
+                        for (int j = 0; j < SU; ++j) dv[k][j] = __ldg(dg + s0 + j);
                     }
+                }
+#pragma unroll
+                for (int k = 0; k < UP; ++k)
+#pragma unroll
+                    for (int j = 0; j < SU; ++j)
+#pragma unroll
+                        for (int p = 0; p < B; ++p) acc[k][j * B + p] = dv[k][j] * xv[k][j * B + p];
+                // flips inside the unit
+#pragma unroll
+                for (int i = 0; i < LS; ++i) {
+                    const T g = gam_s[i];
+#pragma unroll
+                    for (int k = 0; k < UP; ++k)
+#pragma unroll
+                        for (int j = 0; j < SU; ++j)
+#pragma unroll
+                            for (int p = 0; p < B; ++p)
+                                acc[k][j * B + p] = fma(g, xv[k][(j ^ (1 << i)) * B + p], acc[k][j * B + p]);
+                }
+                // flips inside the tile (shared memory)
+                for (int i = 0; i < tub; ++i) {
+                    const T g = gam_s[LS + i];
+#pragma unroll
+                    for (int k = 0; k < UP; ++k) {
+                        if (!val[k]) continue;
+                        T pv[VU];
+                        ld_unit<T, B>(tile + (uu[k] ^ (1 << i)) * VU, pv);
+#pragma unroll
+                        for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[v], acc[k][v]);
+                    }
+                }
+                // flips beyond the tile (global memory, L2-resident partner tiles)
+#pragma unroll 2
+                for (int i = R.tbits; i < R.N; ++i) {
+                    const T g = gam_s[i];
+                    T pv[UP][VU];
+#pragma unroll
+                    for (int k = 0; k < UP; ++k) {
+                        const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
+                        if (val[k]) ld_unit_nc<T, B>(xg + (s0 ^ (static_cast<int64_t>(1) << i)) * B, pv[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < UP; ++k)
+#pragma unroll
+                        for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[k][v], acc[k][v]);
+                }
+#pragma unroll
+                for (int k = 0; k < UP; ++k) {
+                    if (!val[k]) continue;
+                    T o[VU];
+#pragma unroll
+                    for (int v = 0; v < VU; ++v) {
+                        T t = ch * acc[k][v];
+                        if (use1) t = fma(c1, yv[k][v], t);
+                        if (use2) t = fma(c2, zv[k][v], t);
+                        o[v] = t;
+                    }
+                    const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
+                    st_unit<T, B>(out + gbase + s0 * B, o);
+                    if (want_mom) {
+#pragma unroll
+                        for (int j = 0; j < SU; ++j)
+#pragma unroll
+                            for (int p = 0; p < B; ++p)
+#pragma unroll
+                                for (int q = 0; q < B; ++q) {
+                                    const Acc xq = static_cast<Acc>(xv[k][j * B + q]);
+                                    xx[p][q] = fma(static_cast<Acc>(xv[k][j * B + p]), xq, xx[p][q]);
+                                    ox[p][q] = fma(static_cast<Acc>(o[j * B + p]), xq, ox[p][q]);
+                                }
+                    }
+                }
+            }
+        } else {
+            // ---- scalar path for vectors smaller than one unit (N = 1) ----------
+            for (int i = tid; i < tstates * B; i += kThreads) tile[i] = xg[tile0 * B + i];
+            __syncthreads();
+            for (int sl = tid; sl < tstates; sl += kThreads) {
+                const int64_t s = tile0 + sl;
+                T xv[B], acc[B];
+                load_vals<T, B>(tile + sl * B, xv);
+                const T d = dg[s];
+#pragma unroll
+                for (int p = 0; p < B; ++p) acc[p] = d * xv[p];
+                for (int i = 0; i < R.tbits; ++i) {
+                    const T g = gam_s[i];
+                    const T* q = tile + (sl ^ (1 << i)) * B;
+#pragma unroll
+                    for (int p = 0; p < B; ++p) acc[p] = fma(g, q[p], acc[p]);
+                }
+                T o[B];
+#pragma unroll
+                for (int p = 0; p < B; ++p) {
+                    T t = ch * acc[p];
+                    if (use1) t = fma(c1, y1[gbase + s * B + p], t);
+                    if (use2) t = fma(c2, y2[gbase + s * B + p], t);
+                    o[p] = t;
+                }
+#pragma unroll
+                for (int p = 0; p < B; ++p) out[gbase + s * B + p] = o[p];
+                if (want_mom) {
+#pragma unroll
+                    for (int p = 0; p < B; ++p)
+#pragma unroll
+                        for (int q = 0; q < B; ++q) {
+                            xx[p][q] = fma(static_cast<Acc>(xv[p]), static_cast<Acc>(xv[q]), xx[p][q]);
+                            ox[p][q] = fma(static_cast<Acc>(o[p]), static_cast<Acc>(xv[q]), ox[p][q]);
+                        }
+                }
             }
         }
     }
 
+reduce:
     if (want_mom && active) {
         const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll

@@ -1,0 +1,185 @@
+"""Train the parameter network on runs of the method itself (GPU).
+
+For a set of seeded spin-glass problems this script
+
+1. runs plain float64 DACP with the paper's parameters (c = 18, window ratio
+   2, basis ratio 1.5) for the reference central eigenvalues;
+2. runs float32 DACP on a grid of knobs (log window ratio, filter constant c,
+   basis ratio), batched over all problems;
+3. labels each problem with the cheapest grid point that still returns every
+   requested level within 1e-2 of the local mean spacing of the reference
+   (cost = stencil traffic of the two recurrences + an M^3 dense term);
+4. trains the 40 -> 3x256 -> 3 network on the GPU with the library's own
+   kernels (dacp_mlp_train) on standardised features and labels;
+
+and writes the weights, the standardisation and the grid to an .npz file
+(``mlp_weights.npz`` next to this file by default).
+
+  python -m paper_2011_02107_gb300.train_mlp [--problems 1024] [--out path]
+"""
+
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import paper_2011_02107_gb300 as P  # noqa: E402
+import workloads as W  # noqa: E402
+
+WINDOW_RATIOS = (1.4, 1.8, 2.4)
+C_ORDERS = (4.5, 6.0, 8.0)
+BASIS_RATIOS = (0.8, 1.1, 1.5)
+HIDDEN, LAYERS = 256, 3
+SPACING_TOL = 1e-2
+
+
+def make_problems(n, seed=0):
+    """Spin-glass shards of varied size, coupling scale and requested count."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(n):
+        N = int(rng.choice([11, 12, 13]))
+        js = float(rng.choice([0.5, 1.0, 1.5]))
+        m = W.spin_glass_shard(N, seed=10_000 + i, j_scale=js)
+        frac = float(rng.choice([0.012, 0.025, 0.05]))
+        n_eigs = max(20, int(frac * (1 << N)))
+        probs.append((m, n_eigs))
+    return probs
+
+
+def local_spacing(ref, half=10):
+    """Mean spacing of the sorted reference values around each level."""
+    ref = np.sort(ref)
+    out = np.empty(len(ref))
+    for i in range(len(ref)):
+        lo, hi = max(0, i - half), min(len(ref) - 1, i + half)
+        out[i] = (ref[hi] - ref[lo]) / max(1, hi - lo)
+    return out
+
+
+def accurate(eigs, ref):
+    """Every reference level found within SPACING_TOL of its local spacing."""
+    if len(eigs) < len(ref):
+        return False, np.inf
+    eigs = np.sort(eigs)
+    ref = np.sort(ref)
+    sp = local_spacing(ref)
+    err = np.abs(eigs - ref) / sp
+    return bool(err.max() <= SPACING_TOL), float(err.max())
+
+
+def run_batch(probs, b, prec, knobs=None, n_eigs_all=None):
+    """One handle over problems sharing N; returns per-problem (eigs, params)."""
+    models = [m for m, _ in probs]
+    psis = [W.start_vectors(m["N"], b, seed=1, r=i) for i, m in enumerate(models)]
+    n_eigs = max(ne for _, ne in probs)
+    d = P.Dacp(models, psis, block_b=b, precision=prec)
+    try:
+        if knobs is None:
+            d.choose_params(n_eigs)
+        else:
+            d.choose_params(n_eigs, d_ratio=knobs[0], c_order=knobs[1], basis_ratio=knobs[2])
+        feats = d.features()
+        prm = d.params()
+        d.filter()
+        d.basis_moments()
+        eigs, nf, rank = d.central_eigs(n_eigs)
+        ms = d.timings()
+    finally:
+        d.close()
+    return eigs, nf, prm, feats, ms
+
+
+def cost(N, b, prm, r):
+    """Relative cost of one realization: stencil values moved by both
+    recurrences plus the cubic subspace solve (weights from the GB300 runs:
+    ~0.5 ns per float32 value-order at HBM speed, ~1 ns per M^3 / 10 flop)."""
+    D = 1 << N
+    orders = 2 * 2 * int(prm["K"][r]) + int(prm["kn"][r]) + 1
+    M = b * (2 * int(prm["n"][r]) + 1)
+    return 0.5e-9 * D * b * orders + 1e-9 * M ** 3 / 10.0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--problems", type=int, default=768)
+    ap.add_argument("--b", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=400)
+    ap.add_argument("--out", default=os.path.join(HERE, "mlp_weights.npz"))
+    args = ap.parse_args()
+    t0 = time.time()
+    probs = make_problems(args.problems)
+    # group by N so that one handle batches equal n_eigs / N
+    groups = {}
+    for i, (m, ne) in enumerate(probs):
+        groups.setdefault((m["N"], ne), []).append(i)
+    grid = list(itertools.product(WINDOW_RATIOS, C_ORDERS, BASIS_RATIOS))
+    feats = np.zeros((len(probs), P.N_FEATURES), np.float32)
+    best = np.full(len(probs), -1)
+    best_cost = np.full(len(probs), np.inf)
+    ok_count = np.zeros(len(grid), int)
+    for (N, ne), idx in sorted(groups.items()):
+        sub = [probs[i] for i in idx]
+        ref, nf_ref, _, f, _ = run_batch(sub, args.b, P.DACP_FP64)
+        feats[idx] = f
+        for gi, kn in enumerate(grid):
+            eigs, nf, prm, _, _ = run_batch(sub, args.b, P.DACP_FP32, knobs=kn)
+            for j, i in enumerate(idx):
+                if nf_ref[j] < ne or nf[j] < ne:
+                    continue
+                good, _ = accurate(eigs[j, :ne], ref[j, :ne])
+                if good:
+                    ok_count[gi] += 1
+                    cst = cost(N, args.b, prm, j)
+                    if cst < best_cost[i]:
+                        best_cost[i], best[i] = cst, gi
+        print(f"N={N} n_eigs={ne}: {len(idx)} problems labelled ({time.time() - t0:.0f}s)", flush=True)
+    safe = grid.index((max(WINDOW_RATIOS), 6.0, max(BASIS_RATIOS)))
+    best[best < 0] = safe
+    labels = np.array([[math.log(grid[g][0]), grid[g][1], grid[g][2]] for g in best], np.float32)
+    in_mean, in_std = feats.mean(0), feats.std(0)
+    in_std[in_std < 1e-6] = 1.0
+    out_mean, out_std = labels.mean(0), labels.std(0)
+    out_std[out_std < 1e-6] = 1.0
+    m = P.dacp_mlp_create(P.N_FEATURES, HIDDEN, LAYERS, P.N_KNOBS, seed=0)
+    try:
+        P.dacp_mlp_set_normalization(m, in_mean, in_std, out_mean, out_std)
+        loss = P.dacp_mlp_train(m, feats, labels, batch=64, epochs=args.epochs, lr=1e-3, seed=0)
+        w = P.dacp_mlp_get_weights(m)
+        pred = P.dacp_mlp_forward(m, feats, P.N_KNOBS)
+    finally:
+        P.dacp_mlp_destroy(m)
+    np.savez(args.out, weights=w, in_mean=in_mean, in_std=in_std, out_mean=out_mean, out_std=out_std,
+             hidden=HIDDEN, layers=LAYERS, grid=np.array(grid), labels=labels, features=feats,
+             meta=json.dumps({"problems": len(probs), "b": args.b, "epochs": args.epochs, "final_loss": loss,
+                              "grid_ok_counts": ok_count.tolist(), "seconds": time.time() - t0}))
+    fit = np.abs(pred - labels).mean(0)
+    print(json.dumps({"out": args.out, "final_loss": loss, "mean_abs_fit": fit.tolist(),
+                      "label_hist": np.bincount(best, minlength=len(grid)).tolist(),
+                      "seconds": round(time.time() - t0, 1)}), flush=True)
+
+
+def load(path=None, stream=None):
+    """Create a dacp_mlp from a weights file written by main()."""
+    path = path or os.path.join(HERE, "mlp_weights.npz")
+    z = np.load(path)
+    m = P.dacp_mlp_create(P.N_FEATURES, int(z["hidden"]), int(z["layers"]), P.N_KNOBS, weights=z["weights"],
+                          stream=stream)
+    P.dacp_mlp_set_normalization(m, z["in_mean"], z["in_std"], z["out_mean"], z["out_std"])
+    return m
+
+
+if __name__ == "__main__":
+    main()

@@ -213,3 +213,55 @@ def test_emax_not_a_bound_is_reported():
         assert nf[0] == -4                          # -DACP_ERR_NUMERIC
     finally:
         d.close()
+
+
+def test_autotune_keeps_results():
+    """The tuned tile size changes only the work decomposition, not the answer."""
+    models = [W.spin_glass_shard(11, seed=s) for s in range(3)]
+    psis = [W.start_vectors(11, 4, seed=3, r=i) for i in range(3)]
+    out = []
+    for tune in (False, True):
+        d = P.Dacp(models, psis, block_b=4, precision=P.DACP_FP32)
+        try:
+            d.choose_params(80)
+            if tune:
+                tb = d.autotune(orders=40)
+                assert tb in (8192, 16384, 32768, 65536, 131072)
+            d.filter()
+            d.basis_moments()
+            eigs, nf, rank = d.central_eigs(80)
+            out.append((eigs, nf))
+        finally:
+            d.close()
+    for r in range(3):
+        assert out[0][1][r] == out[1][1][r] == 80
+        assert np.abs(out[0][0][r] - out[1][0][r]).max() < 1e-6 * np.abs(out[0][0][r]).max()
+
+
+def test_padded_offsets_with_tiny_realizations():
+    """N=1 and N=2 realizations between larger ones keep every later realization aligned."""
+    models = [W.random_model(1, seed=1), W.random_model(9, seed=2), W.random_model(2, seed=3),
+              W.random_model(10, seed=4)]
+    for fp32 in (False, True):
+        for b in (1, 2, 4):
+            psis = [W.start_vectors(m["N"], b, seed=8, r=i) for i, m in enumerate(models)]
+            d = P.Dacp(models, psis, block_b=b, precision=P.DACP_FP32 if fp32 else P.DACP_FP64)
+            try:
+                for r, m in enumerate(models):
+                    x = W.start_vectors(m["N"], b, seed=9, r=r)
+                    xd = _dev(x, fp32)
+                    yd = torch.zeros_like(xd)
+                    d.apply_h(r, xd.data_ptr(), yd.data_ptr())
+                    torch.cuda.synchronize()
+                    ref = Hm.apply_h(m, x.astype(np.float32).astype(np.float64) if fp32 else x)
+                    tol = (2e-6 if fp32 else 1e-13) * max(1.0, np.abs(ref).max())
+                    assert np.abs(yd.double().cpu().numpy() - ref).max() <= tol
+                d.set_params(np.array([Hm.pauli_norm_bound(m) for m in models]),
+                             np.array([0.3 * Hm.pauli_norm_bound(m) for m in models]), 5, 2)
+                d.filter()
+                for r, m in enumerate(models):
+                    ref = DA.exp_semicircle_filter(m, psis[r], Hm.pauli_norm_bound(m), 0.3 * Hm.pauli_norm_bound(m), 5)
+                    got = d.filtered(r)
+                    assert np.abs(got - ref).max() <= (1e-4 if fp32 else 1e-10)
+            finally:
+                d.close()
