@@ -137,7 +137,8 @@ def oracle_sample(wl, budget_s=15.0):
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
     name = [k for k, v in WORKLOADS.items() if v is wl][0]
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", name,
-                        "--budget", str(budget_s)], env=env, capture_output=True, text=True, check=True)
+                        "--budget", str(budget_s), "--realizations", str(wl["R"]), "--n-eigs", str(wl["n_eigs"]),
+                        "--precision", wl["prec"]], env=env, capture_output=True, text=True, check=True)
     res = json.loads(r.stdout.strip().splitlines()[-1])
     return res["rate"], res["desc"], 1
 
@@ -214,14 +215,23 @@ def run_gpu(args, wl, rank, world):
     def dist_sum(x):
         return reduce_across_ranks(x, "sum", world, dev)
 
+    # ---- the parameter network (learned window / order / basis), if trained
+    mlp = None
+    if args.params == "mlp":
+        from paper_2011_02107_gb300 import train_mlp
+        if os.path.exists(train_mlp.DEFAULT_PATH) and wl["prec"] == "fp32":
+            mlp = train_mlp.load(stream=stream.cuda_stream)
+
     # ---- value: inputs resident on the device, K whole-path steps
     d = P.Dacp(models, psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
+    d.choose_params(n_eigs)
+    tile_bytes = d.autotune(64)            # cached per (sizes, b, precision) for this process
+    fallbacks = [0]
 
     def step():
-        d.choose_params(n_eigs)
-        d.filter()
-        d.basis_moments()
-        return d.central_eigs(n_eigs)
+        eigs, nf, rank, nfb = d.solve(n_eigs, mlp=mlp)
+        fallbacks[0] += nfb
+        return eigs, nf, rank
 
     for _ in range(args.warmup):
         step()
@@ -238,7 +248,7 @@ def run_gpu(args, wl, rank, world):
     bytes_evo = 0.0
     for _ in range(args.steps):
         eigs, nf, rank_ = step()
-        found += int(np.clip(nf, 0, None).sum())
+        found += int(np.clip(np.asarray(nf), 0, None).sum())
         phase += d.timings()
         p = d.params()
         esz = 4 if wl["prec"] == "fp32" else 8
@@ -272,6 +282,9 @@ def run_gpu(args, wl, rank, world):
         hd = P.dacp_create(n_spins, J, h, g, wl["b"], prec, psi_pinned, stream.cuda_stream)
         try:
             P.dacp_choose_params(hd, n_eigs)
+            P.dacp_autotune(hd)            # cached: only switches the tile size
+            if mlp is not None:
+                P.dacp_choose_params_mlp(hd, mlp, n_eigs)
             P.dacp_filter(hd)
             P.dacp_basis_moments(hd)
             eigs, nf, rk = P.dacp_central_eigs(hd, R, n_eigs)
@@ -281,6 +294,9 @@ def run_gpu(args, wl, rank, world):
     torch.cuda.synchronize()
     e2e_s = dist_max(time.perf_counter() - t0)
     e2e_value = dist_sum(found_e2e) / e2e_s
+
+    if mlp is not None:
+        P.dacp_mlp_destroy(mlp)
 
     # ---- roofline of the dominant kernel (evolution stencil): algorithmic bytes / time
     peaks = {}
@@ -317,6 +333,9 @@ def run_gpu(args, wl, rank, world):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "steps": e2e_steps},
         "gpu_launches": int(launches),
+        "parameter_choice": "learned network (heuristic fallback)" if mlp is not None else "heuristic",
+        "fallback_realizations": fallbacks[0],
+        "tile_bytes": tile_bytes,
         "roofline": roof,
         "clocks": clk,
     }
@@ -331,10 +350,25 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--params", default="mlp", choices=["mlp", "heuristic"],
+                    help="parameter choice: the trained network when its weights exist, else the heuristic")
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"], help="override the workload's precision")
+    ap.add_argument("--realizations", type=int, default=None, help="override the number of realizations per GPU")
+    ap.add_argument("--n-eigs", type=int, default=None, help="override the central eigenvalues per realization")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.precision or args.realizations or args.n_eigs:
+        wl = dict(wl)
+        if args.precision:
+            wl["prec"] = args.precision
+        if args.realizations:
+            wl["R"] = args.realizations
+        if args.n_eigs:
+            wl["n_eigs"] = args.n_eigs
+        wl["desc"] += f" [variant: R={wl['R']}, n_eigs={wl['n_eigs']}, {wl['prec']}]"
+        WORKLOADS[args.workload] = wl
     if args.oracle_sample:
         _oracle_sample_child(wl, args.budget)
         return 0

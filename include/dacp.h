@@ -166,13 +166,34 @@ dacp_status dacp_apply_h(dacp_handle hd, int r, const void* x_dev, void* y_dev);
 dacp_status dacp_get_timings(dacp_handle hd, double* ms);
 
 /*
- * dacp_autotune -- pick the stencil tile size (8 to 128 KB of the vector per
- * CTA) by timing `orders` evolution orders of this handle's own realizations
- * for each candidate, keep the fastest, and cache the choice for the process,
- * keyed by (sorted N list, b, precision). Needs parameters; resets filter and
- * moment results (run dacp_filter again). *tile_bytes_out may be NULL.
+ * dacp_autotune -- pick how the recurrences are launched by timing `orders`
+ * evolution orders of this handle's own realizations for every candidate:
+ * tile size (8 to 128 KB of the vector per CTA) x launch mode (per-order
+ * launches replayed from a CUDA graph, or one persistent cooperative launch
+ * with a grid barrier per order). The fastest is kept and cached for the
+ * process, keyed by (sorted N list, b, precision). Needs parameters; resets
+ * filter and moment results (run dacp_filter again). *tile_bytes_out may be
+ * NULL.
  */
 dacp_status dacp_autotune(dacp_handle hd, int orders, int* tile_bytes_out);
+
+/*
+ * dacp_set_launch / dacp_get_launch -- set or read the launch mode (0 = graph
+ * replay of per-order launches, 1 = persistent cooperative launch) and tile
+ * size in bytes (power of two, 1 KB to 128 KB). Setting resets filter and
+ * moment results.
+ */
+dacp_status dacp_set_launch(dacp_handle hd, int mode, int tile_bytes);
+dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);
+
+/*
+ * dacp_test_poison_barrier -- test hook for the bounded waits: the next
+ * persistent launch starts with a grid-barrier arrival count that can never
+ * complete, so every CTA's wait gives up after about one second and the call
+ * returns DACP_ERR_TIMEOUT with the context still usable. No GPU fault is
+ * involved.
+ */
+dacp_status dacp_test_poison_barrier(dacp_handle hd);
 
 /*
  * dacp_get_launch_count -- number of this library's own CUDA kernels launched

@@ -33,7 +33,8 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_get_weights",
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
-           "dacp_get_features", "dacp_autotune"]
+           "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
+           "dacp_test_poison_barrier"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -80,6 +81,9 @@ def _load():
         "dacp_choose_params_mlp": [P, P, I, I, I],
         "dacp_get_features": [P, P, L],
         "dacp_autotune": [P, I, ctypes.POINTER(I)],
+        "dacp_set_launch": [P, I, I],
+        "dacp_test_poison_barrier": [P],
+        "dacp_get_launch": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -294,6 +298,20 @@ def dacp_autotune(hd, orders=64):
     return tb.value
 
 
+def dacp_set_launch(hd, mode, tile_bytes):
+    _check(hd, _lib.dacp_set_launch(hd, int(mode), int(tile_bytes)))
+
+
+def dacp_test_poison_barrier(hd):
+    _check(hd, _lib.dacp_test_poison_barrier(hd))
+
+
+def dacp_get_launch(hd):
+    m, t = ctypes.c_int(0), ctypes.c_int(0)
+    _check(hd, _lib.dacp_get_launch(hd, ctypes.byref(m), ctypes.byref(t)))
+    return m.value, t.value
+
+
 def dacp_get_features(hd, R):
     f = np.zeros((R, N_FEATURES), dtype=np.float32)
     _check(hd, _lib.dacp_get_features(hd, _ptr(f), f.size))
@@ -314,7 +332,10 @@ class Dacp:
         J = np.concatenate([m["J"].ravel() for m in self.models])
         h = np.concatenate([m["h"] for m in self.models])
         g = np.concatenate([m["gamma"] for m in self.models])
-        psi0 = np.concatenate([np.ascontiguousarray(p, dtype=np.float64).ravel() for p in psi0_list])
+        self.psi0_list = [np.ascontiguousarray(p, dtype=np.float64) for p in psi0_list]
+        self.precision = precision
+        self.stream = stream
+        psi0 = np.concatenate([p.ravel() for p in self.psi0_list])
         self.handle = dacp_create(n_spins, J, h, g, block_b, precision, psi0, stream)
 
     def set_params(self, emax, a, K, n):
@@ -331,6 +352,12 @@ class Dacp:
     def autotune(self, orders=64):
         return dacp_autotune(self.handle, orders)
 
+    def set_launch(self, mode, tile_bytes):
+        dacp_set_launch(self.handle, mode, tile_bytes)
+
+    def launch(self):
+        return dacp_get_launch(self.handle)
+
     def features(self):
         return dacp_get_features(self.handle, self.R)
 
@@ -346,6 +373,30 @@ class Dacp:
     def central_eigs(self, n_eigs, window=0.0, eps=0.0):
         eigs, nf, rank = dacp_central_eigs(self.handle, self.R, n_eigs, window, eps)
         return [eigs[r, :max(nf[r], 0)].copy() for r in range(self.R)], nf, rank
+
+    def solve(self, n_eigs, mlp=None, window=0.0, eps=0.0):
+        """Whole path for the batch: parameters (network when given, else the
+        heuristic), filter, evolution, subspace solve. Realizations for which
+        the network's parameters return fewer than n_eigs levels are re-run
+        with the heuristic. Returns (eigs list, n_found, rank, n_fallback)."""
+        if mlp is not None:
+            self.choose_params_mlp(mlp, n_eigs)
+        else:
+            self.choose_params(n_eigs)
+        self.filter()
+        self.basis_moments()
+        eigs, nf, rank = self.central_eigs(n_eigs, window, eps)
+        redo = [r for r in range(self.R) if nf[r] < n_eigs] if mlp is not None else []
+        if redo:
+            sub = Dacp([self.models[r] for r in redo], [self.psi0_list[r] for r in redo], self.b, self.precision,
+                       self.stream)
+            try:
+                e2, nf2, rk2, _ = sub.solve(n_eigs, None, window, eps)
+            finally:
+                sub.close()
+            for j, r in enumerate(redo):
+                eigs[r], nf[r], rank[r] = e2[j], nf2[j], rk2[j]
+        return eigs, nf, rank, len(redo)
 
     def moments(self, r):
         p = self.params()

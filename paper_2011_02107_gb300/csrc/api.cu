@@ -93,6 +93,9 @@ struct dacp_ctx {
     unsigned *real_done_d = nullptr, *launch_done_d = nullptr;
     int* step_ctr_d = nullptr;
     int* err_d = nullptr;               // set by a stencil CTA whose bounded wait gave up
+    unsigned* bar_d = nullptr;          // grid barrier (count, generation) of the persistent launch
+    int launch_mode = 0;                // 0: per-order launches replayed from a CUDA graph, 1: persistent
+    bool poison_barrier = false;        // test hook: the next persistent launch's barrier never opens
     double* mom_d = nullptr;
     int64_t mom_cap = 0;
 
@@ -272,6 +275,8 @@ StepArgs base_args(dacp_ctx* c) {
     a.part = c->part_d;
     a.mom = c->mom_d;
     a.err_flag = c->err_d;
+    a.bar_count = c->bar_d;
+    a.bar_gen = c->bar_d + 1;
     return a;
 }
 
@@ -284,6 +289,17 @@ dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
     CK(cudaMemsetAsync(c->step_ctr_d, 0, sizeof(int), c->st));
     const StepArgs a = base_args(c);
     const int ni = static_cast<int>(c->items.size());
+    if (c->launch_mode == 1) {
+        // every order in one cooperative launch with a bounded grid barrier
+        // a poisoned arrival count can never reach gridDim - 1: every CTA's bounded wait runs out
+        CK(cudaMemsetAsync(c->bar_d, c->poison_barrier ? 0x40 : 0, sizeof(unsigned), c->st));
+        CK(cudaMemsetAsync(c->bar_d + 1, 0, sizeof(unsigned), c->st));
+        c->poison_barrier = false;
+        int grid = 0;
+        CK(launch_persistent(c->fp32, c->b, filter ? 0 : 1, a, ni, orders, c->smem, c->st, &grid));
+        c->launches += 1;
+        return DACP_OK;
+    }
     auto launch_order = [&]() -> cudaError_t {
         cudaError_t e;
         if (filter) {
@@ -576,6 +592,7 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
     ALLOC(dalloc_t(c, &c->launch_done_d, 1));
     ALLOC(dalloc_t(c, &c->step_ctr_d, 1));
     ALLOC(dalloc_t(c, &c->err_d, 1));
+    ALLOC(dalloc_t(c, &c->bar_d, 2));
 #undef ALLOC
 
     auto ck = [&](cudaError_t e) { return e == cudaSuccess; };
@@ -586,7 +603,8 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
               ck(cudaMemcpyAsync(c->pnorm_d, c->pnorm.data(), n_real * 8, cudaMemcpyHostToDevice, c->st)) &&
               ck(cudaMemsetAsync(c->real_done_d, 0, sizeof(unsigned) * n_real, c->st)) &&
               ck(cudaMemsetAsync(c->launch_done_d, 0, sizeof(unsigned), c->st)) &&
-              ck(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st));
+              ck(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->st)) &&
+              ck(cudaMemsetAsync(c->bar_d, 0, 2 * sizeof(unsigned), c->st));
     if (!ok) return bail(fail(c, DACP_ERR_CUDA, "upload failed"));
     // x-fields in the vector precision
     {
@@ -1039,6 +1057,7 @@ dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
 
 // Tile sizes the autotuner tries, and its cache keyed by (sizes, b, precision).
 static const int kTileCandidates[] = {8192, 16384, 32768, 65536, 131072};
+static const int kNumTiles = 5;
 static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tune_cache;
 
@@ -1059,7 +1078,9 @@ dacp_status dacp_autotune(dacp_handle c, int orders, int* tile_bytes_out) {
     if (best < 0) {
         const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
         double best_ms = 1e300;
-        for (int tb : kTileCandidates) {
+        for (int cand = 0; cand < 2 * kNumTiles; ++cand) {
+            const int tb = kTileCandidates[cand % kNumTiles];
+            c->launch_mode = cand / kNumTiles;
             TRY(retile(c, tb));
             TRY(set_evolution_coef(c, c->emax));
             CK(cudaMemcpyAsync(c->A_d, c->psi0_d, vec_bytes, cudaMemcpyDeviceToDevice, c->st));
@@ -1074,15 +1095,40 @@ dacp_status dacp_autotune(dacp_handle c, int orders, int* tile_bytes_out) {
             CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
             if (ms < best_ms) {
                 best_ms = ms;
-                best = tb;
+                best = cand;
             }
         }
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    TRY(retile(c, best));
+    c->launch_mode = best / kNumTiles;
+    TRY(retile(c, kTileCandidates[best % kNumTiles]));
     TRY(apply_params(c));          // filter coefficients back; results must be recomputed
-    if (tile_bytes_out) *tile_bytes_out = best;
+    if (tile_bytes_out) *tile_bytes_out = kTileCandidates[best % kNumTiles];
+    return DACP_OK;
+}
+
+dacp_status dacp_set_launch(dacp_handle c, int mode, int tile_bytes) {
+    TRY(check_handle(c));
+    if (mode != 0 && mode != 1) return fail(c, DACP_ERR_ARG, "launch mode must be 0 or 1");
+    if (tile_bytes < 1024 || tile_bytes > 131072 || (tile_bytes & (tile_bytes - 1)))
+        return fail(c, DACP_ERR_ARG, "tile_bytes must be a power of two in [1 KB, 128 KB]");
+    c->launch_mode = mode;
+    TRY(retile(c, tile_bytes));
+    if (c->state > 1) c->state = 1;
+    return DACP_OK;
+}
+
+dacp_status dacp_test_poison_barrier(dacp_handle c) {
+    TRY(check_handle(c));
+    c->poison_barrier = true;
+    return DACP_OK;
+}
+
+dacp_status dacp_get_launch(dacp_handle c, int* mode, int* tile_bytes) {
+    TRY(check_handle(c));
+    if (mode) *mode = c->launch_mode;
+    if (tile_bytes) *tile_bytes = c->tile_bytes;
     return DACP_OK;
 }
 

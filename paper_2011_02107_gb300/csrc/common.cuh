@@ -56,6 +56,8 @@ struct StepArgs {
     int nsteps_override;     // > 0: run this many orders instead of RealInfo.nf / ne
     int mom_rows_fixed;      // > 0: realization r's rows start at r * mom_rows_fixed
     int* err_flag;           // set to 1 when a bounded device wait gives up
+    unsigned* bar_count;     // grid barrier of the persistent launch: arrivals
+    unsigned* bar_gen;       // and generation
 };
 
 }  // namespace dacp

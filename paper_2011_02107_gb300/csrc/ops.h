@@ -10,6 +10,8 @@ namespace dacp {
 
 // stencil.cu
 cudaError_t prepare_step(bool fp32, int b, int smem);
+cudaError_t launch_persistent(bool fp32, int b, int seq, const StepArgs& a, int n_items, int orders, int smem,
+                              cudaStream_t st, int* grid_out);
 cudaError_t launch_step(bool fp32, int b, int mode, const StepArgs& a, int item_base, int n_items, int smem,
                         cudaStream_t st);
 cudaError_t launch_diag(bool fp32, const RealInfo* real, int r, int N, const double* J, const double* h,

@@ -142,7 +142,9 @@ __global__ void kpm_window_kernel(int R, const RealInfo* __restrict__ real, cons
                                   int M, const double* __restrict__ emax, double d_target, double c_order,
                                   double basis_ratio, int b, const float* __restrict__ knobs, int n_eigs,
                                   double* a_out, int* K_out, int* n_out) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per realization: the lanes share the moment sum of each count evaluation
+    const int r = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
     if (r >= R) return;
     if (knobs) {
         // learned knobs per realization: log(window ratio), filter constant, basis ratio;
@@ -157,12 +159,14 @@ __global__ void kpm_window_kernel(int R, const RealInfo* __restrict__ real, cons
     const double cq = 1.0 / tan(q);
     auto count = [&](double ar) {
         const double phi = acos(ar);
-        double tot = Pr[0] * (M_PI - 2.0 * phi) / M_PI;           // g_0 = 1, mu_0 = P_0
-        for (int j = 1; j < M; ++j) {
+        double tot = lane == 0 ? Pr[0] * (M_PI - 2.0 * phi) / M_PI : 0.0;   // g_0 = 1, mu_0 = P_0
+        for (int j = 1 + lane; j < M; j += 32) {
             const double g = ((M - j + 1) * cos(q * j) + sin(q * j) * cq) / (M + 1);
             const double mu = 2.0 * Pr[j] - Pr[j & 1];
             tot += 2.0 * g * mu * (sin(j * (M_PI - phi)) - sin(j * phi)) / (M_PI * j);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
         return D * tot;
     };
     const double em = emax[r];
@@ -177,10 +181,12 @@ __global__ void kpm_window_kernel(int R, const RealInfo* __restrict__ real, cons
         }
         a = 0.5 * (lo + hi) * em;
     }
-    a_out[r] = a;
-    K_out[r] = static_cast<int>(ceil(c_order * em / a));
-    const double n = ceil((basis_ratio * d_target / b - 1.0) / 2.0);
-    n_out[r] = n < 1.0 ? 1 : static_cast<int>(n);
+    if (lane == 0) {
+        a_out[r] = a;
+        K_out[r] = static_cast<int>(ceil(c_order * em / a));
+        const double n = ceil((basis_ratio * d_target / b - 1.0) / 2.0);
+        n_out[r] = n < 1.0 ? 1 : static_cast<int>(n);
+    }
 }
 
 cudaError_t launch_lanczos_orth(bool fp32, const Item* items, const RealInfo* real, int n_items, const void* v,
@@ -218,8 +224,8 @@ cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const doub
 cudaError_t launch_kpm_window(int R, const RealInfo* real, const double* P, int M, const double* emax,
                               double d_target, double c_order, double basis_ratio, int b, const float* knobs,
                               int n_eigs, double* a_out, int* K_out, int* n_out, cudaStream_t st) {
-    kpm_window_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, real, P, M, emax, d_target, c_order, basis_ratio, b, knobs,
-                                                    n_eigs, a_out, K_out, n_out);
+    kpm_window_kernel<<<(R + 3) / 4, 128, 0, st>>>(R, real, P, M, emax, d_target, c_order, basis_ratio, b, knobs,
+                                                   n_eigs, a_out, K_out, n_out);
     return cudaGetLastError();
 }
 

@@ -84,6 +84,26 @@ __device__ __forceinline__ void ld_unit_nc(const T* p, T (&v)[Unit<T, B>::kVals]
     }
 }
 
+// L2-coherent load (bypasses L1): for vectors rewritten inside one persistent launch.
+template <typename T, int B>
+__device__ __forceinline__ void ld_unit_cg(const T* p, T (&v)[Unit<T, B>::kVals]) {
+#pragma unroll
+    for (int q = 0; q < Unit<T, B>::kVec; ++q) {
+        const float4 f = __ldcg(reinterpret_cast<const float4*>(p) + q);
+        memcpy(reinterpret_cast<char*>(v) + 16 * q, &f, 16);
+    }
+}
+
+template <typename T, int B, bool COHERENT>
+__device__ __forceinline__ void ld_unit_g(const T* p, T (&v)[Unit<T, B>::kVals]) {
+    if (COHERENT) ld_unit_cg<T, B>(p, v); else ld_unit_nc<T, B>(p, v);
+}
+
+template <typename T, int B, bool COHERENT>
+__device__ __forceinline__ void ld_unit_rw(const T* p, T (&v)[Unit<T, B>::kVals]) {
+    if (COHERENT) ld_unit_cg<T, B>(p, v); else ld_unit<T, B>(p, v);
+}
+
 template <typename T, int B>
 __device__ __forceinline__ void st_unit(T* p, const T (&v)[Unit<T, B>::kVals]) {
 #pragma unroll
@@ -115,9 +135,18 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-// Spin on phase 0 of the barrier at most `limit` times; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
-    for (int i = 0; i < limit; ++i) {
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitNs = 1000000000ull;   // bounded waits give up after one second
+
+// Wait for the barrier phase `parity`; false when kWaitNs pass first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int /*unused*/) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -125,15 +154,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
     }
-    return false;
 }
 
-constexpr int kWaitLimit = 1 << 22;   // try_wait polls (each may suspend briefly): far beyond a 64 KB copy
+constexpr int kWaitLimit = 0;         // (time-based: kWaitNs)
 constexpr int kUnitsPerPass = 2;      // units per thread in flight
 
-template <typename T, int B, int MODE>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int item_base) {
+// One tile of one realization at order `step`. COHERENT = the vectors may have
+// been rewritten earlier in the same (persistent) launch: global reads then
+// bypass L1.
+template <typename T, int B, int MODE, bool COHERENT>
+__device__ __forceinline__ void tile_step(const StepArgs& a, const int item, const int step) {
     using U = Unit<T, B>;
     constexpr int VU = U::kVals, SU = U::kStates, LS = U::kLog, UP = kUnitsPerPass;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -144,11 +176,8 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int it
     __shared__ __align__(8) uint64_t bar_s;
 
     const int tid = threadIdx.x;
-    const int item = item_base + blockIdx.x;
     const Item it = a.items[item];
     const RealInfo R = a.real[it.r];
-    int step = 0;
-    if (MODE != kApply) step = *a.step_ctr;
     int nsteps = (MODE == kEvolve) ? R.ne : (MODE == kApply ? 1 : R.nf);
     if (MODE != kApply && a.nsteps_override > 0) nsteps = a.nsteps_override;
     const bool active = step < nsteps;
@@ -224,8 +253,8 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int it
                     const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
                     if (val[k]) {
                         ld_unit<T, B>(tile + uu[k] * VU, xv[k]);
-                        if (use1) ld_unit<T, B>(y1 + gbase + s0 * B, yv[k]);
-                        if (use2) ld_unit<T, B>(y2 + gbase + s0 * B, zv[k]);
+                        if (use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
+                        if (use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
 #pragma unroll
                         for (int j = 0; j < SU; ++j) dv[k][j] = __ldg(dg + s0 + j);
                     }
@@ -268,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int it
 #pragma unroll
                     for (int k = 0; k < UP; ++k) {
                         const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
-                        if (val[k]) ld_unit_nc<T, B>(xg + (s0 ^ (static_cast<int64_t>(1) << i)) * B, pv[k]);
+                        if (val[k]) ld_unit_g<T, B, COHERENT>(xg + (s0 ^ (static_cast<int64_t>(1) << i)) * B, pv[k]);
                     }
 #pragma unroll
                     for (int k = 0; k < UP; ++k)
@@ -304,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int it
             }
         } else {
             // ---- scalar path for vectors smaller than one unit (N = 1) ----------
-            for (int i = tid; i < tstates * B; i += kThreads) tile[i] = xg[tile0 * B + i];
+            for (int i = tid; i < tstates * B; i += kThreads) tile[i] = COHERENT ? __ldcg(xg + tile0 * B + i) : xg[tile0 * B + i];
             __syncthreads();
             for (int sl = tid; sl < tstates; sl += kThreads) {
                 const int64_t s = tile0 + sl;
@@ -323,8 +352,8 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int it
 #pragma unroll
                 for (int p = 0; p < B; ++p) {
                     T t = ch * acc[p];
-                    if (use1) t = fma(c1, y1[gbase + s * B + p], t);
-                    if (use2) t = fma(c2, y2[gbase + s * B + p], t);
+                    if (use1) t = fma(c1, COHERENT ? __ldcg(y1 + gbase + s * B + p) : y1[gbase + s * B + p], t);
+                    if (use2) t = fma(c2, COHERENT ? __ldcg(y2 + gbase + s * B + p) : y2[gbase + s * B + p], t);
                     o[p] = t;
                 }
 #pragma unroll
@@ -382,9 +411,16 @@ reduce:
         }
     }
 
+    __syncthreads();   // the tile buffer is reused by the next tile of a persistent CTA
+}
+
+template <typename T, int B, int MODE>
+__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int item_base) {
+    int step = 0;
+    if (MODE != kApply) step = *a.step_ctr;
+    tile_step<T, B, MODE, false>(a, item_base + blockIdx.x, step);
     if (MODE == kFilter2 || MODE == kEvolve) {
-        __syncthreads();
-        if (tid == 0) {
+        if (threadIdx.x == 0) {
             __threadfence();
             const unsigned prev = atomicAdd(a.launch_done, 1u);
             if (prev == gridDim.x - 1) {
@@ -392,6 +428,57 @@ reduce:
                 __threadfence();
                 atomicAdd(a.step_ctr, 1);
             }
+        }
+    }
+}
+
+// Device-wide barrier of a cooperative launch. The wait is bounded (kWaitNs):
+// on expiry it raises err_flag (2) and every CTA leaves the order loop at its
+// next barrier, so no CTA spins forever.
+
+__device__ __forceinline__ bool grid_sync(const StepArgs& a) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = a.bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(a.bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(a.bar_count, 0u);
+            __threadfence();
+            atomicAdd(a.bar_gen, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*gen == g) {
+                if (global_ns() - t0 > kWaitNs) {
+                    ok = 0;
+                    atomicExch(a.err_flag, 2);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok && (*reinterpret_cast<volatile int*>(a.err_flag) == 0);
+    }
+    __syncthreads();
+    return ok_s;
+}
+
+// All orders of the filter (SEQ = 0: two passes per order) or the evolution
+// (SEQ = 1) in one cooperative launch; CTAs take tiles round-robin.
+template <typename T, int B, int SEQ>
+__global__ void __launch_bounds__(kThreads) persistent_kernel(const StepArgs a, int n_items, int orders) {
+    for (int k = 0; k < orders; ++k) {
+        if (SEQ == 0) {
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step<T, B, kFilter1, true>(a, item, k);
+            if (!grid_sync(a)) return;
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step<T, B, kFilter2, true>(a, item, k);
+            if (!grid_sync(a)) return;
+        } else {
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step<T, B, kEvolve, true>(a, item, k);
+            if (!grid_sync(a)) return;
         }
     }
 }
@@ -446,6 +533,46 @@ static cudaError_t launch_b(int b, int mode, const StepArgs& a, int item_base, i
         case 2: return launch_mode<T, 2>(mode, a, item_base, n_items, smem, st);
         case 4: return launch_mode<T, 4>(mode, a, item_base, n_items, smem, st);
     }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int B, int SEQ>
+static cudaError_t launch_persistent_tb(const StepArgs& a, int n_items, int orders, int smem, cudaStream_t st,
+                                       int* grid_out) {
+    auto k = persistent_kernel<T, B, SEQ>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int grid = sms * per_sm;
+    if (grid > n_items) grid = n_items;
+    if (grid_out) *grid_out = grid;
+    StepArgs args = a;
+    int ni = n_items, no = orders;
+    void* params[] = {&args, &ni, &no};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k), dim3(grid), dim3(kThreads), params, smem, st);
+}
+
+// Every filter (seq 0) or evolution (seq 1) order in one cooperative launch.
+cudaError_t launch_persistent(bool fp32, int b, int seq, const StepArgs& a, int n_items, int orders, int smem,
+                              cudaStream_t st, int* grid_out) {
+#define DACP_LP(T, BB) \
+    return seq == 0 ? launch_persistent_tb<T, BB, 0>(a, n_items, orders, smem, st, grid_out) \
+                    : launch_persistent_tb<T, BB, 1>(a, n_items, orders, smem, st, grid_out)
+    if (fp32) {
+        if (b == 1) DACP_LP(float, 1);
+        if (b == 2) DACP_LP(float, 2);
+        if (b == 4) DACP_LP(float, 4);
+    } else {
+        if (b == 1) DACP_LP(double, 1);
+        if (b == 2) DACP_LP(double, 2);
+        if (b == 4) DACP_LP(double, 4);
+    }
+#undef DACP_LP
     return cudaErrorInvalidValue;
 }
 

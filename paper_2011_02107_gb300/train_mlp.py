@@ -42,6 +42,7 @@ WINDOW_RATIOS = (1.4, 1.8, 2.4)
 C_ORDERS = (4.5, 6.0, 8.0)
 BASIS_RATIOS = (0.8, 1.1, 1.5)
 HIDDEN, LAYERS = 256, 3
+DEFAULT_PATH = os.path.join(HERE, "mlp_weights.npz")
 SPACING_TOL = 1e-2
 
 
@@ -117,7 +118,7 @@ def main():
     ap.add_argument("--problems", type=int, default=768)
     ap.add_argument("--b", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=400)
-    ap.add_argument("--out", default=os.path.join(HERE, "mlp_weights.npz"))
+    ap.add_argument("--out", default=DEFAULT_PATH)
     args = ap.parse_args()
     t0 = time.time()
     probs = make_problems(args.problems)
@@ -173,7 +174,7 @@ def main():
 
 def load(path=None, stream=None):
     """Create a dacp_mlp from a weights file written by main()."""
-    path = path or os.path.join(HERE, "mlp_weights.npz")
+    path = path or DEFAULT_PATH
     z = np.load(path)
     m = P.dacp_mlp_create(P.N_FEATURES, int(z["hidden"]), int(z["layers"]), P.N_KNOBS, weights=z["weights"],
                           stream=stream)

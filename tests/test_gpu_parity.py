@@ -265,3 +265,48 @@ def test_padded_offsets_with_tiny_realizations():
                     assert np.abs(got - ref).max() <= (1e-4 if fp32 else 1e-10)
             finally:
                 d.close()
+
+
+def test_persistent_launch_matches_graph_replay():
+    """One cooperative launch with a grid barrier per order gives the same moments
+    as per-order launches: the tiles, their order and the reductions are the same."""
+    models = [W.spin_glass_shard(12, seed=s) for s in range(5)] + [W.chain(9)]
+    psis = [W.start_vectors(m["N"], 2, seed=6, r=i) for i, m in enumerate(models)]
+    mus = []
+    for mode in (0, 1):
+        d = P.Dacp(models, psis, block_b=2, precision=P.DACP_FP32)
+        try:
+            d.choose_params(60)
+            d.set_launch(mode, 16384)
+            assert d.launch() == (mode, 16384)
+            d.filter()
+            d.basis_moments()
+            mus.append([d.moments(r) for r in range(len(models))])
+            eigs, nf, rank = d.central_eigs(60)
+            assert (nf == 60).all()
+        finally:
+            d.close()
+    for a, b in zip(*mus):
+        assert np.array_equal(a, b)
+
+
+def test_bounded_barrier_wait_reports_timeout_and_recovers():
+    """A grid barrier that can never open (host-side poisoned arrival count): each
+    CTA gives up after about a second, the call returns DACP_ERR_TIMEOUT and the
+    context keeps working."""
+    m = W.spin_glass_shard(10, seed=1)
+    psi = W.start_vectors(10, 1, seed=2)
+    d = P.Dacp([m], [psi], block_b=1, precision=P.DACP_FP32)
+    try:
+        d.choose_params(30)
+        d.set_launch(1, 8192)
+        P.dacp_test_poison_barrier(d.handle)
+        with pytest.raises(P.DacpError) as e:
+            d.filter()
+        assert e.value.status == 5
+        d.filter()
+        d.basis_moments()
+        eigs, nf, rank = d.central_eigs(30)
+        assert nf[0] == 30
+    finally:
+        d.close()
