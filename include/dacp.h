@@ -259,6 +259,40 @@ dacp_status dacp_choose_params_mlp(dacp_handle hd, dacp_mlp m, int n_eigs, int l
  * (float32, [n_real][40]) from the last parameter choice. */
 dacp_status dacp_get_features(dacp_handle hd, float* feats, int64_t cap);
 
+/*
+ * dacp_moments_noalloc -- Chebyshev moments of one realization without any
+ * device allocation. The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc -- code running while its stream is
+ * being captured into a CUDA graph (allocation is illegal there), engines
+ * whose device memory all comes from their own pool or arena, and loops that
+ * must not enter an allocator.
+ *
+ *   n_spins      N, 1 <= N <= 16; larger N returns DACP_ERR_ARG (the scratch
+ *                array below holds 3 x 2^16 float64 states).
+ *   J, h, gamma  host arrays as in dacp_create for one realization (J is
+ *                N x N row-major, only i<j read).
+ *   emax         bound on |E|; G = H / emax.
+ *   psi_dev      device pointer, 2^N float64: the start vector (used as given,
+ *                not normalised).
+ *   n_orders     evolution orders k = 0 .. n_orders-1.
+ *   mu_dev       device pointer, 2 * n_orders float64: on return
+ *                mu_j = <psi| T_j(G) |psi>, j = 0 .. 2 n_orders - 1, from the
+ *                same fused stencil kernel as dacp_basis_moments.
+ *   stream       cudaStream_t or NULL; the call returns when the work is done.
+ *
+ * Scratch: one file-scope device array of about 1.6 MB (vectors, diagonal,
+ * couplings, partial sums, counters), held by every GPU that loads the
+ * library until the process exits. The first call on a device looks up the
+ * array's address and sets the kernel's shared-memory limit; make that first
+ * call before any stream capture. Every call overwrites the array, and two
+ * calls that overlap on the GPU (different streams or threads) race on it and
+ * corrupt each other's results: serialise them.
+ * Returns DACP_OK, DACP_ERR_ARG, DACP_ERR_CUDA or DACP_ERR_TIMEOUT.
+ */
+dacp_status dacp_moments_noalloc(int n_spins, const double* J, const double* h, const double* gamma,
+                                 double emax, const double* psi_dev, int n_orders, double* mu_dev,
+                                 void* stream);
+
 /* dacp_last_error -- message of the last failure on this handle (owned by
  * the handle, valid until the next call on it). */
 const char* dacp_last_error(dacp_handle hd);

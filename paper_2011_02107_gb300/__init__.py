@@ -34,7 +34,7 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
-           "dacp_test_poison_barrier"]
+           "dacp_test_poison_barrier", "dacp_moments_noalloc"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -83,6 +83,7 @@ def _load():
         "dacp_autotune": [P, I, ctypes.POINTER(I)],
         "dacp_set_launch": [P, I, I],
         "dacp_test_poison_barrier": [P],
+        "dacp_moments_noalloc": [I, P, P, P, D, P, I, P, P],
         "dacp_get_launch": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
@@ -300,6 +301,19 @@ def dacp_autotune(hd, orders=64):
 
 def dacp_set_launch(hd, mode, tile_bytes):
     _check(hd, _lib.dacp_set_launch(hd, int(mode), int(tile_bytes)))
+
+
+def dacp_moments_noalloc(model, emax, psi_dev_ptr, n_orders, mu_dev_ptr, stream=None):
+    """Allocation-free moments of one realization (see include/dacp.h); device pointers in and out."""
+    N = int(model["N"])
+    J = np.ascontiguousarray(model["J"], dtype=np.float64).reshape(N, N)
+    h = np.ascontiguousarray(model["h"], dtype=np.float64)
+    g = np.ascontiguousarray(model["gamma"], dtype=np.float64)
+    st = _lib.dacp_moments_noalloc(N, _ptr(J), _ptr(h), _ptr(g), float(emax), ctypes.c_void_p(psi_dev_ptr),
+                                   int(n_orders), ctypes.c_void_p(mu_dev_ptr),
+                                   ctypes.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise DacpError(st, "dacp_moments_noalloc")
 
 
 def dacp_test_poison_barrier(hd):
