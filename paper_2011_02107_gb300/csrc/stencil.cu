@@ -160,6 +160,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int /*
 
 constexpr int kWaitLimit = 0;         // (time-based: kWaitNs)
 constexpr int kUnitsPerPass = 2;      // units per thread in flight
+constexpr int kMaxTileUnitBits = 14;   // unit bits of the largest tile (128 KB of float32 b = 1)
+constexpr int kMaxGlobalBitsUnrolled = 10;
 
 // One tile of one realization at order `step`. COHERENT = the vectors may have
 // been rewritten earlier in the same (persistent) launch: global reads then
@@ -277,32 +279,51 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                             for (int p = 0; p < B; ++p)
                                 acc[k][j * B + p] = fma(g, xv[k][(j ^ (1 << i)) * B + p], acc[k][j * B + p]);
                 }
-                // flips inside the tile (shared memory)
-                for (int i = 0; i < tub; ++i) {
-                    const T g = gam_s[LS + i];
+                // flips inside the tile (shared memory). Unrolled at compile time and
+                // predicated on the tile's bit count so that every partner load of a
+                // unit is independent; idle slots read a masked, in-range address.
+                const int umask = nunits - 1;
 #pragma unroll
-                    for (int k = 0; k < UP; ++k) {
-                        if (!val[k]) continue;
-                        T pv[VU];
-                        ld_unit<T, B>(tile + (uu[k] ^ (1 << i)) * VU, pv);
+                for (int i = 0; i < kMaxTileUnitBits; ++i) {
+                    if (i < tub) {
+                        const T g = gam_s[LS + i];
 #pragma unroll
-                        for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[v], acc[k][v]);
+                        for (int k = 0; k < UP; ++k) {
+                            T pv[VU];
+                            ld_unit<T, B>(tile + ((uu[k] ^ (1 << i)) & umask) * VU, pv);
+#pragma unroll
+                            for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[v], acc[k][v]);
+                        }
                     }
                 }
                 // flips beyond the tile (global memory, L2-resident partner tiles)
-#pragma unroll 2
-                for (int i = R.tbits; i < R.N; ++i) {
-                    const T g = gam_s[i];
-                    T pv[UP][VU];
+                const int ngb = R.N - R.tbits;
+                int64_t sbase[UP];
+#pragma unroll
+                for (int k = 0; k < UP; ++k) sbase[k] = val[k] ? tile0 + static_cast<int64_t>(uu[k]) * SU : tile0;
+#pragma unroll
+                for (int j = 0; j < kMaxGlobalBitsUnrolled; ++j) {
+                    if (j < ngb) {
+                        const T g = gam_s[R.tbits + j];
+                        T pv[UP][VU];
+#pragma unroll
+                        for (int k = 0; k < UP; ++k)
+                            ld_unit_g<T, B, COHERENT>(xg + (sbase[k] ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B, pv[k]);
+#pragma unroll
+                        for (int k = 0; k < UP; ++k)
+#pragma unroll
+                            for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[k][v], acc[k][v]);
+                    }
+                }
+                for (int j = kMaxGlobalBitsUnrolled; j < ngb; ++j) {
+                    const T g = gam_s[R.tbits + j];
 #pragma unroll
                     for (int k = 0; k < UP; ++k) {
-                        const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
-                        if (val[k]) ld_unit_g<T, B, COHERENT>(xg + (s0 ^ (static_cast<int64_t>(1) << i)) * B, pv[k]);
+                        T pv[VU];
+                        ld_unit_g<T, B, COHERENT>(xg + (sbase[k] ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B, pv);
+#pragma unroll
+                        for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[v], acc[k][v]);
                     }
-#pragma unroll
-                    for (int k = 0; k < UP; ++k)
-#pragma unroll
-                        for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[k][v], acc[k][v]);
                 }
 #pragma unroll
                 for (int k = 0; k < UP; ++k) {
