@@ -198,7 +198,7 @@ def run_gpu(args, wl, rank, world):
     import paper_2011_02107_gb300 as P
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    prec = P.DACP_FP32 if wl["prec"] == "fp32" else P.DACP_FP64
+    prec = {"fp32": P.DACP_FP32, "df32": P.DACP_DF32}.get(wl["prec"], P.DACP_FP64)
     models, psis = make_inputs(wl, rank)
     stream = torch.cuda.Stream(device=dev)
     n_eigs = wl["n_eigs"]
@@ -251,7 +251,7 @@ def run_gpu(args, wl, rank, world):
         found += int(np.clip(np.asarray(nf), 0, None).sum())
         phase += d.timings()
         p = d.params()
-        esz = 4 if wl["prec"] == "fp32" else 8
+        esz = 4 if wl["prec"] == "fp32" else 8           # df32 pairs are 8 bytes
         bytes_evo += sum(3.0 * (int(p["kn"][r]) + 1) * (1 << models[r]["N"]) * wl["b"] * esz for r in range(R))
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -317,7 +317,7 @@ def run_gpu(args, wl, rank, world):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": wl["prec"] if wl["prec"] == "fp64" else "fp32+fp64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32 vectors + f64 moments", "df32": "f32-pair vectors + f64 moments"}[wl["prec"]],
         "data": "synthetic (seeded random couplings and Gaussian start vectors)",
         "config": {"workload": wl["desc"], "realizations_per_gpu": R, "N": wl["N"], "n_eigs": n_eigs,
                    "block_b": wl["b"], "precision": wl["prec"],
@@ -352,7 +352,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--params", default="mlp", choices=["mlp", "heuristic"],
                     help="parameter choice: the trained network when its weights exist, else the heuristic")
-    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"], help="override the workload's precision")
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "df32"],
+                    help="override the workload's precision (df32: double-float vectors on the float32 pipes)")
     ap.add_argument("--realizations", type=int, default=None, help="override the number of realizations per GPU")
     ap.add_argument("--n-eigs", type=int, default=None, help="override the central eigenvalues per realization")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)

@@ -48,7 +48,11 @@ typedef enum {
 
 typedef enum {
     DACP_FP64 = 0,             /* float64 vectors, float64 moments (plain DACP) */
-    DACP_FP32 = 1              /* float32 vectors, float64 moments and solve    */
+    DACP_FP32 = 1,             /* float32 vectors, float64 moments and solve    */
+    DACP_DF32 = 2              /* double-float vectors (pairs of float32, about
+                                  48 significant bits, float32 arithmetic with
+                                  error-free transformations), float64 moments
+                                  and solve                                     */
 } dacp_precision;
 
 /*
@@ -92,7 +96,7 @@ dacp_status dacp_set_params(dacp_handle hd, const double* emax, const double* a,
  *          the same vector; [-a, a] holds d = d_ratio * n_eigs levels;
  *   n:     b(2n+1) >= basis_ratio * d (Sec. II B: 2n+1 = 1.5 d);
  *   K:     ceil(c_order * E_max / a) (Sec. II A: c_order = 18). c_order <= 0
- *          picks the precision default: 18 for DACP_FP64, 6 for DACP_FP32
+ *          picks the precision default: 18 for DACP_FP64 and DACP_DF32, 6 for DACP_FP32
  *          (float32 moments resolve a dynamic range of about e^12).
  * Errors: DACP_ERR_ARG, DACP_ERR_CUDA.
  */
@@ -130,7 +134,7 @@ dacp_status dacp_basis_moments(dacp_handle hd);
  * nu_k = E_max (mu_{k+1} + mu_{|k-1|})/2 for H), solve H B = S B Lambda
  * (Eq. gep) after dropping eigenvalues of S below eps * lambda_max(S)
  * (eps <= 0 -> 1e-12 for DACP_FP64 as in Sec. II C, 1e-6 for DACP_FP32,
- * whose moments carry float32 round-off), and return up to n_eigs eigenvalues of
+ * whose moments carry float32 round-off, 1e-11 for DACP_DF32), and return up to n_eigs eigenvalues of
  * smallest |E| inside [-window, window] (window <= 0 -> a) in ascending order.
  *   eigs     n_real * n_eigs doubles; realization r at r * n_eigs.
  *   n_found  n_real ints: count written for r, or -dacp_status on failure.

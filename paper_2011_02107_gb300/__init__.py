@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libdacp.so")
 
 DACP_FP64 = 0
 DACP_FP32 = 1
+DACP_DF32 = 2
 
 _STATUS = {0: "DACP_OK", 1: "DACP_ERR_ARG", 2: "DACP_ERR_CUDA", 3: "DACP_ERR_NOMEM", 4: "DACP_ERR_NUMERIC",
            5: "DACP_ERR_TIMEOUT", 6: "DACP_ERR_STATE", 7: "DACP_ERR_NOT_CONVERGED", 8: "DACP_ERR_LIBRARY"}

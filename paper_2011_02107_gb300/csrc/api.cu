@@ -37,6 +37,9 @@ constexpr double kLaneBytes = 24e9;  // device memory budget of the lanes
 constexpr double kEpsFp32 = 1e-6;
 constexpr double kCOrderFp32 = 6.0;
 constexpr double kCOrderFp64 = 18.0;
+// Double-float vectors carry about 2^-44 relative round-off per operation:
+// the float64 filter constant holds, the cut-off sits a decade above 1e-12.
+constexpr double kEpsDf32 = 1e-11;
 
 struct Graph {
     cudaGraphExec_t exec = nullptr;
@@ -67,6 +70,7 @@ struct Lane {
 
 struct dacp_ctx {
     int R = 0, b = 1;
+    int prec = kPrecF64;                // vector precision (kPrecF64 / kPrecF32 / kPrecDF32)
     bool fp32 = false;
     size_t esz = 8;
     cudaStream_t st = nullptr;
@@ -296,17 +300,17 @@ dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
         CK(cudaMemsetAsync(c->bar_d + 1, 0, sizeof(unsigned), c->st));
         c->poison_barrier = false;
         int grid = 0;
-        CK(launch_persistent(c->fp32, c->b, filter ? 0 : 1, a, ni, orders, c->smem, c->st, &grid));
+        CK(launch_persistent(c->prec, c->b, filter ? 0 : 1, a, ni, orders, c->smem, c->st, &grid));
         c->launches += 1;
         return DACP_OK;
     }
     auto launch_order = [&]() -> cudaError_t {
         cudaError_t e;
         if (filter) {
-            if ((e = launch_step(c->fp32, c->b, kFilter1, a, 0, ni, c->smem, c->st)) != cudaSuccess) return e;
-            return launch_step(c->fp32, c->b, kFilter2, a, 0, ni, c->smem, c->st);
+            if ((e = launch_step(c->prec, c->b, kFilter1, a, 0, ni, c->smem, c->st)) != cudaSuccess) return e;
+            return launch_step(c->prec, c->b, kFilter2, a, 0, ni, c->smem, c->st);
         }
-        return launch_step(c->fp32, c->b, kEvolve, a, 0, ni, c->smem, c->st);
+        return launch_step(c->prec, c->b, kEvolve, a, 0, ni, c->smem, c->st);
     };
     Graph& g = filter ? c->gf : c->ge;
     if (!g.exec && orders >= kGraphOrders) {
@@ -370,7 +374,7 @@ size_t part_capacity(const dacp_ctx* c) {
 // Switch the handle to a new tile size: items, smem attribute, graphs.
 dacp_status retile(dacp_ctx* c, int tile_bytes) {
     tile_geometry(c, tile_bytes);
-    if (prepare_step(c->fp32, c->b, c->smem) != cudaSuccess || prepare_step(c->fp32, 1, c->smem) != cudaSuccess)
+    if (prepare_step(c->prec, c->b, c->smem) != cudaSuccess || prepare_step(c->prec, 1, c->smem) != cudaSuccess)
         return fail(c, DACP_ERR_CUDA, "shared-memory attribute for %d bytes", c->smem);
     dfree(c, c->items_d);
     c->items_d = nullptr;
@@ -500,7 +504,7 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
     *out = nullptr;
     if (n_real <= 0 || !n_spins || !J || !h || !gamma || !psi0) return DACP_ERR_ARG;
     if (!(block_b == 1 || block_b == 2 || block_b == 4)) return DACP_ERR_ARG;
-    if (precision != DACP_FP64 && precision != DACP_FP32) return DACP_ERR_ARG;
+    if (precision != DACP_FP64 && precision != DACP_FP32 && precision != DACP_DF32) return DACP_ERR_ARG;
     for (int r = 0; r < n_real; ++r)
         if (n_spins[r] < 1 || n_spins[r] > kMaxSpins) return DACP_ERR_ARG;
 
@@ -512,8 +516,9 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
     cudaGetDevice(&c->device);
     c->R = n_real;
     c->b = block_b;
-    c->fp32 = precision == DACP_FP32;
-    c->esz = c->fp32 ? 4 : 8;
+    c->prec = precision == DACP_FP32 ? kPrecF32 : (precision == DACP_DF32 ? kPrecDF32 : kPrecF64);
+    c->fp32 = c->prec == kPrecF32;
+    c->esz = c->fp32 ? 4 : 8;             // double-float pairs are 8 bytes like float64
     if (stream) {
         c->st = static_cast<cudaStream_t>(stream);
     } else {
@@ -611,7 +616,7 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         if ((s = dalloc_t(c, &c->g64_d, c->g_h.size())) != DACP_OK) return bail(s);
         double* tmp = c->g64_d;
         ok = ck(cudaMemcpyAsync(tmp, c->g_h.data(), c->g_h.size() * 8, cudaMemcpyHostToDevice, c->st)) &&
-             ck(launch_convert(c->fp32, tmp, c->gam_d, static_cast<int64_t>(c->g_h.size()), c->st));
+             ck(launch_convert(c->prec, tmp, c->gam_d, static_cast<int64_t>(c->g_h.size()), c->st));
         // start vectors: host float64 -> device, converted in place of psi0
         double* tmp2 = nullptr;
         const int64_t nv = c->Dtot * block_b;
@@ -624,13 +629,13 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         int64_t src_off = 0;
         for (int r = 0; ok && r < n_real; ++r) {
             const int64_t len = (static_cast<int64_t>(1) << c->N[r]) * block_b;
-            ok = ck(launch_convert(c->fp32, tmp2 + src_off,
+            ok = ck(launch_convert(c->prec, tmp2 + src_off,
                                    static_cast<char*>(c->psi0_d) + static_cast<size_t>(c->info[r].off) * block_b * c->esz,
                                    len, c->st));
             src_off += len;
         }
         c->launches += n_real - 1;
-        for (int r = 0; ok && r < n_real; ++r) ok = ck(launch_diag(c->fp32, c->info_d, r, c->N[r], c->J_d, c->h_d, c->diag_d, c->st));
+        for (int r = 0; ok && r < n_real; ++r) ok = ck(launch_diag(c->prec, c->info_d, r, c->N[r], c->J_d, c->h_d, c->diag_d, c->st));
         c->launches += 2 + n_real;
         std::vector<double> ac(8 * static_cast<size_t>(n_real), 0.0);
         for (int r = 0; r < n_real; ++r) ac[8 * r] = 1.0;
@@ -640,7 +645,7 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         if (!ok) return bail(fail(c, DACP_ERR_CUDA, "set-up kernels failed: %s", cudaGetErrorString(cudaGetLastError())));
     }
     // b-column stencil for the recurrences, 1-column stencil for the Lanczos / KPM pre-pass
-    if (prepare_step(c->fp32, block_b, c->smem) != cudaSuccess || prepare_step(c->fp32, 1, c->smem) != cudaSuccess)
+    if (prepare_step(c->prec, block_b, c->smem) != cudaSuccess || prepare_step(c->prec, 1, c->smem) != cudaSuccess)
         return bail(DACP_ERR_CUDA);
     for (auto& e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(DACP_ERR_CUDA);
@@ -716,9 +721,9 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
         TRY(dalloc_t(c, &knobs, static_cast<size_t>(R) * 3));
         if (!c->feats_d) TRY(dalloc_t(c, &c->feats_d, static_cast<size_t>(R) * kFeatures));
         // v = column 0 of psi0, normalised; kept in kA for the KPM run
-        CK(launch_extract_col(c->fp32, c->b, c->psi0_d, v2, c->Dtot, c->st));
+        CK(launch_extract_col(c->prec, c->b, c->psi0_d, v2, c->Dtot, c->st));
         c->launches += 3 + 4 * static_cast<int64_t>(steps) + 1 + kpm_moments / 2 + 2;
-        CK(launch_normalize(c->fp32, 1, c->items_d, c->info_d, ni, v2, v2, 0, c->part_d, c->real_done_d,
+        CK(launch_normalize(c->prec, 1, c->items_d, c->info_d, ni, v2, v2, 0, c->part_d, c->real_done_d,
                             c->norms_d, v1, kA, c->st));
         // Lanczos: w = H v - beta v_prev; alpha = <w, v>; w -= alpha v; beta = |w|
         std::vector<double> lc(8 * static_cast<size_t>(R), 0.0);
@@ -738,10 +743,10 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
             a.apply_row = j;
             a.mom = lmom;
             a.mom_rows_fixed = rows;
-            CK(launch_step(c->fp32, 1, kApply, a, 0, ni, c->smem, c->st));
-            CK(launch_lanczos_orth(c->fp32, c->items_d, c->info_d, ni, vc, w, lmom, rows, j, c->part_d,
+            CK(launch_step(c->prec, 1, kApply, a, 0, ni, c->smem, c->st));
+            CK(launch_lanczos_orth(c->prec, c->items_d, c->info_d, ni, vc, w, lmom, rows, j, c->part_d,
                                    c->real_done_d, beta2, steps, c->st));
-            CK(launch_lanczos_scale(c->fp32, c->items_d, c->info_d, ni, w, beta2, j, steps, c->apply_coef_d, R, c->st));
+            CK(launch_lanczos_scale(c->prec, c->items_d, c->info_d, ni, w, beta2, j, steps, c->apply_coef_d, R, c->st));
             void* t = vp;
             vp = vc;
             vc = w;
@@ -763,7 +768,7 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
         a.mom_rows_fixed = kpm_moments;
         a.nsteps_override = kpm_moments / 2;
         CK(cudaMemsetAsync(c->step_ctr_d, 0, sizeof(int), c->st));
-        for (int k = 0; k < kpm_moments / 2; ++k) CK(launch_step(c->fp32, 1, kEvolve, a, 0, ni, c->smem, c->st));
+        for (int k = 0; k < kpm_moments / 2; ++k) CK(launch_step(c->prec, 1, kEvolve, a, 0, ni, c->smem, c->st));
         CK(launch_features(R, c->info_d, c->J_d, c->h_d, c->g64_d, kp, kpm_moments, n_eigs, c->feats_d, c->st));
         if (net) {
             int64_t nl = 0;
@@ -844,7 +849,7 @@ dacp_status dacp_filter(dacp_handle c) {
     TRY(run_orders(c, true, maxK));
     // psi_E = w_K / |w_K| per column; w_K sits in A (K even) or B (K odd); also w_0 of the evolution
     c->launches += 2;
-    CK(launch_normalize(c->fp32, c->b, c->items_d, c->info_d, static_cast<int>(c->items.size()), c->A_d, c->B_d, 1,
+    CK(launch_normalize(c->prec, c->b, c->items_d, c->info_d, static_cast<int>(c->items.size()), c->A_d, c->B_d, 1,
                         c->part_d, c->real_done_d, c->norms_d, c->psiE_d, nullptr, c->st));
     CK(cudaEventRecord(c->ev[1], c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -883,7 +888,7 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
     TRY(check_handle(c));
     if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_central_eigs before dacp_basis_moments");
     if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
-    if (!(eps > 0.0)) eps = c->fp32 ? kEpsFp32 : 1e-12;
+    if (!(eps > 0.0)) eps = c->fp32 ? kEpsFp32 : (c->prec == kPrecDF32 ? kEpsDf32 : 1e-12);
     const int b = c->b;
     int Mmax = 0;
     int64_t rows_max = 0;
@@ -1026,7 +1031,7 @@ dacp_status dacp_get_filtered(dacp_handle c, int r, double* psi, int64_t cap) {
     auto run = [&]() -> dacp_status {
         TRY(dalloc_t(c, &tmp, static_cast<size_t>(n)));
         const char* src = static_cast<const char*>(c->psiE_d) + static_cast<size_t>(c->info[r].off) * c->b * c->esz;
-        CK(launch_to_double(c->fp32, src, tmp, n, c->st));
+        CK(launch_to_double(c->prec, src, tmp, n, c->st));
         c->launches += 1;
         CK(cudaMemcpyAsync(psi, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
@@ -1049,7 +1054,7 @@ dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
     a.x = static_cast<const char*>(x_dev) - shift;
     a.y1 = nullptr;
     a.out = static_cast<char*>(y_dev) - shift;
-    CK(launch_step(c->fp32, c->b, kApply, a, c->info[r].item_begin, c->info[r].item_count, c->smem, c->st));
+    CK(launch_step(c->prec, c->b, kApply, a, c->info[r].item_begin, c->info[r].item_count, c->smem, c->st));
     c->launches += 1;
     CK(cudaStreamSynchronize(c->st));
     return check_device_flag(c);
@@ -1067,7 +1072,7 @@ dacp_status dacp_autotune(dacp_handle c, int orders, int* tile_bytes_out) {
     if (orders < 4 || orders > 100000) return fail(c, DACP_ERR_ARG, "orders out of range");
     std::vector<int> ns = c->N;
     std::sort(ns.begin(), ns.end());
-    std::string key = std::to_string(c->b) + (c->fp32 ? "f" : "d");
+    std::string key = std::to_string(c->b) + "p" + std::to_string(c->prec);
     for (int v : ns) key += "," + std::to_string(v);
     int best = -1;
     {

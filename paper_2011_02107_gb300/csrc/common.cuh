@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df32.cuh"
+
 namespace dacp {
 
 constexpr int kThreads = 256;       // threads per CTA of the stencil kernels
@@ -31,6 +33,35 @@ struct Item {
 };
 
 enum StepMode { kApply = 0, kFilter1 = 1, kFilter2 = 2, kEvolve = 3 };
+
+// Vector precision: float64, float32, or double-float (float32 pairs).
+enum Precision { kPrecF64 = 0, kPrecF32 = 1, kPrecDF32 = 2 };
+
+// Run the body (the variadic argument) with T bound to the vector element type of `prec` (the body returns).
+#define DACP_FOR_PREC(prec, ...)                   \
+    switch (prec) {                                 \
+        case ::dacp::kPrecF32: {                    \
+            using T = float;                        \
+            __VA_ARGS__;                            \
+        }                                           \
+        case ::dacp::kPrecDF32: {                   \
+            using T = ::dacp::df32;                 \
+            __VA_ARGS__;                            \
+        }                                           \
+        default: {                                  \
+            using T = double;                       \
+            __VA_ARGS__;                            \
+        }                                           \
+    }
+
+// Run the body with BB bound to the block size b in {1, 2, 4} (the body returns).
+#define DACP_FOR_B(b, ...)                                  \
+    switch (b) {                                             \
+        case 1: { constexpr int BB = 1; __VA_ARGS__; }              \
+        case 2: { constexpr int BB = 2; __VA_ARGS__; }              \
+        case 4: { constexpr int BB = 4; __VA_ARGS__; }              \
+        default: return cudaErrorInvalidValue;               \
+    }
 
 // Arguments of one stencil launch. Vectors are [state][b] in precision T.
 struct StepArgs {

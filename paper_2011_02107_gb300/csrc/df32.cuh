@@ -1,0 +1,78 @@
+// Double-float numbers: a value is the unevaluated sum hi + lo of two float32,
+// with |lo| <= ulp(hi) / 2, carrying about 48 significant bits. Arithmetic is
+// built from error-free transformations (Knuth's TwoSum, Dekker's
+// Fast2Sum, and the FMA form of TwoProduct; see Muller et al., "Handbook of
+// Floating-Point Arithmetic", chs. 4-5), so it runs on the float32 pipes.
+// On GB300 the float64 pipes deliver 1/64 of the float32 rate, which makes
+// this the fast route to near-float64 accuracy for the recurrences.
+//
+// Every primitive uses the _rn intrinsics so that the compiler cannot fuse
+// or reassociate the steps the error terms depend on.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dacp {
+
+using ::fma;   // keep the float / double overloads visible next to the df32 one
+
+struct __align__(8) df32 {
+    float hi, lo;
+    df32() = default;
+    __host__ __device__ constexpr df32(float h, float l) : hi(h), lo(l) {}
+    // from float64: hi = rn(x), lo = rn(x - hi)
+    __host__ __device__ explicit df32(double x) : hi(static_cast<float>(x)), lo(static_cast<float>(x - static_cast<double>(static_cast<float>(x)))) {}
+    __host__ __device__ explicit df32(int x) : hi(static_cast<float>(x)), lo(0.f) {}
+    __host__ __device__ explicit operator double() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
+// s + e = a + b exactly (Knuth, no ordering needed)
+__device__ __forceinline__ df32 df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df32(s, e);
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker)
+__device__ __forceinline__ df32 df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return df32(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+// p + e = a * b exactly (FMA form)
+__device__ __forceinline__ df32 df_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return df32(p, __fmaf_rn(a, b, -p));
+}
+
+__device__ __forceinline__ df32 operator+(df32 a, df32 b) {
+    df32 s = df_two_sum(a.hi, b.hi);
+    const float t = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return df_fast_two_sum(s.hi, t);
+}
+
+__device__ __forceinline__ df32 operator-(df32 a) { return df32(-a.hi, -a.lo); }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + (-b); }
+
+__device__ __forceinline__ df32 operator*(df32 a, df32 b) {
+    df32 p = df_two_prod(a.hi, b.hi);
+    const float t = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return df_fast_two_sum(p.hi, t);
+}
+
+__device__ __forceinline__ df32& operator*=(df32& a, df32 b) {
+    a = a * b;
+    return a;
+}
+
+// a * b + c
+__device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) {
+    df32 p = df_two_prod(a.hi, b.hi);
+    const float cross = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    df32 s = df_two_sum(p.hi, c.hi);
+    const float t = __fadd_rn(s.lo, __fadd_rn(__fadd_rn(p.lo, cross), c.lo));
+    return df_fast_two_sum(s.hi, t);
+}
+
+}  // namespace dacp

@@ -87,7 +87,7 @@ extern "C" dacp_status dacp_moments_noalloc(int n_spins, const double* J, const 
         if (!g_na_ptr[dev]) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DACP_ERR_CUDA;
-            if (prepare_step(false, 1, kNaTileStates * static_cast<int>(sizeof(double))) != cudaSuccess)
+            if (prepare_step(kPrecF64, 1, kNaTileStates * static_cast<int>(sizeof(double))) != cudaSuccess)
                 return DACP_ERR_CUDA;
             g_na_ptr[dev] = static_cast<double*>(p);
         }
@@ -135,7 +135,7 @@ extern "C" dacp_status dacp_moments_noalloc(int n_spins, const double* J, const 
                 ok(cudaMemcpyAsync(base + kRegA, psi_dev, sizeof(double) * D, cudaMemcpyDeviceToDevice, st));
     if (!good) return DACP_ERR_CUDA;
     const RealInfo* info_d = reinterpret_cast<const RealInfo*>(base + kRegInfo);
-    if (launch_diag(false, info_d, 0, N, base + kRegJ, base + kRegH, base + kRegDiag, st) != cudaSuccess)
+    if (launch_diag(kPrecF64, info_d, 0, N, base + kRegJ, base + kRegH, base + kRegDiag, st) != cudaSuccess)
         return DACP_ERR_CUDA;
 
     StepArgs a;
@@ -158,7 +158,7 @@ extern "C" dacp_status dacp_moments_noalloc(int n_spins, const double* J, const 
     a.mom = mu_dev;                      // product rows P_0 .. P_{2 n_orders - 1}
     const int smem = (1 << R.tbits) * static_cast<int>(sizeof(double));
     for (int k = 0; k < n_orders; ++k)
-        if (launch_step(false, 1, kEvolve, a, 0, R.item_count, smem, st) != cudaSuccess) return DACP_ERR_CUDA;
+        if (launch_step(kPrecF64, 1, kEvolve, a, 0, R.item_count, smem, st) != cudaSuccess) return DACP_ERR_CUDA;
     const int n = 2 * n_orders;
     noalloc_moments_from_products<<<(n + 255) / 256, 256, 0, st>>>(mu_dev, n);
     if (cudaGetLastError() != cudaSuccess) return DACP_ERR_CUDA;

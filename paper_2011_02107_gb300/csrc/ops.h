@@ -9,19 +9,19 @@
 namespace dacp {
 
 // stencil.cu
-cudaError_t prepare_step(bool fp32, int b, int smem);
-cudaError_t launch_persistent(bool fp32, int b, int seq, const StepArgs& a, int n_items, int orders, int smem,
+cudaError_t prepare_step(int prec, int b, int smem);
+cudaError_t launch_persistent(int prec, int b, int seq, const StepArgs& a, int n_items, int orders, int smem,
                               cudaStream_t st, int* grid_out);
-cudaError_t launch_step(bool fp32, int b, int mode, const StepArgs& a, int item_base, int n_items, int smem,
+cudaError_t launch_step(int prec, int b, int mode, const StepArgs& a, int item_base, int n_items, int smem,
                         cudaStream_t st);
-cudaError_t launch_diag(bool fp32, const RealInfo* real, int r, int N, const double* J, const double* h,
+cudaError_t launch_diag(int prec, const RealInfo* real, int r, int N, const double* J, const double* h,
                         void* diag, cudaStream_t st);
-cudaError_t launch_convert(bool fp32, const double* src, void* dst, int64_t n, cudaStream_t st);
-cudaError_t launch_to_double(bool fp32, const void* src, double* dst, int64_t n, cudaStream_t st);
-cudaError_t launch_normalize(bool fp32, int b, const Item* items, const RealInfo* real, int n_items,
+cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_normalize(int prec, int b, const Item* items, const RealInfo* real, int n_items,
                              const void* A, const void* Bv, int by_parity, double* part, unsigned* real_done,
                              double* norms, void* dst, void* dst2, cudaStream_t st);
-cudaError_t launch_extract_col(bool fp32, int b, const void* src, void* dst, int64_t states, cudaStream_t st);
+cudaError_t launch_extract_col(int prec, int b, const void* src, void* dst, int64_t states, cudaStream_t st);
 
 // subspace.cu
 cudaError_t launch_orders(int L, double a_r, int* orders, cudaStream_t st);
@@ -35,10 +35,10 @@ cudaError_t launch_select(const double* lam, int m, int n_eigs, double w, double
                           cudaStream_t st);
 
 // params.cu
-cudaError_t launch_lanczos_orth(bool fp32, const Item* items, const RealInfo* real, int n_items, const void* v,
+cudaError_t launch_lanczos_orth(int prec, const Item* items, const RealInfo* real, int n_items, const void* v,
                                 void* w, const double* lmom, int rows, int j, double* part, unsigned* real_done,
                                 double* beta2, int steps, cudaStream_t st);
-cudaError_t launch_lanczos_scale(bool fp32, const Item* items, const RealInfo* real, int n_items, void* w,
+cudaError_t launch_lanczos_scale(int prec, const Item* items, const RealInfo* real, int n_items, void* w,
                                  const double* beta2, int j, int steps, double* coef, int R, cudaStream_t st);
 cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps,
                                  const double* pnorm, double safety, double* emax, cudaStream_t st);

@@ -189,27 +189,30 @@ __global__ void kpm_window_kernel(int R, const RealInfo* __restrict__ real, cons
     }
 }
 
-cudaError_t launch_lanczos_orth(bool fp32, const Item* items, const RealInfo* real, int n_items, const void* v,
+cudaError_t launch_lanczos_orth(int prec, const Item* items, const RealInfo* real, int n_items, const void* v,
                                 void* w, const double* lmom, int rows, int j, double* part, unsigned* real_done,
                                 double* beta2, int steps, cudaStream_t st) {
-    if (fp32)
-        lanczos_orth_kernel<float><<<n_items, kThreads, 0, st>>>(items, real, static_cast<const float*>(v),
-                                                                  static_cast<float*>(w), lmom, rows, j, part,
-                                                                  real_done, beta2, steps);
-    else
-        lanczos_orth_kernel<double><<<n_items, kThreads, 0, st>>>(items, real, static_cast<const double*>(v),
-                                                                   static_cast<double*>(w), lmom, rows, j, part,
-                                                                   real_done, beta2, steps);
-    return cudaGetLastError();
+    DACP_FOR_PREC(prec, lanczos_orth_kernel<T><<<n_items, kThreads, 0, st>>>(items, real, static_cast<const T*>(v),
+                                                                             static_cast<T*>(w), lmom, rows, j, part,
+                                                                             real_done, beta2, steps);
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_lanczos_scale(bool fp32, const Item* items, const RealInfo* real, int n_items, void* w,
+cudaError_t launch_lanczos_scale(int prec, const Item* items, const RealInfo* real, int n_items, void* w,
                                  const double* beta2, int j, int steps, double* coef, int R, cudaStream_t st) {
-    if (fp32)
-        lanczos_scale_kernel<float><<<n_items, kThreads, 0, st>>>(items, real, static_cast<float*>(w), beta2, j, steps);
-    else
-        lanczos_scale_kernel<double><<<n_items, kThreads, 0, st>>>(items, real, static_cast<double*>(w), beta2, j, steps);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    switch (prec) {
+        case kPrecF32:
+            lanczos_scale_kernel<float><<<n_items, kThreads, 0, st>>>(items, real, static_cast<float*>(w), beta2, j, steps);
+            break;
+        case kPrecDF32:
+            lanczos_scale_kernel<df32><<<n_items, kThreads, 0, st>>>(items, real, static_cast<df32*>(w), beta2, j, steps);
+            break;
+        default:
+            lanczos_scale_kernel<double><<<n_items, kThreads, 0, st>>>(items, real, static_cast<double*>(w), beta2, j, steps);
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     lanczos_coef_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, beta2, j, steps, coef);
     return cudaGetLastError();

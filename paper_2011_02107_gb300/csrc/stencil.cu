@@ -33,6 +33,23 @@ namespace dacp {
 
 template <typename T> struct MomAcc { using type = double; };
 template <> struct MomAcc<float> { using type = float; };   // short per-thread runs, then float64
+template <> struct MomAcc<df32> { using type = df32; };     // double-float per thread, then float64
+
+// L2-coherent scalar load, and read-only scalar load.
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ df32 ld_cg<df32>(const df32* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return df32(v.x, v.y);
+}
+template <typename T>
+__device__ __forceinline__ T ld_ro(const T* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ df32 ld_ro<df32>(const df32* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return df32(v.x, v.y);
+}
 
 template <typename T, int B>
 __device__ __forceinline__ void load_vals(const T* __restrict__ p, T (&v)[B]) {
@@ -258,7 +275,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                         if (use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
                         if (use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
 #pragma unroll
-                        for (int j = 0; j < SU; ++j) dv[k][j] = __ldg(dg + s0 + j);
+                        for (int j = 0; j < SU; ++j) dv[k][j] = ld_ro(dg + s0 + j);
                     }
                 }
 #pragma unroll
@@ -354,7 +371,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
             }
         } else {
             // ---- scalar path for vectors smaller than one unit (N = 1) ----------
-            for (int i = tid; i < tstates * B; i += kThreads) tile[i] = COHERENT ? __ldcg(xg + tile0 * B + i) : xg[tile0 * B + i];
+            for (int i = tid; i < tstates * B; i += kThreads) tile[i] = COHERENT ? ld_cg(xg + tile0 * B + i) : xg[tile0 * B + i];
             __syncthreads();
             for (int sl = tid; sl < tstates; sl += kThreads) {
                 const int64_t s = tile0 + sl;
@@ -373,8 +390,8 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                 for (int p = 0; p < B; ++p) {
                     T t = ch * acc[p];
-                    if (use1) t = fma(c1, COHERENT ? __ldcg(y1 + gbase + s * B + p) : y1[gbase + s * B + p], t);
-                    if (use2) t = fma(c2, COHERENT ? __ldcg(y2 + gbase + s * B + p) : y2[gbase + s * B + p], t);
+                    if (use1) t = fma(c1, COHERENT ? ld_cg(y1 + gbase + s * B + p) : y1[gbase + s * B + p], t);
+                    if (use2) t = fma(c2, COHERENT ? ld_cg(y2 + gbase + s * B + p) : y2[gbase + s * B + p], t);
                     o[p] = t;
                 }
 #pragma unroll
@@ -521,16 +538,8 @@ static cudaError_t prepare_tb(int smem) {
 
 // Allow the dynamic shared-memory tile for every mode of (precision, b);
 // called once per handle, outside any stream capture.
-cudaError_t prepare_step(bool fp32, int b, int smem) {
-    if (fp32) {
-        if (b == 1) return prepare_tb<float, 1>(smem);
-        if (b == 2) return prepare_tb<float, 2>(smem);
-        if (b == 4) return prepare_tb<float, 4>(smem);
-    } else {
-        if (b == 1) return prepare_tb<double, 1>(smem);
-        if (b == 2) return prepare_tb<double, 2>(smem);
-        if (b == 4) return prepare_tb<double, 4>(smem);
-    }
+cudaError_t prepare_step(int prec, int b, int smem) {
+    DACP_FOR_PREC(prec, DACP_FOR_B(b, return prepare_tb<T, BB>(smem)));
     return cudaErrorInvalidValue;
 }
 
@@ -579,28 +588,18 @@ static cudaError_t launch_persistent_tb(const StepArgs& a, int n_items, int orde
 }
 
 // Every filter (seq 0) or evolution (seq 1) order in one cooperative launch.
-cudaError_t launch_persistent(bool fp32, int b, int seq, const StepArgs& a, int n_items, int orders, int smem,
+cudaError_t launch_persistent(int prec, int b, int seq, const StepArgs& a, int n_items, int orders, int smem,
                               cudaStream_t st, int* grid_out) {
-#define DACP_LP(T, BB) \
-    return seq == 0 ? launch_persistent_tb<T, BB, 0>(a, n_items, orders, smem, st, grid_out) \
-                    : launch_persistent_tb<T, BB, 1>(a, n_items, orders, smem, st, grid_out)
-    if (fp32) {
-        if (b == 1) DACP_LP(float, 1);
-        if (b == 2) DACP_LP(float, 2);
-        if (b == 4) DACP_LP(float, 4);
-    } else {
-        if (b == 1) DACP_LP(double, 1);
-        if (b == 2) DACP_LP(double, 2);
-        if (b == 4) DACP_LP(double, 4);
-    }
-#undef DACP_LP
+    DACP_FOR_PREC(prec, DACP_FOR_B(b, return seq == 0
+                                                   ? launch_persistent_tb<T, BB, 0>(a, n_items, orders, smem, st, grid_out)
+                                                   : launch_persistent_tb<T, BB, 1>(a, n_items, orders, smem, st, grid_out)));
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(bool fp32, int b, int mode, const StepArgs& a, int item_base, int n_items,
+cudaError_t launch_step(int prec, int b, int mode, const StepArgs& a, int item_base, int n_items,
                         int smem, cudaStream_t st) {
-    return fp32 ? launch_b<float>(b, mode, a, item_base, n_items, smem, st)
-                : launch_b<double>(b, mode, a, item_base, n_items, smem, st);
+    DACP_FOR_PREC(prec, return launch_b<T>(b, mode, a, item_base, n_items, smem, st));
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -731,37 +730,37 @@ __global__ void __launch_bounds__(kThreads) normalize_kernel(const Item* __restr
     }
 }
 
-cudaError_t launch_diag(bool fp32, const RealInfo* real, int r, int N, const double* J, const double* h,
+cudaError_t launch_diag(int prec, const RealInfo* real, int r, int N, const double* J, const double* h,
                         void* diag, cudaStream_t st) {
     const int64_t D = static_cast<int64_t>(1) << N;
     const int grid = static_cast<int>((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096);
-    if (fp32) diag_kernel<float><<<grid, 256, 0, st>>>(real, r, J, h, static_cast<float*>(diag));
-    else diag_kernel<double><<<grid, 256, 0, st>>>(real, r, J, h, static_cast<double*>(diag));
-    return cudaGetLastError();
+    DACP_FOR_PREC(prec, diag_kernel<T><<<grid, 256, 0, st>>>(real, r, J, h, static_cast<T*>(diag));
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_convert(bool fp32, const double* src, void* dst, int64_t n, cudaStream_t st) {
+cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t st) {
     const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
     if (n == 0) return cudaSuccess;
-    if (fp32) convert_kernel<float><<<grid, 256, 0, st>>>(src, static_cast<float*>(dst), n);
-    else convert_kernel<double><<<grid, 256, 0, st>>>(src, static_cast<double*>(dst), n);
-    return cudaGetLastError();
+    DACP_FOR_PREC(prec, convert_kernel<T><<<grid, 256, 0, st>>>(src, static_cast<T*>(dst), n);
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
 }
 
 // dst[s] = src[s][0]: column 0 of a [state][b] vector.
-cudaError_t launch_extract_col(bool fp32, int b, const void* src, void* dst, int64_t states, cudaStream_t st) {
+cudaError_t launch_extract_col(int prec, int b, const void* src, void* dst, int64_t states, cudaStream_t st) {
     const int grid = static_cast<int>((states + 255) / 256 < 8192 ? (states + 255) / 256 : 8192);
-    if (fp32) extract_col_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(src), static_cast<float*>(dst), b, states);
-    else extract_col_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(src), static_cast<double*>(dst), b, states);
-    return cudaGetLastError();
+    DACP_FOR_PREC(prec, extract_col_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), b, states);
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_to_double(bool fp32, const void* src, double* dst, int64_t n, cudaStream_t st) {
+cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, cudaStream_t st) {
     const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
     if (n == 0) return cudaSuccess;
-    if (fp32) to_double_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(src), dst, n);
-    else to_double_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double*>(src), dst, n);
-    return cudaGetLastError();
+    DACP_FOR_PREC(prec, to_double_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(src), dst, n);
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
 }
 
 template <typename T, int B>
@@ -779,20 +778,11 @@ static cudaError_t norm_and_scale(const Item* items, const RealInfo* real, int n
     return cudaGetLastError();
 }
 
-cudaError_t launch_normalize(bool fp32, int b, const Item* items, const RealInfo* real, int n_items,
+cudaError_t launch_normalize(int prec, int b, const Item* items, const RealInfo* real, int n_items,
                              const void* A, const void* Bv, int by_parity, double* part,
                              unsigned* real_done, double* norms, void* dst, void* dst2, cudaStream_t st) {
-#define DACP_NS(T, BB) return norm_and_scale<T, BB>(items, real, n_items, A, Bv, by_parity, part, real_done, norms, dst, dst2, st)
-    if (fp32) {
-        if (b == 1) DACP_NS(float, 1);
-        if (b == 2) DACP_NS(float, 2);
-        if (b == 4) DACP_NS(float, 4);
-    } else {
-        if (b == 1) DACP_NS(double, 1);
-        if (b == 2) DACP_NS(double, 2);
-        if (b == 4) DACP_NS(double, 4);
-    }
-#undef DACP_NS
+    DACP_FOR_PREC(prec, DACP_FOR_B(b, return norm_and_scale<T, BB>(items, real, n_items, A, Bv, by_parity, part,
+                                                                   real_done, norms, dst, dst2, st)));
     return cudaErrorInvalidValue;
 }
 

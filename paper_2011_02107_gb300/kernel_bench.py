@@ -32,12 +32,12 @@ def main():
     ap.add_argument("--N", type=int, default=14)
     ap.add_argument("--R", type=int, default=256)
     ap.add_argument("--b", type=int, default=4)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "df32"])
     ap.add_argument("--orders", type=int, default=200)
     ap.add_argument("--mode", type=int, default=-1)
     ap.add_argument("--tile", type=int, default=0)
     args = ap.parse_args()
-    prec = P.DACP_FP32 if args.precision == "fp32" else P.DACP_FP64
+    prec = {"fp32": P.DACP_FP32, "df32": P.DACP_DF32}.get(args.precision, P.DACP_FP64)
     esz = 4 if prec == P.DACP_FP32 else 8
     models = [W.spin_glass_shard(args.N, seed=r) for r in range(args.R)]
     psis = [W.start_vectors(args.N, args.b, seed=0, r=r) for r in range(args.R)]
