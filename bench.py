@@ -219,8 +219,10 @@ def run_gpu(args, wl, rank, world):
     mlp = None
     if args.params == "mlp":
         from paper_2011_02107_gb300 import train_mlp
-        if os.path.exists(train_mlp.DEFAULT_PATH) and wl["prec"] == "fp32":
-            mlp = train_mlp.load(stream=stream.cuda_stream)
+        if os.path.exists(train_mlp.DEFAULT_PATH):
+            z = np.load(train_mlp.DEFAULT_PATH)
+            if str(z["precision"]) == wl["prec"]:          # knobs are learned per vector precision
+                mlp = train_mlp.load(stream=stream.cuda_stream)
 
     # ---- value: inputs resident on the device, K whole-path steps
     d = P.Dacp(models, psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)

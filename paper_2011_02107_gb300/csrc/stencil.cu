@@ -176,7 +176,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int /*
 }
 
 constexpr int kWaitLimit = 0;         // (time-based: kWaitNs)
-constexpr int kUnitsPerPass = 2;      // units per thread in flight
+// Units per thread in flight: two for float32; one for the 8-byte types,
+// whose units and accumulators already use twice the registers.
+template <typename T> struct UnitsPerPass { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
+// Minimum resident CTAs per SM the compiler must allow: three for float32
+// (80 registers, no spills), two for the 8-byte types (128 registers; three
+// would spill their double-float / float64 accumulators).
+template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 2; };
 constexpr int kMaxTileUnitBits = 14;   // unit bits of the largest tile (128 KB of float32 b = 1)
 constexpr int kMaxGlobalBitsUnrolled = 10;
 
@@ -186,7 +192,8 @@ constexpr int kMaxGlobalBitsUnrolled = 10;
 template <typename T, int B, int MODE, bool COHERENT>
 __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, const int step) {
     using U = Unit<T, B>;
-    constexpr int VU = U::kVals, SU = U::kStates, LS = U::kLog, UP = kUnitsPerPass;
+    constexpr int VU = U::kVals, SU = U::kStates, LS = U::kLog, UP = UnitsPerPass<T>::value;
+    constexpr bool kEarlyY = sizeof(T) == 4;     // prefetch y1 / y2 before the flips (float32 only)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
     __shared__ T gam_s[kMaxSpins];
@@ -272,8 +279,8 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
                     if (val[k]) {
                         ld_unit<T, B>(tile + uu[k] * VU, xv[k]);
-                        if (use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
-                        if (use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
+                        if (kEarlyY && use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
+                        if (kEarlyY && use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
 #pragma unroll
                         for (int j = 0; j < SU; ++j) dv[k][j] = ld_ro(dg + s0 + j);
                     }
@@ -345,6 +352,11 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                 for (int k = 0; k < UP; ++k) {
                     if (!val[k]) continue;
+                    if (!kEarlyY) {
+                        const int64_t sy = tile0 + static_cast<int64_t>(uu[k]) * SU;
+                        if (use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + sy * B, yv[k]);
+                        if (use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + sy * B, zv[k]);
+                    }
                     T o[VU];
 #pragma unroll
                     for (int v = 0; v < VU; ++v) {
@@ -363,7 +375,8 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                                 for (int q = 0; q < B; ++q) {
                                     const Acc xq = static_cast<Acc>(xv[k][j * B + q]);
-                                    xx[p][q] = fma(static_cast<Acc>(xv[k][j * B + p]), xq, xx[p][q]);
+                                    // <x_p, x_q> is symmetric: only q >= p is accumulated
+                                    if (q >= p) xx[p][q] = fma(static_cast<Acc>(xv[k][j * B + p]), xq, xx[p][q]);
                                     ox[p][q] = fma(static_cast<Acc>(o[j * B + p]), xq, ox[p][q]);
                                 }
                     }
@@ -401,7 +414,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     for (int p = 0; p < B; ++p)
 #pragma unroll
                         for (int q = 0; q < B; ++q) {
-                            xx[p][q] = fma(static_cast<Acc>(xv[p]), static_cast<Acc>(xv[q]), xx[p][q]);
+                            if (q >= p) xx[p][q] = fma(static_cast<Acc>(xv[p]), static_cast<Acc>(xv[q]), xx[p][q]);
                             ox[p][q] = fma(static_cast<Acc>(o[p]), static_cast<Acc>(xv[q]), ox[p][q]);
                         }
                 }
@@ -416,7 +429,7 @@ reduce:
         for (int p = 0; p < B; ++p)
 #pragma unroll
             for (int q = 0; q < B; ++q) {
-                const double v1 = warp_sum(static_cast<double>(xx[p][q]));
+                const double v1 = warp_sum(static_cast<double>(xx[p < q ? p : q][p < q ? q : p]));
                 const double v2 = warp_sum(static_cast<double>(ox[p][q]));
                 if (lane == 0) { red_s[warp][p * B + q] = v1; red_s[warp][B * B + p * B + q] = v2; }
             }
@@ -453,7 +466,7 @@ reduce:
 }
 
 template <typename T, int B, int MODE>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs a, int item_base) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) step_kernel(const StepArgs a, int item_base) {
     int step = 0;
     if (MODE != kApply) step = *a.step_ctr;
     tile_step<T, B, MODE, false>(a, item_base + blockIdx.x, step);
@@ -507,7 +520,8 @@ __device__ __forceinline__ bool grid_sync(const StepArgs& a) {
 // All orders of the filter (SEQ = 0: two passes per order) or the evolution
 // (SEQ = 1) in one cooperative launch; CTAs take tiles round-robin.
 template <typename T, int B, int SEQ>
-__global__ void __launch_bounds__(kThreads) persistent_kernel(const StepArgs a, int n_items, int orders) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) persistent_kernel(const StepArgs a, int n_items,
+                                                                                 int orders) {
     for (int k = 0; k < orders; ++k) {
         if (SEQ == 0) {
             for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step<T, B, kFilter1, true>(a, item, k);
