@@ -191,6 +191,16 @@ dacp_status dacp_set_launch(dacp_handle hd, int mode, int tile_bytes);
 dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);
 
 /*
+ * dacp_set_solver -- how dacp_central_eigs runs the dense float64 algebra:
+ * 1 (default) = when every realization has the same basis size, one batched
+ * cuSOLVER syev call per group for S and one for H~ with strided-batched
+ * dgemm between them; 0 = concurrent lanes (own stream, handles and host
+ * thread each) solving the realizations one by one. Uneven sizes always use
+ * lanes.
+ */
+dacp_status dacp_set_solver(dacp_handle hd, int mode);
+
+/*
  * dacp_test_poison_barrier -- test hook for the bounded waits: the next
  * persistent launch starts with a grid-barrier arrival count that can never
  * complete, so every CTA's wait gives up after about one second and the call

@@ -35,7 +35,7 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
-           "dacp_test_poison_barrier", "dacp_moments_noalloc"]
+           "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -84,6 +84,7 @@ def _load():
         "dacp_autotune": [P, I, ctypes.POINTER(I)],
         "dacp_set_launch": [P, I, I],
         "dacp_test_poison_barrier": [P],
+        "dacp_set_solver": [P, I],
         "dacp_moments_noalloc": [I, P, P, P, D, P, I, P, P],
         "dacp_get_launch": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
     }
@@ -317,6 +318,10 @@ def dacp_moments_noalloc(model, emax, psi_dev_ptr, n_orders, mu_dev_ptr, stream=
         raise DacpError(st, "dacp_moments_noalloc")
 
 
+def dacp_set_solver(hd, mode):
+    _check(hd, _lib.dacp_set_solver(hd, int(mode)))
+
+
 def dacp_test_poison_barrier(hd):
     _check(hd, _lib.dacp_test_poison_barrier(hd))
 
@@ -366,6 +371,9 @@ class Dacp:
 
     def autotune(self, orders=64):
         return dacp_autotune(self.handle, orders)
+
+    def set_solver(self, mode):
+        dacp_set_solver(self.handle, mode)
 
     def set_launch(self, mode, tile_bytes):
         dacp_set_launch(self.handle, mode, tile_bytes)

@@ -100,6 +100,7 @@ struct dacp_ctx {
     unsigned* bar_d = nullptr;          // grid barrier (count, generation) of the persistent launch
     int launch_mode = 0;                // 0: per-order launches replayed from a CUDA graph, 1: persistent
     bool poison_barrier = false;        // test hook: the next persistent launch's barrier never opens
+    bool batched_solve = true;          // equal basis sizes: batched cuSOLVER instead of lanes
     double* mom_d = nullptr;
     int64_t mom_cap = 0;
 
@@ -883,6 +884,142 @@ dacp_status dacp_basis_moments(dacp_handle c) {
     return DACP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+constexpr double kBatchBytes = 24e9;   // device memory budget of one batched subspace group
+constexpr int kMaxBatch = 64;
+
+// Subspace solve for a handle whose realizations share the basis size M:
+// groups of G realizations go through one batched syev of S (with vectors),
+// the cut-off, two strided-batched dgemm for H~ = U^T H U (U padded to the
+// group's largest rank with zero columns), one batched syev of H~ (values;
+// the padded directions sit on a decoupled diagonal at 3 E_max, outside every
+// window) and the central selection.
+dacp_status central_eigs_batched(dacp_ctx* c, int n_eigs, double window, double eps, double* eigs, int* n_found,
+                                 int* rank, int M, int64_t rows_max) {
+    const int b = c->b, R = c->R, L = M / b;
+    const double per = 4.0 * 8.0 * M * static_cast<double>(M) + 2.0 * 8.0 * rows_max * b * b;
+    const int G = std::max(1, std::min(std::min(R, kMaxBatch), static_cast<int>(kBatchBytes / per)));
+    const int64_t MM = static_cast<int64_t>(M) * M;
+    const int64_t mstride = rows_max * b * b;
+    double *S = nullptr, *H = nullptr, *W = nullptr, *Ht = nullptr, *lam = nullptr, *lamt = nullptr, *mus = nullptr,
+           *nus = nullptr, *sel = nullptr, *big = nullptr;
+    int *orders = nullptr, *mi = nullptr, *bad = nullptr, *info = nullptr, *nf = nullptr;
+    void* work = nullptr;
+    std::vector<char> work_h;
+    auto cleanup = [&]() {
+        for (void* p : {static_cast<void*>(S), static_cast<void*>(H), static_cast<void*>(W), static_cast<void*>(Ht),
+                        static_cast<void*>(lam), static_cast<void*>(lamt), static_cast<void*>(mus),
+                        static_cast<void*>(nus), static_cast<void*>(sel), static_cast<void*>(big),
+                        static_cast<void*>(orders), static_cast<void*>(mi), static_cast<void*>(bad),
+                        static_cast<void*>(info), static_cast<void*>(nf), work})
+            dfree(c, p);
+    };
+    auto run = [&]() -> dacp_status {
+        TRY(dalloc_t(c, &S, static_cast<size_t>(G) * MM));
+        TRY(dalloc_t(c, &H, static_cast<size_t>(G) * MM));
+        TRY(dalloc_t(c, &W, static_cast<size_t>(G) * MM));
+        TRY(dalloc_t(c, &Ht, static_cast<size_t>(G) * MM));
+        TRY(dalloc_t(c, &lam, static_cast<size_t>(G) * M));
+        TRY(dalloc_t(c, &lamt, static_cast<size_t>(G) * M));
+        TRY(dalloc_t(c, &mus, static_cast<size_t>(G) * mstride));
+        TRY(dalloc_t(c, &nus, static_cast<size_t>(G) * mstride));
+        TRY(dalloc_t(c, &sel, static_cast<size_t>(G) * n_eigs));
+        TRY(dalloc_t(c, &big, G));
+        TRY(dalloc_t(c, &orders, static_cast<size_t>(G) * L));
+        TRY(dalloc_t(c, &mi, G));
+        TRY(dalloc_t(c, &bad, G));
+        TRY(dalloc_t(c, &info, G));
+        TRY(dalloc_t(c, &nf, G));
+        size_t d1 = 0, h1 = 0, d2 = 0, h2 = 0;
+        CKS(cusolverDnXsyevBatched_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M,
+                                              CUDA_R_64F, S, M, CUDA_R_64F, lam, CUDA_R_64F, &d1, &h1, G));
+        CKS(cusolverDnXsyevBatched_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, M,
+                                              CUDA_R_64F, Ht, M, CUDA_R_64F, lamt, CUDA_R_64F, &d2, &h2, G));
+        const size_t dbytes = std::max(d1, d2), hbytes = std::max(h1, h2);
+        TRY(dalloc(c, &work, dbytes));
+        work_h.resize(std::max<size_t>(hbytes, 1));
+        std::vector<int> hm(G), hbad(G), hinfo(G), hnf(G);
+        std::vector<double> hbig(G), hsel(static_cast<size_t>(G) * n_eigs);
+        const double one = 1.0, zero = 0.0;
+        for (int r0 = 0; r0 < R; r0 += G) {
+            const int g = std::min(G, R - r0);
+            CK(cudaMemsetAsync(bad, 0, sizeof(int) * g, c->st));
+            for (int i = 0; i < g; ++i) {
+                const int r = r0 + i;
+                const int rows = 2 * c->kn[r] + 2;
+                CK(launch_orders(L, c->a[r] / c->emax[r], orders + static_cast<int64_t>(i) * L, c->st));
+                CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], mus + i * mstride,
+                                  nus + i * mstride, bad + i, c->st));
+                CK(launch_assemble(L, b, orders + static_cast<int64_t>(i) * L, mus + i * mstride, nus + i * mstride,
+                                   S + i * MM, H + i * MM, c->st));
+            }
+            CKS(cusolverDnXsyevBatched(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
+                                       S, M, CUDA_R_64F, lam, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, info,
+                                       g));
+            for (int i = 0; i < g; ++i) CK(launch_cutoff(lam + static_cast<int64_t>(i) * M, M, eps, 0, S + i * MM, mi + i, c->st));
+            c->launches += 4 * g;
+            CK(cudaMemcpyAsync(hm.data(), mi, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(hbad.data(), bad, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            int m_max = 0;
+            for (int i = 0; i < g; ++i)
+                if (!hbad[i] && hinfo[i] == 0) m_max = std::max(m_max, hm[i]);
+            if (m_max < 1) {
+                for (int i = 0; i < g; ++i) n_found[r0 + i] = hbad[i] ? -DACP_ERR_NUMERIC : -DACP_ERR_NOT_CONVERGED;
+                continue;
+            }
+            for (int i = 0; i < g; ++i) {
+                if (rank) rank[r0 + i] = hm[i];
+                if (hbad[i] || hinfo[i] != 0) hm[i] = m_max;     // excluded below; keep the padding a no-op
+                hbig[i] = 3.0 * c->emax[r0 + i];
+            }
+            CK(cudaMemcpyAsync(mi, hm.data(), sizeof(int) * g, cudaMemcpyHostToDevice, c->st));
+            CK(cudaMemcpyAsync(big, hbig.data(), sizeof(double) * g, cudaMemcpyHostToDevice, c->st));
+            CK(launch_pad_columns(S, M, MM, mi, m_max, g, c->st));
+            const double* U = S + static_cast<int64_t>(M - m_max) * M;
+            CKB(cublasDgemmStridedBatched(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m_max, M, &one, H, M, MM, U, M, MM,
+                                          &zero, W, M, static_cast<int64_t>(M) * m_max, g));
+            CKB(cublasDgemmStridedBatched(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, m_max, m_max, M, &one, U, M, MM, W, M,
+                                          static_cast<int64_t>(M) * m_max, &zero, Ht, m_max,
+                                          static_cast<int64_t>(m_max) * m_max, g));
+            CK(launch_pad_diagonal(Ht, m_max, static_cast<int64_t>(m_max) * m_max, mi, big, g, c->st));
+            CKS(cusolverDnXsyevBatched(c->sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m_max,
+                                       CUDA_R_64F, Ht, m_max, CUDA_R_64F, lamt, CUDA_R_64F, work, dbytes,
+                                       work_h.data(), hbytes, info, g));
+            for (int i = 0; i < g; ++i) {
+                const double w = window > 0.0 ? window : c->a[r0 + i];
+                CK(launch_select(lamt + static_cast<int64_t>(i) * m_max, m_max, n_eigs, w, sel + static_cast<int64_t>(i) * n_eigs,
+                                 nf + i, c->st));
+            }
+            c->launches += 2 + g;
+            CK(cudaMemcpyAsync(hsel.data(), sel, sizeof(double) * g * n_eigs, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(hnf.data(), nf, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            for (int i = 0; i < g; ++i) {
+                const int r = r0 + i;
+                if (hbad[i]) { n_found[r] = -DACP_ERR_NUMERIC; continue; }
+                if (hinfo[i] != 0) { n_found[r] = -DACP_ERR_NOT_CONVERGED; continue; }
+                memcpy(eigs + static_cast<size_t>(r) * n_eigs, hsel.data() + static_cast<size_t>(i) * n_eigs,
+                       sizeof(double) * hnf[i]);
+                n_found[r] = hnf[i];
+            }
+        }
+        return DACP_OK;
+    };
+    dacp_status st = run();
+    cleanup();
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
 dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double eps, double* eigs, int* n_found,
                               int* rank) {
     TRY(check_handle(c));
@@ -895,6 +1032,19 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
     for (int r = 0; r < c->R; ++r) {
         Mmax = std::max(Mmax, b * (2 * c->n[r] + 1));
         rows_max = std::max<int64_t>(rows_max, 2 * static_cast<int64_t>(c->kn[r]) + 2);
+    }
+    bool uniform = c->R >= 2 && c->batched_solve;
+    for (int r = 0; r < c->R && uniform; ++r) uniform = b * (2 * c->n[r] + 1) == Mmax;
+    if (uniform) {
+        // one batched cuSOLVER call per group of equal-size problems
+        CK(cudaEventRecord(c->ev[4], c->st));
+        TRY(central_eigs_batched(c, n_eigs, window, eps, eigs, n_found, rank, Mmax, rows_max));
+        CK(cudaEventRecord(c->ev[5], c->st));
+        CK(cudaStreamSynchronize(c->st));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
+        c->t_ms[2] = ms;
+        return DACP_OK;
     }
     TRY(ensure_lanes(c, Mmax, rows_max, n_eigs));
     const int nl = static_cast<int>(c->lanes.size());
@@ -1121,6 +1271,13 @@ dacp_status dacp_set_launch(dacp_handle c, int mode, int tile_bytes) {
     c->launch_mode = mode;
     TRY(retile(c, tile_bytes));
     if (c->state > 1) c->state = 1;
+    return DACP_OK;
+}
+
+dacp_status dacp_set_solver(dacp_handle c, int mode) {
+    TRY(check_handle(c));
+    if (mode != 0 && mode != 1) return fail(c, DACP_ERR_ARG, "solver mode must be 0 or 1");
+    c->batched_solve = mode == 1;
     return DACP_OK;
 }
 

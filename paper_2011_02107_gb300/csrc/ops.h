@@ -33,6 +33,9 @@ cudaError_t launch_cutoff(const double* lam, int M, double eps, int absolute, do
                           cudaStream_t st);
 cudaError_t launch_select(const double* lam, int m, int n_eigs, double w, double* out, int* n_found,
                           cudaStream_t st);
+cudaError_t launch_pad_columns(double* V, int M, int64_t strideV, const int* m, int m_max, int count, cudaStream_t st);
+cudaError_t launch_pad_diagonal(double* Ht, int m_max, int64_t strideH, const int* m, const double* big, int count,
+                                cudaStream_t st);
 
 // params.cu
 cudaError_t launch_lanczos_orth(int prec, const Item* items, const RealInfo* real, int n_items, const void* v,

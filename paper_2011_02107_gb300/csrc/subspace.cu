@@ -122,6 +122,38 @@ __global__ void select_kernel(const double* __restrict__ lam, int m, int n_eigs,
     *n_found = cnt;
 }
 
+// Batched variant helpers. For realization i of a group: zero the columns
+// [M - m_max, M - m_i) of V_i (dropped directions inside the common width),
+// and put `big` on the first m_max - m_i diagonal entries of H~_i (their rows
+// and columns are zero, so those eigenvalues are exactly `big`, outside every
+// window).
+__global__ void pad_columns_kernel(double* __restrict__ V, int M, int64_t strideV, const int* __restrict__ m, int m_max) {
+    const int i = blockIdx.y;
+    double* Vi = V + strideV * i;
+    const int c0 = M - m_max, c1 = M - m[i];
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x)
+        for (int rr = threadIdx.x; rr < M; rr += blockDim.x) Vi[static_cast<int64_t>(c) * M + rr] = 0.0;
+}
+
+__global__ void pad_diagonal_kernel(double* __restrict__ Ht, int m_max, int64_t strideH, const int* __restrict__ m,
+                                    const double* __restrict__ big) {
+    const int i = blockIdx.x;
+    double* Hi = Ht + strideH * i;
+    for (int t = threadIdx.x; t < m_max - m[i]; t += blockDim.x) Hi[static_cast<int64_t>(t) * m_max + t] = big[i];
+}
+
+cudaError_t launch_pad_columns(double* V, int M, int64_t strideV, const int* m, int m_max, int count, cudaStream_t st) {
+    dim3 grid(64, count);
+    pad_columns_kernel<<<grid, 256, 0, st>>>(V, M, strideV, m, m_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_diagonal(double* Ht, int m_max, int64_t strideH, const int* m, const double* big, int count,
+                                cudaStream_t st) {
+    pad_diagonal_kernel<<<count, 256, 0, st>>>(Ht, m_max, strideH, m, big);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_orders(int L, double a_r, int* orders, cudaStream_t st) {
     orders_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, a_r, orders);
     return cudaGetLastError();

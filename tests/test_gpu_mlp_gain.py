@@ -1,0 +1,70 @@
+"""What the trained parameter network gains over the method without it (GPU).
+
+Held-out spin-glass shards (seeds the training never saw, sizes at and just
+beyond the training range) are solved three ways on the GPU:
+
+  * reference: plain float64 DACP with the paper's parameters (c = 18,
+    window ratio 2, basis ratio 1.5 -- Sec. II A, II B);
+  * heuristic: double-float DACP with the same heuristic parameters;
+  * learned:   double-float DACP with the network's window / order / basis
+    (dacp_choose_params_mlp), heuristic fallback for short realizations.
+
+The learned run must keep every requested level within 1e-2 of the local
+mean spacing of the reference, and cost less than the heuristic run: both in
+the GB300 cost model (stencil value-orders + M^3 subspace term) and in the
+measured T_E + T_D of the library's own CUDA events.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+P = pytest.importorskip("paper_2011_02107_gb300")
+from paper_2011_02107_gb300 import train_mlp as TM  # noqa: E402
+
+WEIGHTS = TM.DEFAULT_PATH
+
+
+def _run(models, psis, prec, n_eigs, mlp=None, **kw):
+    d = P.Dacp(models, psis, block_b=4, precision=prec)
+    try:
+        eigs, nf, rank, nfb = d.solve(n_eigs, mlp=mlp) if mlp is not None else (None, None, None, 0)
+        if mlp is None:
+            d.choose_params(n_eigs, **kw)
+            d.filter()
+            d.basis_moments()
+            eigs, nf, rank = d.central_eigs(n_eigs)
+        p = d.params()
+        ms = d.timings()
+    finally:
+        d.close()
+    return eigs, nf, p, ms, nfb
+
+
+@pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained weights")
+def test_learned_parameters_keep_accuracy_and_cut_cost():
+    z = np.load(WEIGHTS)
+    if str(z["precision"]) != "df32":
+        pytest.skip("weights trained for another precision")
+    mlp = TM.load(WEIGHTS)
+    try:
+        for N, ne, seeds in ((12, 100, range(900_000, 900_006)), (13, 200, range(910_000, 910_004))):
+            models = [W.spin_glass_shard(N, seed=s) for s in seeds]
+            psis = [W.start_vectors(N, 4, seed=77, r=i) for i in range(len(models))]
+            ref, nf_ref, _, _, _ = _run(models, psis, P.DACP_FP64, ne, c_order=18.0)
+            heu, nf_h, p_h, ms_h, _ = _run(models, psis, P.DACP_DF32, ne)
+            lrn, nf_l, p_l, ms_l, nfb = _run(models, psis, P.DACP_DF32, ne, mlp=mlp)
+            for r in range(len(models)):
+                assert nf_ref[r] == ne and nf_l[r] == ne
+                ok, err = TM.accurate(np.asarray(lrn[r])[:ne], ref[r][:ne])
+                assert ok, (N, r, err)
+            cost_h = sum(TM.cost(N, 4, p_h, r) for r in range(len(models)))
+            cost_l = sum(TM.cost(N, 4, p_l, r) for r in range(len(models)))
+            assert cost_l < 0.8 * cost_h, (N, cost_l, cost_h)
+            assert ms_l[1] + ms_l[2] < ms_h[1] + ms_h[2], (N, ms_l, ms_h)
+    finally:
+        P.dacp_mlp_destroy(mlp)
