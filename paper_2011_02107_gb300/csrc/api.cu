@@ -627,17 +627,24 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         for (int r = 0; r < n_real; ++r) packed_total += (static_cast<int64_t>(1) << c->N[r]) * block_b;
         ok = ok && ck(cudaMemsetAsync(c->psi0_d, 0, static_cast<size_t>(nv) * c->esz, c->st)) &&
              ck(cudaMemcpyAsync(tmp2, psi0, static_cast<size_t>(packed_total) * 8, cudaMemcpyHostToDevice, c->st));
-        int64_t src_off = 0;
-        for (int r = 0; ok && r < n_real; ++r) {
-            const int64_t len = (static_cast<int64_t>(1) << c->N[r]) * block_b;
-            ok = ck(launch_convert(c->prec, tmp2 + src_off,
-                                   static_cast<char*>(c->psi0_d) + static_cast<size_t>(c->info[r].off) * block_b * c->esz,
-                                   len, c->st));
-            src_off += len;
+        std::vector<int64_t> src_off(n_real);
+        int64_t so = 0;
+        for (int r = 0; r < n_real; ++r) {
+            src_off[r] = so;
+            so += (static_cast<int64_t>(1) << c->N[r]) * block_b;
         }
-        c->launches += n_real - 1;
-        for (int r = 0; ok && r < n_real; ++r) ok = ck(launch_diag(c->prec, c->info_d, r, c->N[r], c->J_d, c->h_d, c->diag_d, c->st));
-        c->launches += 2 + n_real;
+        int64_t* src_off_d = nullptr;
+        int max_N0 = 1;
+        for (int r = 0; r < n_real; ++r) max_N0 = std::max(max_N0, c->N[r]);
+        if (ok && (s = dalloc_t(c, &src_off_d, n_real)) != DACP_OK) return bail(s);
+        ok = ok && ck(cudaMemcpyAsync(src_off_d, src_off.data(), sizeof(int64_t) * n_real, cudaMemcpyHostToDevice, c->st)) &&
+             ck(launch_scatter_convert(c->prec, tmp2, src_off_d, c->info_d, n_real, max_N0, block_b, c->psi0_d, c->st)) &&
+             ck(cudaStreamSynchronize(c->st));
+        dfree(c, src_off_d);
+        int max_N = 1;
+        for (int r = 0; r < n_real; ++r) max_N = std::max(max_N, c->N[r]);
+        ok = ok && ck(launch_diag_all(c->prec, c->info_d, n_real, max_N, c->J_d, c->h_d, c->diag_d, c->st));
+        c->launches += 3;
         std::vector<double> ac(8 * static_cast<size_t>(n_real), 0.0);
         for (int r = 0; r < n_real; ++r) ac[8 * r] = 1.0;
         ok = ok && ck(cudaMemcpyAsync(c->apply_coef_d, ac.data(), ac.size() * 8, cudaMemcpyHostToDevice, c->st)) &&

@@ -16,6 +16,10 @@ cudaError_t launch_step(int prec, int b, int mode, const StepArgs& a, int item_b
                         cudaStream_t st);
 cudaError_t launch_diag(int prec, const RealInfo* real, int r, int N, const double* J, const double* h,
                         void* diag, cudaStream_t st);
+cudaError_t launch_diag_all(int prec, const RealInfo* real, int R, int max_N, const double* J, const double* h,
+                            void* diag, cudaStream_t st);
+cudaError_t launch_scatter_convert(int prec, const double* src, const int64_t* src_off, const RealInfo* real, int R,
+                                   int max_N, int b, void* dst, cudaStream_t st);
 cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t st);
 cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, cudaStream_t st);
 cudaError_t launch_normalize(int prec, int b, const Item* items, const RealInfo* real, int n_items,

@@ -642,6 +642,45 @@ __global__ void diag_kernel(const RealInfo* __restrict__ real, int r, const doub
     }
 }
 
+// All realizations in one launch: blockIdx.y is the realization.
+template <typename T>
+__global__ void diag_all_kernel(const RealInfo* __restrict__ real, const double* __restrict__ J,
+                                const double* __restrict__ h, T* __restrict__ diag) {
+    const int r = blockIdx.y;
+    const RealInfo R = real[r];
+    const int64_t D = static_cast<int64_t>(1) << R.N;
+    const double* Jr = J + static_cast<int64_t>(r) * kMaxSpins * kMaxSpins;
+    const double* hr = h + static_cast<int64_t>(r) * kMaxSpins;
+    for (int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; s < D;
+         s += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double d = 0.0;
+        for (int i = 0; i < R.N; ++i) {
+            const double zi = ((s >> i) & 1) ? -1.0 : 1.0;
+            d += hr[i] * zi;
+            for (int j = i + 1; j < R.N; ++j) {
+                const double zj = ((s >> j) & 1) ? -1.0 : 1.0;
+                d += Jr[i * kMaxSpins + j] * zi * zj;
+            }
+        }
+        diag[R.off + s] = static_cast<T>(d);
+    }
+}
+
+// Start vectors: realization r's packed float64 block (at src_off[r]) into its
+// padded slot of the device layout, converted to T. blockIdx.y is r.
+template <typename T>
+__global__ void scatter_convert_kernel(const double* __restrict__ src, const int64_t* __restrict__ src_off,
+                                       const RealInfo* __restrict__ real, int b, T* __restrict__ dst) {
+    const int r = blockIdx.y;
+    const RealInfo R = real[r];
+    const int64_t n = (static_cast<int64_t>(1) << R.N) * b;
+    const double* s = src + src_off[r];
+    T* d = dst + R.off * b;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        d[i] = static_cast<T>(s[i]);
+}
+
 template <typename T>
 __global__ void convert_kernel(const double* __restrict__ src, T* __restrict__ dst, int64_t n) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -749,6 +788,24 @@ cudaError_t launch_diag(int prec, const RealInfo* real, int r, int N, const doub
     const int64_t D = static_cast<int64_t>(1) << N;
     const int grid = static_cast<int>((D + 255) / 256 < 4096 ? (D + 255) / 256 : 4096);
     DACP_FOR_PREC(prec, diag_kernel<T><<<grid, 256, 0, st>>>(real, r, J, h, static_cast<T*>(diag));
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_diag_all(int prec, const RealInfo* real, int R, int max_N, const double* J, const double* h,
+                            void* diag, cudaStream_t st) {
+    const int64_t D = static_cast<int64_t>(1) << max_N;
+    dim3 grid(static_cast<unsigned>((D + 255) / 256 < 1024 ? (D + 255) / 256 : 1024), static_cast<unsigned>(R));
+    DACP_FOR_PREC(prec, diag_all_kernel<T><<<grid, 256, 0, st>>>(real, J, h, static_cast<T*>(diag));
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scatter_convert(int prec, const double* src, const int64_t* src_off, const RealInfo* real, int R,
+                                   int max_N, int b, void* dst, cudaStream_t st) {
+    const int64_t n = (static_cast<int64_t>(1) << max_N) * b;
+    dim3 grid(static_cast<unsigned>((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), static_cast<unsigned>(R));
+    DACP_FOR_PREC(prec, scatter_convert_kernel<T><<<grid, 256, 0, st>>>(src, src_off, real, b, static_cast<T*>(dst));
                         return cudaGetLastError());
     return cudaErrorInvalidValue;
 }

@@ -148,7 +148,7 @@ def main():
             for j, i in enumerate(idx):
                 if nf_ref[j] < ne or nf[j] < ne:
                     continue
-                good, _ = accurate(eigs[j, :ne], ref[j, :ne])
+                good, _ = accurate(np.asarray(eigs[j])[:ne], np.asarray(ref[j])[:ne])
                 if good:
                     ok_count[gi] += 1
                     cst = cost(N, args.b, prm, j)
