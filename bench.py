@@ -62,6 +62,59 @@ def make_inputs(wl, rank=0):
     return models, psis
 
 
+# float32 instructions per double-float fused multiply-add in the library's
+# arithmetic (TwoProduct 2, cross terms 2, TwoSum 6, folding 3, Fast2Sum 3)
+DF_FMA_INSTR = 16
+SMS, FP32_LANES_PER_SM = 152, 128
+
+
+def roofline(wl, models, phase, bytes_evo, states_evo, clk):
+    """Roofline of the evolution stencil over the timed steps.
+
+    float32: HBM-bound; algorithmic bytes = 3 * 2^N * b * 4 per order (read
+    w_k, read w_{k-1}, write w_{k+1}) against the measured copy bandwidth.
+    double-float: float32-issue bound; algorithmic work per state and order =
+    (N b flips + b diagonal + 2b recurrence + b(b+1)/2 + b^2 moment products)
+    double-float FMAs x DF_FMA_INSTR float32 instructions, against
+    152 SMs x 128 lanes x the SM clock sampled during the run.
+    float64: FP64-pipe bound; same FMA count against the measured float64
+    dgemm rate (1.10 TFLOP/s = 0.55 T FMA/s on this GB300).
+    """
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    t_e = phase[1] / 1e3
+    b = wl["b"]
+    N = wl["N"]
+    fma_per_state = N * b + 3 * b + b * (b + 1) // 2 + b * b
+    kern = {"fp32": "step_kernel<float,4,kEvolve>", "df32": "step_kernel<df32,4,kEvolve>",
+            "fp64": "step_kernel<double,4,kEvolve>"}[wl["prec"]]
+    if wl["prec"] == "fp32":
+        peak = peaks.get("hbm_gbs") or 6800.0
+        achieved = bytes_evo / t_e / 1e9 if t_e > 0 else None
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None, "kernel": kern,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic": "3 * 2^N * b * 4 B per realization and order"}
+    if wl["prec"] == "df32":
+        mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        peak = SMS * FP32_LANES_PER_SM * mhz * 1e6 / 1e12            # T instr/s
+        achieved = states_evo * fma_per_state * DF_FMA_INSTR / t_e / 1e12 if t_e > 0 else None
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T float32 instr/s",
+                "frac": achieved / peak if achieved else None, "traffic": None, "kernel": kern,
+                "peak_source": f"152 SMs x 128 float32 lanes x {mhz:.0f} MHz (sampled)",
+                "algorithmic": f"{fma_per_state} double-float FMA x {DF_FMA_INSTR} instr per state and order"}
+    peak = 0.55                                                         # T FMA/s, measured dgemm
+    achieved = states_evo * fma_per_state / t_e / 1e12 if t_e > 0 else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T float64 FMA/s",
+            "frac": achieved / peak if achieved else None, "traffic": None, "kernel": kern,
+            "peak_source": "measured float64 dgemm 1.10 TFLOP/s",
+            "algorithmic": f"{fma_per_state} float64 FMA per state and order"}
+
+
 def reduce_across_ranks(value, op, world, device=None):
     """max / sum of a float over the ranks (identity for one rank)."""
     if world <= 1:
@@ -248,6 +301,7 @@ def run_gpu(args, wl, rank, world):
     l0 = d.launch_count()
     ev0.record(stream)
     bytes_evo = 0.0
+    states_evo = 0.0
     for _ in range(args.steps):
         eigs, nf, rank_ = step()
         found += int(np.clip(np.asarray(nf), 0, None).sum())
@@ -255,6 +309,7 @@ def run_gpu(args, wl, rank, world):
         p = d.params()
         esz = 4 if wl["prec"] == "fp32" else 8           # df32 pairs are 8 bytes
         bytes_evo += sum(3.0 * (int(p["kn"][r]) + 1) * (1 << models[r]["N"]) * wl["b"] * esz for r in range(R))
+        states_evo += sum((int(p["kn"][r]) + 1) * float(1 << models[r]["N"]) for r in range(R))
     ev1.record(stream)
     torch.cuda.synchronize()
     dist_barrier()
@@ -300,22 +355,8 @@ def run_gpu(args, wl, rank, world):
     if mlp is not None:
         P.dacp_mlp_destroy(mlp)
 
-    # ---- roofline of the dominant kernel (evolution stencil): algorithmic bytes / time
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
-    achieved = bytes_evo / (phase[1] / 1e3) / 1e9 if phase[1] > 0 else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "kernel": "step_kernel<float,4,kEvolve> (fused H.v + recurrence + fp64 moments)",
-            "peak_source": peak_src,
-            "algorithmic_bytes_per_order": "3 * 2^N * b * 4 B per realization"}
+    # ---- roofline of the dominant kernel (evolution stencil), per vector precision
+    roof = roofline(wl, models, phase, bytes_evo, states_evo, clk)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,

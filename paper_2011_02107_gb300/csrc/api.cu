@@ -898,15 +898,18 @@ namespace {
 constexpr double kBatchBytes = 24e9;   // device memory budget of one batched subspace group
 constexpr int kMaxBatch = 64;
 
-// Subspace solve for a handle whose realizations share the basis size M:
-// groups of G realizations go through one batched syev of S (with vectors),
+// Batched subspace solve. Every realization's S and H sit in the top-left
+// corner of an M x M slot (M = the largest basis size), zero elsewhere: the
+// zero rows and columns give S eigenvalues 0, which the cut-off removes, so
+// the padding changes nothing. Groups of G realizations go through one batched
+// syev of S (with vectors),
 // the cut-off, two strided-batched dgemm for H~ = U^T H U (U padded to the
 // group's largest rank with zero columns), one batched syev of H~ (values;
 // the padded directions sit on a decoupled diagonal at 3 E_max, outside every
 // window) and the central selection.
 dacp_status central_eigs_batched(dacp_ctx* c, int n_eigs, double window, double eps, double* eigs, int* n_found,
                                  int* rank, int M, int64_t rows_max) {
-    const int b = c->b, R = c->R, L = M / b;
+    const int b = c->b, R = c->R, L = M / b;   // L: orders of the largest basis
     const double per = 4.0 * 8.0 * M * static_cast<double>(M) + 2.0 * 8.0 * rows_max * b * b;
     const int G = std::max(1, std::min(std::min(R, kMaxBatch), static_cast<int>(kBatchBytes / per)));
     const int64_t MM = static_cast<int64_t>(M) * M;
@@ -954,14 +957,21 @@ dacp_status central_eigs_batched(dacp_ctx* c, int n_eigs, double window, double 
         for (int r0 = 0; r0 < R; r0 += G) {
             const int g = std::min(G, R - r0);
             CK(cudaMemsetAsync(bad, 0, sizeof(int) * g, c->st));
+            bool padded = false;
+            for (int i = 0; i < g; ++i) padded = padded || b * (2 * c->n[r0 + i] + 1) != M;
+            if (padded) {
+                CK(cudaMemsetAsync(S, 0, sizeof(double) * g * MM, c->st));
+                CK(cudaMemsetAsync(H, 0, sizeof(double) * g * MM, c->st));
+            }
             for (int i = 0; i < g; ++i) {
                 const int r = r0 + i;
                 const int rows = 2 * c->kn[r] + 2;
-                CK(launch_orders(L, c->a[r] / c->emax[r], orders + static_cast<int64_t>(i) * L, c->st));
+                const int Lr = 2 * c->n[r] + 1;
+                CK(launch_orders(Lr, c->a[r] / c->emax[r], orders + static_cast<int64_t>(i) * L, c->st));
                 CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], mus + i * mstride,
                                   nus + i * mstride, bad + i, c->st));
-                CK(launch_assemble(L, b, orders + static_cast<int64_t>(i) * L, mus + i * mstride, nus + i * mstride,
-                                   S + i * MM, H + i * MM, c->st));
+                CK(launch_assemble(Lr, b, orders + static_cast<int64_t>(i) * L, mus + i * mstride, nus + i * mstride,
+                                   S + i * MM, H + i * MM, c->st, M));
             }
             CKS(cusolverDnXsyevBatched(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
                                        S, M, CUDA_R_64F, lam, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, info,
@@ -1040,9 +1050,11 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
         Mmax = std::max(Mmax, b * (2 * c->n[r] + 1));
         rows_max = std::max<int64_t>(rows_max, 2 * static_cast<int64_t>(c->kn[r]) + 2);
     }
-    bool uniform = c->R >= 2 && c->batched_solve;
-    for (int r = 0; r < c->R && uniform; ++r) uniform = b * (2 * c->n[r] + 1) == Mmax;
-    if (uniform) {
+    // batched whenever there are several realizations and their sizes are within
+    // 25 % of the largest (padding beyond that would cost more than lanes)
+    bool batch = c->R >= 2 && c->batched_solve;
+    for (int r = 0; r < c->R && batch; ++r) batch = 4 * b * (2 * c->n[r] + 1) >= 3 * Mmax;
+    if (batch) {
         // one batched cuSOLVER call per group of equal-size problems
         CK(cudaEventRecord(c->ev[4], c->st));
         TRY(central_eigs_batched(c, n_eigs, window, eps, eigs, n_found, rank, Mmax, rows_max));

@@ -32,7 +32,7 @@ cudaError_t launch_orders(int L, double a_r, int* orders, cudaStream_t st);
 cudaError_t launch_moments(const double* P, int rows, int b, double emax, double* mus, double* nus, int* bad,
                            cudaStream_t st);
 cudaError_t launch_assemble(int L, int b, const int* orders, const double* mus, const double* nus, double* S,
-                            double* H, cudaStream_t st);
+                            double* H, cudaStream_t st, int ld = 0);
 cudaError_t launch_cutoff(const double* lam, int M, double eps, int absolute, double* V, int* m_out,
                           cudaStream_t st);
 cudaError_t launch_select(const double* lam, int m, int n_eigs, double w, double* out, int* n_found,

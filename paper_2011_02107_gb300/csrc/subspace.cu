@@ -57,7 +57,8 @@ __global__ void moments_kernel(const double* __restrict__ P, int rows, int b, do
 // S_{(i,p),(j,q)} = (mu_{x_i+x_j} + mu_{|x_i-x_j|}) / 2, H likewise with nu.
 // Row index i*b + p; column-major M x M (symmetric).
 __global__ void assemble_kernel(int L, int b, const int* __restrict__ orders, const double* __restrict__ mus,
-                                const double* __restrict__ nus, double* __restrict__ S, double* __restrict__ H) {
+                                const double* __restrict__ nus, double* __restrict__ S, double* __restrict__ H,
+                                int ld) {
     const int M = L * b;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const int col = blockIdx.y;
@@ -70,7 +71,7 @@ __global__ void assemble_kernel(int L, int b, const int* __restrict__ orders, co
     const int bb = b * b;
     const int64_t e1 = static_cast<int64_t>(ks) * bb + p * b + q;
     const int64_t e2 = static_cast<int64_t>(kd) * bb + p * b + q;
-    const int64_t o = static_cast<int64_t>(col) * M + row;
+    const int64_t o = static_cast<int64_t>(col) * ld + row;
     S[o] = 0.5 * (mus[e1] + mus[e2]);
     H[o] = 0.5 * (nus[e1] + nus[e2]);
 }
@@ -168,10 +169,10 @@ cudaError_t launch_moments(const double* P, int rows, int b, double emax, double
 }
 
 cudaError_t launch_assemble(int L, int b, const int* orders, const double* mus, const double* nus, double* S,
-                            double* H, cudaStream_t st) {
+                            double* H, cudaStream_t st, int ld) {
     const int M = L * b;
     dim3 grid((M + 127) / 128, M);
-    assemble_kernel<<<grid, 128, 0, st>>>(L, b, orders, mus, nus, S, H);
+    assemble_kernel<<<grid, 128, 0, st>>>(L, b, orders, mus, nus, S, H, ld > 0 ? ld : M);
     return cudaGetLastError();
 }
 

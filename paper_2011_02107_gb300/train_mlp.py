@@ -41,8 +41,8 @@ import workloads as W  # noqa: E402
 
 # knob grids per vector precision: (window ratio d / n_eigs, filter constant c, basis ratio b(2n+1) / d)
 GRIDS = {
-    "df32": ((1.25, 1.6, 2.0), (12.0, 18.0), (0.7, 1.0, 1.5)),
-    "fp64": ((1.25, 1.6, 2.0), (12.0, 18.0), (0.7, 1.0, 1.5)),
+    "df32": ((1.4, 1.7, 2.0, 2.4), (9.0, 12.0, 18.0), (0.7, 0.85, 1.0, 1.5)),
+    "fp64": ((1.4, 1.7, 2.0, 2.4), (9.0, 12.0, 18.0), (0.7, 0.85, 1.0, 1.5)),
     "fp32": ((1.4, 1.8, 2.4), (4.5, 6.0, 8.0), (0.8, 1.1, 1.5)),
 }
 HIDDEN, LAYERS = 256, 3
@@ -55,7 +55,7 @@ def make_problems(n, seed=0):
     rng = np.random.default_rng(seed)
     probs = []
     for i in range(n):
-        N = int(rng.choice([10, 11, 12]))
+        N = int(rng.choice([10, 11, 12, 13, 14], p=[0.22, 0.22, 0.22, 0.2, 0.14]))
         js = float(rng.choice([0.5, 1.0, 1.5]))
         m = W.spin_glass_shard(N, seed=10_000 + i, j_scale=js)
         frac = float(rng.choice([0.012, 0.025, 0.05]))
@@ -120,7 +120,7 @@ def cost(N, b, prm, r):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--problems", type=int, default=576)
+    ap.add_argument("--problems", type=int, default=640)
     ap.add_argument("--b", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--out", default=DEFAULT_PATH)

@@ -395,5 +395,19 @@ def test_batched_solver_matches_lanes():
         for r, m in enumerate(models):
             assert nf0[r] == 80
             assert np.abs(e0[r] - e1[r]).max() < 1e-9 * 2 * Hm.pauli_norm_bound(m)
+        # uneven basis sizes: the batched path zero-pads to the largest
+        p = d.params()
+        n_uneven = np.array([p["n"][r] - 2 * (r % 3) for r in range(5)])
+        d.set_params(p["emax"], p["a"], p["K"], n_uneven)
+        d.filter()
+        d.basis_moments()
+        d.set_solver(0)
+        e0, nf0, rk0 = d.central_eigs(60)
+        d.set_solver(1)
+        e1, nf1, rk1 = d.central_eigs(60)
+        assert np.array_equal(nf0, nf1) and np.array_equal(rk0, rk1)
+        for r, m in enumerate(models):
+            assert nf0[r] == 60
+            assert np.abs(e0[r] - e1[r]).max() < 1e-9 * 2 * Hm.pauli_norm_bound(m)
     finally:
         d.close()
