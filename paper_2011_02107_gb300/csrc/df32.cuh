@@ -75,4 +75,42 @@ __device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) {
     return df_fast_two_sum(s.hi, t);
 }
 
+// Compensated dot-product accumulator (Ogita, Rump & Oishi, "Accurate sum and
+// dot product", SIAM J. Sci. Comput. 26, 2005, algorithm Dot2): the running
+// sum is a float32 `hi` plus one float32 `err` that collects the exact
+// TwoProduct / TwoSum error terms; it is folded into a double-float only at
+// the end. Each term costs TwoProduct (2) + cross terms (2) + TwoSum (6) + 2.
+struct Dot2 {
+    float hi, err;
+};
+
+__device__ __forceinline__ Dot2 dot2_init(df32 x) { return Dot2{x.hi, x.lo}; }
+__device__ __forceinline__ Dot2 dot2_zero() { return Dot2{0.f, 0.f}; }
+
+// acc += a * b
+__device__ __forceinline__ void dot2_mad(Dot2& acc, df32 a, df32 b) {
+    const df32 p = df_two_prod(a.hi, b.hi);
+    const float cross = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    const df32 s = df_two_sum(acc.hi, p.hi);
+    acc.hi = s.hi;
+    acc.err = __fadd_rn(acc.err, __fadd_rn(s.lo, __fadd_rn(p.lo, cross)));
+}
+
+__device__ __forceinline__ df32 dot2_final(Dot2 acc) { return df_fast_two_sum(acc.hi, acc.err); }
+
+// Generic accumulation used by the stencil: plain FMA for float / double,
+// Dot2 for double-float.
+template <typename T> struct Accum {
+    using type = T;
+    __device__ static T zero() { return T(0); }
+    __device__ static void mad(T& acc, T a, T b) { acc = fma(a, b, acc); }
+    __device__ static T final(T acc) { return acc; }
+};
+template <> struct Accum<df32> {
+    using type = Dot2;
+    __device__ static Dot2 zero() { return dot2_zero(); }
+    __device__ static void mad(Dot2& acc, df32 a, df32 b) { dot2_mad(acc, a, b); }
+    __device__ static df32 final(Dot2 acc) { return dot2_final(acc); }
+};
+
 }  // namespace dacp

@@ -31,9 +31,21 @@
 
 namespace dacp {
 
-template <typename T> struct MomAcc { using type = double; };
-template <> struct MomAcc<float> { using type = float; };   // short per-thread runs, then float64
-template <> struct MomAcc<df32> { using type = df32; };     // double-float per thread, then float64
+// Per-thread moment accumulation: float32 over the thread's short run (then
+// float64 across threads), float64 as is, and the Dot2 compensated sum for
+// double-float values.
+template <typename T> struct MomOps {
+    using acc = T;
+    __device__ static acc zero() { return T(0); }
+    __device__ static void mad(acc& s, T a, T b) { s = fma(a, b, s); }
+    __device__ static double to_double(acc s) { return static_cast<double>(s); }
+};
+template <> struct MomOps<df32> {
+    using acc = Dot2;
+    __device__ static acc zero() { return dot2_zero(); }
+    __device__ static void mad(acc& s, df32 a, df32 b) { dot2_mad(s, a, b); }
+    __device__ static double to_double(acc s) { return static_cast<double>(s.hi) + static_cast<double>(s.err); }
+};
 
 // L2-coherent scalar load, and read-only scalar load.
 template <typename T>
@@ -209,12 +221,13 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
     const bool active = step < nsteps;
     const bool want_mom = (MODE == kEvolve) || (MODE == kApply && a.apply_moments);
 
-    using Acc = typename MomAcc<T>::type;
-    Acc xx[B][B], ox[B][B];
+    using MO = MomOps<T>;
+    using AC = Accum<T>;
+    typename MO::acc xx[B][B], ox[B][B];
 #pragma unroll
     for (int p = 0; p < B; ++p)
 #pragma unroll
-        for (int q = 0; q < B; ++q) { xx[p][q] = Acc(0); ox[p][q] = Acc(0); }
+        for (int q = 0; q < B; ++q) { xx[p][q] = MO::zero(); ox[p][q] = MO::zero(); }
 
     if (active) {
         T* wA = static_cast<T*>(a.bufA);
@@ -271,7 +284,8 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
             for (int ub = 0; ub < nunits; ub += kThreads * UP) {
                 int uu[UP];
                 bool val[UP];
-                T xv[UP][VU], acc[UP][VU], yv[UP][VU], zv[UP][VU], dv[UP][SU];
+                T xv[UP][VU], yv[UP][VU], zv[UP][VU], dv[UP][SU];
+                typename AC::type acc[UP][VU];
 #pragma unroll
                 for (int k = 0; k < UP; ++k) {
                     uu[k] = ub + k * kThreads + tid;
@@ -290,7 +304,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                     for (int j = 0; j < SU; ++j)
 #pragma unroll
-                        for (int p = 0; p < B; ++p) acc[k][j * B + p] = dv[k][j] * xv[k][j * B + p];
+                        for (int p = 0; p < B; ++p) {
+                            acc[k][j * B + p] = AC::zero();
+                            AC::mad(acc[k][j * B + p], dv[k][j], xv[k][j * B + p]);
+                        }
                 // flips inside the unit
 #pragma unroll
                 for (int i = 0; i < LS; ++i) {
@@ -301,7 +318,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                         for (int j = 0; j < SU; ++j)
 #pragma unroll
                             for (int p = 0; p < B; ++p)
-                                acc[k][j * B + p] = fma(g, xv[k][(j ^ (1 << i)) * B + p], acc[k][j * B + p]);
+                                AC::mad(acc[k][j * B + p], g, xv[k][(j ^ (1 << i)) * B + p]);
                 }
                 // flips inside the tile (shared memory). Unrolled at compile time and
                 // predicated on the tile's bit count so that every partner load of a
@@ -316,7 +333,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                             T pv[VU];
                             ld_unit<T, B>(tile + ((uu[k] ^ (1 << i)) & umask) * VU, pv);
 #pragma unroll
-                            for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[v], acc[k][v]);
+                            for (int v = 0; v < VU; ++v) AC::mad(acc[k][v], g, pv[v]);
                         }
                     }
                 }
@@ -336,7 +353,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                         for (int k = 0; k < UP; ++k)
 #pragma unroll
-                            for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[k][v], acc[k][v]);
+                            for (int v = 0; v < VU; ++v) AC::mad(acc[k][v], g, pv[k][v]);
                     }
                 }
                 for (int j = kMaxGlobalBitsUnrolled; j < ngb; ++j) {
@@ -346,7 +363,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                         T pv[VU];
                         ld_unit_g<T, B, COHERENT>(xg + (sbase[k] ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B, pv);
 #pragma unroll
-                        for (int v = 0; v < VU; ++v) acc[k][v] = fma(g, pv[v], acc[k][v]);
+                        for (int v = 0; v < VU; ++v) AC::mad(acc[k][v], g, pv[v]);
                     }
                 }
 #pragma unroll
@@ -360,10 +377,11 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     T o[VU];
 #pragma unroll
                     for (int v = 0; v < VU; ++v) {
-                        T t = ch * acc[k][v];
-                        if (use1) t = fma(c1, yv[k][v], t);
-                        if (use2) t = fma(c2, zv[k][v], t);
-                        o[v] = t;
+                        typename AC::type t = AC::zero();
+                        AC::mad(t, ch, AC::final(acc[k][v]));
+                        if (use1) AC::mad(t, c1, yv[k][v]);
+                        if (use2) AC::mad(t, c2, zv[k][v]);
+                        o[v] = AC::final(t);
                     }
                     const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
                     st_unit<T, B>(out + gbase + s0 * B, o);
@@ -374,10 +392,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                             for (int p = 0; p < B; ++p)
 #pragma unroll
                                 for (int q = 0; q < B; ++q) {
-                                    const Acc xq = static_cast<Acc>(xv[k][j * B + q]);
+                                    const T xq = xv[k][j * B + q];
                                     // <x_p, x_q> is symmetric: only q >= p is accumulated
-                                    if (q >= p) xx[p][q] = fma(static_cast<Acc>(xv[k][j * B + p]), xq, xx[p][q]);
-                                    ox[p][q] = fma(static_cast<Acc>(o[j * B + p]), xq, ox[p][q]);
+                                    if (q >= p) MO::mad(xx[p][q], xv[k][j * B + p], xq);
+                                    MO::mad(ox[p][q], o[j * B + p], xq);
                                 }
                     }
                 }
@@ -414,8 +432,8 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     for (int p = 0; p < B; ++p)
 #pragma unroll
                         for (int q = 0; q < B; ++q) {
-                            if (q >= p) xx[p][q] = fma(static_cast<Acc>(xv[p]), static_cast<Acc>(xv[q]), xx[p][q]);
-                            ox[p][q] = fma(static_cast<Acc>(o[p]), static_cast<Acc>(xv[q]), ox[p][q]);
+                            if (q >= p) MO::mad(xx[p][q], xv[p], xv[q]);
+                            MO::mad(ox[p][q], o[p], xv[q]);
                         }
                 }
             }
@@ -429,8 +447,8 @@ reduce:
         for (int p = 0; p < B; ++p)
 #pragma unroll
             for (int q = 0; q < B; ++q) {
-                const double v1 = warp_sum(static_cast<double>(xx[p < q ? p : q][p < q ? q : p]));
-                const double v2 = warp_sum(static_cast<double>(ox[p][q]));
+                const double v1 = warp_sum(MO::to_double(xx[p < q ? p : q][p < q ? q : p]));
+                const double v2 = warp_sum(MO::to_double(ox[p][q]));
                 if (lane == 0) { red_s[warp][p * B + q] = v1; red_s[warp][B * B + p * B + q] = v2; }
             }
         __syncthreads();
