@@ -107,6 +107,29 @@ def chebyshev_moments(model, psi_E, emax: float, kmax: int, diag=None):
     return mu, nu
 
 
+def h2_moments(model, psi_E, emax: float, kmax: int, diag=None):
+    """omega[k, p, q] = <psi_p| H^2 T_k(G) |psi_q> for k = 0..kmax, recorded directly.
+
+    The second moments of the energy that the residual norm of Sec. II C needs
+    (<H^2> of a Ritz vector), as (H^2 psi_p)^T (T_k(G) psi_q) since H is
+    symmetric and commutes with T_k(G).
+    """
+    if diag is None:
+        diag = diagonal(model)
+    psi = _as_block(psi_E)
+    b = psi.shape[1]
+    h2psi = apply_h(model, apply_h(model, psi, diag), diag)
+    om = np.zeros((kmax + 1, b, b))
+    v_prev, v = None, psi
+    for k in range(kmax + 1):
+        if k == 1:
+            v_prev, v = v, apply_h(model, psi, diag) / emax
+        elif k >= 2:
+            v_prev, v = v, 2.0 * apply_h(model, v, diag) / emax - v_prev
+        om[k] = h2psi.T @ v
+    return om
+
+
 def assemble(mu, nu, x):
     """S and H of Appendix C: S = (mu_{x_i+x_j} + mu_{|x_i-x_j|})/2, same for H with nu."""
     x = np.asarray(x, dtype=np.int64)
@@ -143,12 +166,53 @@ def solve_gep(S, H, eps: float = 1e-12, cutoff: str = "relative"):
     return np.linalg.eigvalsh(Ht), int(keep.sum())
 
 
+def ritz_pairs(S, H, eps: float = 1e-12, cutoff: str = "relative"):
+    """Eigenpairs of the generalized problem (Appendix C) with basis coefficients.
+
+    Returns (lam ascending, Bc) where column j of Bc holds the coefficients
+    b_j of the Ritz vector phi_j = sum_(i,p) b_j[i*b+p] T_{x_i}(G) psi_p, so that
+    b_j^T S b_j = 1 and b_j^T H b_j = lam_j: Bc = U Y with U = V~ Lam~^{-1/2} and
+    Y the orthonormal eigenvectors of H~ = U^T H U.
+    """
+    lam_s, V = np.linalg.eigh(S)
+    if cutoff == "relative":
+        keep = lam_s > eps * lam_s.max()
+    elif cutoff == "absolute":
+        keep = (np.abs(lam_s) > eps) & (lam_s > 0.0)
+    else:
+        raise ValueError(cutoff)
+    U = V[:, keep] / np.sqrt(lam_s[keep])
+    Ht = U.T @ H @ U
+    Ht = 0.5 * (Ht + Ht.T)
+    lam, Y = np.linalg.eigh(Ht)
+    return lam, U @ Y
+
+
+def residual_norms(Bc, lam, H2):
+    """||r_j|| = sqrt(<H^2> - <H>^2) of the Ritz vectors (Sec. II C).
+
+    With phi_j normalised (b_j^T S b_j = 1), <H> = lam_j and <H^2> =
+    b_j^T H2 b_j, where H2 is assembled from the omega moments like S from mu.
+    Round-off can push the difference slightly below zero; it is clamped at 0.
+    """
+    h2 = np.einsum("ij,ij->j", Bc, H2 @ Bc)
+    return np.sqrt(np.maximum(h2 - lam * lam, 0.0))
+
+
 def select_central(lams, n_eigs: int, window: float):
     """Eigenvalues inside [-window, window]; the n_eigs of smallest |E|, ascending."""
     lams = np.asarray(lams)
     inside = lams[np.abs(lams) <= window]
     order = np.argsort(np.abs(inside), kind="stable")[:n_eigs]
     return np.sort(inside[order])
+
+
+def select_central_index(lams, n_eigs: int, window: float):
+    """Indices (ascending) into lams of the values select_central returns."""
+    lams = np.asarray(lams)
+    idx = np.nonzero(np.abs(lams) <= window)[0]
+    order = np.argsort(np.abs(lams[idx]), kind="stable")[:n_eigs]
+    return np.sort(idx[order])
 
 
 def dacp(model, psi, emax: float, a: float, K: int, n: int, n_eigs: int,

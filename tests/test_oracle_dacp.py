@@ -136,3 +136,99 @@ def test_planted_sign_error_is_caught(small):
     c = V.T @ psi
     ref = c @ (C.cheb_closed(10, E / emax) * c)
     assert abs(float(psi @ v1) - float(ref)) > 1e-3
+
+
+def test_h2_moments_from_spectrum(small):
+    """omega_k = <psi|H^2 T_k(G)|psi> = sum_i |c_i|^2 E_i^2 T_k(E_i/E_max) (Sec. II C <H^2>)."""
+    m, E, V, emax = small
+    psi = W.start_vectors(8, 2, seed=4)
+    psi /= np.linalg.norm(psi, axis=0)
+    om = DA.h2_moments(m, psi, emax, 120)
+    c = V.T @ psi
+    for k in (0, 1, 2, 3, 57, 119, 120):
+        Tk = C.cheb_closed(k, E / emax)
+        assert np.abs(om[k] - c.T @ ((E * E * Tk)[:, None] * c)).max() < 1e-10 * emax ** 2, k
+
+
+def test_h2_moments_follow_from_mu(small):
+    """G^2 T_k = (T_{k+2} + T_k + T_{|k-1|+1} + T_{||k-1|-1|})/4: omega is linear in mu.
+
+    The GPU path derives omega this way from its moments; here both sides are
+    recorded directly, so a wrong index in the identity fails."""
+    m, E, V, emax = small
+    psi = W.start_vectors(8, 2, seed=5)
+    psi /= np.linalg.norm(psi, axis=0)
+    mu, _ = DA.chebyshev_moments(m, psi, emax, 90)
+    om = DA.h2_moments(m, psi, emax, 88)
+    for k in (0, 1, 2, 3, 40, 88):
+        k1 = abs(k - 1)
+        k2 = abs(k1 - 1)
+        ref = 0.25 * emax ** 2 * (mu[k + 2] + mu[k] + mu[k1 + 1] + mu[k2])
+        assert np.abs(om[k] - ref).max() < 1e-10 * emax ** 2, k
+
+
+@pytest.fixture(scope="module")
+def ritz_case():
+    N, b, ne = 8, 2, 30
+    m = W.chain(N, J=1.0, hx=0.9045, hz=0.8090)
+    Hd = Hm.dense_h(m)
+    E = np.linalg.eigvalsh(Hd)
+    emax = Hm.pauli_norm_bound(m)
+    a = np.sort(np.abs(E))[2 * ne]
+    K = int(np.ceil(18 * emax / a))
+    psi_E = DA.exp_semicircle_filter(m, W.start_vectors(N, b, seed=0), emax, a, K)
+    x = C.basis_orders(a / emax, 24)
+    kmax = int(2 * x[-1])
+    mu, nu = DA.chebyshev_moments(m, psi_E, emax, kmax)
+    om = DA.h2_moments(m, psi_E, emax, kmax)
+    S, H = DA.assemble(mu, nu, x)
+    _, H2 = DA.assemble(mu, om, x)
+    lam, Bc = DA.ritz_pairs(S, H)
+    idx = DA.select_central_index(lam, ne, a)
+    vecs = DA.chebyshev_vectors(m, psi_E, emax, int(x[-1]))
+    basis = np.concatenate([vecs[xi] for xi in x], axis=1)     # column i*b + p = T_{x_i} psi_p
+    return dict(m=m, Hd=Hd, E=E, emax=emax, a=a, S=S, H=H, H2=H2, lam=lam, Bc=Bc, idx=idx, basis=basis, ne=ne)
+
+
+def test_ritz_pairs_are_s_normalised(ritz_case):
+    rc = ritz_case
+    B = rc["Bc"][:, rc["idx"]]
+    lam = rc["lam"][rc["idx"]]
+    assert np.abs(np.einsum("ij,ij->j", B, rc["S"] @ B) - 1.0).max() < 1e-9
+    assert np.abs(np.einsum("ij,ij->j", B, rc["H"] @ B) - lam).max() < 1e-9 * rc["emax"]
+    assert np.allclose(DA.select_central(rc["lam"], rc["ne"], rc["a"]), lam)
+
+
+def test_residual_norms_match_explicit_ritz_vectors(ritz_case):
+    """||r_j||^2 from H2 equals ||(H - lam_j) phi_j||^2 of the explicit Ritz vector,
+    and ||r_j|| bounds the distance of lam_j to the exact spectrum (Sec. II C)."""
+    rc = ritz_case
+    idx = rc["idx"]
+    lam = rc["lam"][idx]
+    phi = rc["basis"] @ rc["Bc"][:, idx]
+    assert np.abs(np.linalg.norm(phi, axis=0) - 1.0).max() < 1e-9
+    r_ex = np.linalg.norm(rc["Hd"] @ phi - phi * lam, axis=0)
+    r = DA.residual_norms(rc["Bc"], rc["lam"], rc["H2"])[idx]
+    assert np.abs(r ** 2 - r_ex ** 2).max() < 1e-12 * rc["emax"] ** 2
+    err = np.array([np.abs(rc["E"] - l).min() for l in lam])
+    assert np.all(err <= r_ex * (1 + 1e-9) + 1e-13 * rc["emax"])
+    assert np.all(err <= np.sqrt(r ** 2 + 1e-12 * rc["emax"] ** 2))
+
+
+def test_residual_norms_flag_a_poor_basis(ritz_case):
+    """With too few orders the levels near the window edge are not converged: their
+    residuals grow while the well-converged central ones stay small."""
+    rc = ritz_case
+    m, emax, a = rc["m"], rc["emax"], rc["a"]
+    psi_E = DA.exp_semicircle_filter(m, W.start_vectors(8, 2, seed=0), emax, a, int(np.ceil(18 * emax / a)))
+    x = C.basis_orders(a / emax, 8)
+    mu, nu = DA.chebyshev_moments(m, psi_E, emax, int(2 * x[-1]))
+    om = DA.h2_moments(m, psi_E, emax, int(2 * x[-1]))
+    S, H = DA.assemble(mu, nu, x)
+    _, H2 = DA.assemble(mu, om, x)
+    lam, Bc = DA.ritz_pairs(S, H)
+    idx = DA.select_central_index(lam, rc["ne"], a)
+    r = DA.residual_norms(Bc, lam, H2)[idx]
+    err = np.array([np.abs(rc["E"] - l).min() for l in lam[idx]])
+    assert r.max() > 1e3 * DA.residual_norms(rc["Bc"], rc["lam"], rc["H2"])[rc["idx"]].max()
+    assert np.all(err <= np.sqrt(r ** 2 + 1e-12 * emax ** 2))
