@@ -150,6 +150,27 @@ dacp_status dacp_central_eigs(dacp_handle hd, int n_eigs, double window, double 
  */
 dacp_status dacp_get_moments(dacp_handle hd, int r, double* mu, int64_t cap, int64_t* count);
 
+/*
+ * dacp_residuals -- the central levels of realization r together with their
+ * residual norms ||r_j|| = sqrt(<H^2> - <H>^2) (Sec. II C), computed from the
+ * moments alone: <H^2> of the Ritz vector phi_j = sum b_j[i,p] T_{x_i}(G) psi_p
+ * is b_j^T H2 b_j, where H2_ij = (omega_{x_i+x_j} + omega_{|x_i-x_j|}) / 2 and
+ * omega_k = <psi|H^2 T_k(G)|psi> = E_max^2 (mu_{k+2} + mu_k + mu_{|k-1|+1}
+ * + mu_{||k-1|-1|}) / 4 (so the evolution runs one order beyond 2k_n+1).
+ * ||r_j|| bounds the distance from the eigenvalue to the exact spectrum; the
+ * moment form loses accuracy below about 1e-7 E_max (the difference of two
+ * O(lam^2 + r^2) numbers), where it is clamped at 0.
+ *   r        realization index.
+ *   n_eigs, window, eps  as in dacp_central_eigs (same selection, same values).
+ *   eigs, resid  host arrays of n_eigs doubles, written ascending in eigs.
+ *   n_found  count written, or -dacp_status (DACP_ERR_NUMERIC,
+ *            DACP_ERR_NOT_CONVERGED) when this realization failed.
+ * Needs dacp_basis_moments first (else DACP_ERR_STATE). Allocates its own
+ * workspace (O(M^2) doubles, M the basis size) and frees it before returning.
+ */
+dacp_status dacp_residuals(dacp_handle hd, int r, int n_eigs, double window, double eps, double* eigs,
+                           double* resid, int* n_found);
+
 /* dacp_get_filtered -- copy realization r's psi_E (2^N_r x b, float64) into
  * psi (capacity cap doubles). Test hook. */
 dacp_status dacp_get_filtered(dacp_handle hd, int r, double* psi, int64_t cap);

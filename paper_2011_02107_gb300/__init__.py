@@ -29,7 +29,7 @@ _STATUS = {0: "DACP_OK", 1: "DACP_ERR_ARG", 2: "DACP_ERR_CUDA", 3: "DACP_ERR_NOM
            5: "DACP_ERR_TIMEOUT", 6: "DACP_ERR_STATE", 7: "DACP_ERR_NOT_CONVERGED", 8: "DACP_ERR_LIBRARY"}
 
 EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_params", "dacp_filter",
-           "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered",
+           "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered", "dacp_residuals",
            "dacp_apply_h", "dacp_get_timings", "dacp_get_launch_count", "dacp_last_error", "dacp_status_string",
            "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_get_weights",
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
@@ -68,6 +68,7 @@ def _load():
         "dacp_central_eigs": [P, I, D, D, P, P, P],
         "dacp_get_moments": [P, I, P, L, ctypes.POINTER(L)],
         "dacp_get_filtered": [P, I, P, L],
+        "dacp_residuals": [P, I, I, D, D, P, P, P],
         "dacp_apply_h": [P, I, P, P],
         "dacp_get_timings": [P, P],
         "dacp_get_launch_count": [P, ctypes.POINTER(L)],
@@ -186,6 +187,16 @@ def dacp_get_filtered(hd, r, n):
     out = np.zeros(n)
     _check(hd, _lib.dacp_get_filtered(hd, int(r), _ptr(out), int(n)))
     return out
+
+
+def dacp_residuals(hd, r, n_eigs, window=0.0, eps=0.0):
+    eigs = np.zeros(n_eigs)
+    resid = np.zeros(n_eigs)
+    nf = ctypes.c_int(0)
+    _check(hd, _lib.dacp_residuals(hd, int(r), int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(resid),
+                                   ctypes.byref(nf)))
+    n = max(nf.value, 0)
+    return eigs[:n], resid[:n], nf.value
 
 
 def dacp_apply_h(hd, r, x_dev_ptr, y_dev_ptr):
@@ -426,6 +437,10 @@ class Dacp:
         rows = 2 * int(p["kn"][r]) + 2
         mu = dacp_get_moments(self.handle, r, rows * self.b * self.b)
         return mu.reshape(rows, self.b, self.b)
+
+    def residuals(self, r, n_eigs, window=0.0, eps=0.0):
+        """Central levels of realization r and their residual norms (Sec. II C)."""
+        return dacp_residuals(self.handle, r, n_eigs, window, eps)
 
     def filtered(self, r):
         n = (1 << self.N[r]) * self.b

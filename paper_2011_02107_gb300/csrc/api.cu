@@ -417,9 +417,9 @@ dacp_status apply_params(dacp_ctx* c) {
         const double ar = c->a[r] / c->emax[r];
         c->kn[r] = static_cast<int>(floor(static_cast<double>(c->n[r]) * M_PI / ar));
         c->info[r].nf = c->K[r];
-        c->info[r].ne = c->kn[r] + 1;
+        c->info[r].ne = c->kn[r] + 2;   // one order beyond mu_{2k_n+1}: mu_{2k_n+3} for the H^2 elements
         c->info[r].mom_off = rows_total;
-        rows_total += 2 * static_cast<int64_t>(c->kn[r]) + 2;
+        rows_total += 2 * static_cast<int64_t>(c->kn[r]) + 4;
     }
     const int64_t need = rows_total * c->b * c->b;
     if (need > c->mom_cap) {
@@ -1208,6 +1208,106 @@ dacp_status dacp_get_filtered(dacp_handle c, int r, double* psi, int64_t cap) {
     };
     dacp_status s = run();
     dfree(c, tmp);
+    return s;
+}
+
+dacp_status dacp_residuals(dacp_handle c, int r, int n_eigs, double window, double eps, double* eigs, double* resid,
+                           int* n_found) {
+    TRY(check_handle(c));
+    if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_residuals before dacp_basis_moments");
+    if (r < 0 || r >= c->R || n_eigs < 1 || !eigs || !resid || !n_found)
+        return fail(c, DACP_ERR_ARG, "bad realization or output arguments");
+    if (!(eps > 0.0)) eps = c->fp32 ? kEpsFp32 : (c->prec == kPrecDF32 ? kEpsDf32 : 1e-12);
+    const int b = c->b, Ln = 2 * c->n[r] + 1, M = b * Ln;
+    const int rows = 2 * c->kn[r] + 4;          // mu_0 .. mu_{2 k_n + 3}
+    const int64_t bb = static_cast<int64_t>(b) * b, MM = static_cast<int64_t>(M) * M;
+    double *mus = nullptr, *nus = nullptr, *om = nullptr, *S = nullptr, *H = nullptr, *H2 = nullptr, *W = nullptr,
+           *Ht = nullptr, *lam = nullptr, *lamt = nullptr, *Bsel = nullptr, *W2 = nullptr, *rs = nullptr;
+    int *orders = nullptr, *ints = nullptr;      // ints: bad, m, info, first, count
+    void* work = nullptr;
+    auto run = [&]() -> dacp_status {
+        TRY(dalloc_t(c, &mus, static_cast<size_t>(rows * bb)));
+        TRY(dalloc_t(c, &nus, static_cast<size_t>(rows * bb)));
+        TRY(dalloc_t(c, &om, static_cast<size_t>(rows * bb)));
+        TRY(dalloc_t(c, &S, static_cast<size_t>(MM)));
+        TRY(dalloc_t(c, &H, static_cast<size_t>(MM)));
+        TRY(dalloc_t(c, &H2, static_cast<size_t>(MM)));
+        TRY(dalloc_t(c, &W, static_cast<size_t>(MM)));
+        TRY(dalloc_t(c, &Ht, static_cast<size_t>(MM)));
+        TRY(dalloc_t(c, &lam, M));
+        TRY(dalloc_t(c, &lamt, M));
+        TRY(dalloc_t(c, &orders, Ln));
+        TRY(dalloc_t(c, &ints, 8));
+        size_t d1 = 0, h1 = 0;
+        CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
+                                        S, M, CUDA_R_64F, lam, CUDA_R_64F, &d1, &h1));
+        TRY(dalloc(c, &work, std::max<size_t>(d1, 8)));
+        std::vector<char> work_h(std::max<size_t>(h1, 1));
+        CK(cudaMemsetAsync(ints, 0, 8 * sizeof(int), c->st));
+        CK(launch_orders(Ln, c->a[r] / c->emax[r], orders, c->st));
+        CK(launch_moments(c->mom_d + c->info[r].mom_off * bb, rows, b, c->emax[r], mus, nus, ints + 0, c->st));
+        CK(launch_omega(mus, rows - 2, b, c->emax[r], om, c->st));
+        // S and H, then H2 from omega (S is written twice with the same values)
+        CK(launch_assemble(Ln, b, orders, mus, nus, S, H, c->st));
+        CK(launch_assemble(Ln, b, orders, mus, om, S, H2, c->st));
+        CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, S, M,
+                             CUDA_R_64F, lam, CUDA_R_64F, work, d1, work_h.data(), h1, ints + 2));
+        CK(launch_cutoff(lam, M, eps, 0, S, ints + 1, c->st));
+        c->launches += 6;
+        int hv[3] = {0, 0, 0};
+        CK(cudaMemcpyAsync(hv, ints, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (hv[0]) { *n_found = -DACP_ERR_NUMERIC; return DACP_OK; }
+        if (hv[2] != 0 || hv[1] < 1) { *n_found = -DACP_ERR_NOT_CONVERGED; return DACP_OK; }
+        const int m = hv[1];
+        const double* U = S + static_cast<int64_t>(M - m) * M;
+        const double one = 1.0, zero = 0.0;
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m, M, &one, H, M, U, M, &zero, W, M));
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, M, &one, U, M, W, M, &zero, Ht, m));
+        size_t d2 = 0, h2 = 0;
+        CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F,
+                                        Ht, m, CUDA_R_64F, lamt, CUDA_R_64F, &d2, &h2));
+        if (d2 > d1) {
+            CK(cudaStreamSynchronize(c->st));
+            dfree(c, work);
+            work = nullptr;
+            TRY(dalloc(c, &work, d2));
+            d1 = d2;
+        }
+        if (h2 > work_h.size()) work_h.resize(h2);
+        // H~ = Y diag(lamt) Y^T; Y overwrites Ht
+        CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, Ht, m,
+                             CUDA_R_64F, lamt, CUDA_R_64F, work, d1, work_h.data(), h2, ints + 2));
+        const double w = window > 0.0 ? window : c->a[r];
+        CK(launch_select_range(lamt, m, n_eigs, w, ints + 3, c->st));
+        c->launches += 1;
+        CK(cudaMemcpyAsync(hv, ints + 2, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (hv[0] != 0) { *n_found = -DACP_ERR_NOT_CONVERGED; return DACP_OK; }
+        const int first = hv[1], cnt = hv[2];
+        *n_found = cnt;
+        if (cnt < 1) return DACP_OK;
+        TRY(dalloc_t(c, &Bsel, static_cast<size_t>(M) * cnt));
+        TRY(dalloc_t(c, &W2, static_cast<size_t>(M) * cnt));
+        TRY(dalloc_t(c, &rs, cnt));
+        // coefficients of the selected Ritz vectors, b_j = U y_j, then H2 b_j
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, cnt, m, &one, U, M, Ht + static_cast<int64_t>(first) * m,
+                        m, &zero, Bsel, M));
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, cnt, M, &one, H2, M, Bsel, M, &zero, W2, M));
+        CK(launch_residual(Bsel, W2, M, cnt, lamt + first, rs, c->st));
+        c->launches += 1;
+        CK(cudaMemcpyAsync(eigs, lamt + first, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(resid, rs, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        return DACP_OK;
+    };
+    dacp_status s = run();
+    cudaStreamSynchronize(c->st);
+    for (void* p : {static_cast<void*>(mus), static_cast<void*>(nus), static_cast<void*>(om), static_cast<void*>(S),
+                    static_cast<void*>(H), static_cast<void*>(H2), static_cast<void*>(W), static_cast<void*>(Ht),
+                    static_cast<void*>(lam), static_cast<void*>(lamt), static_cast<void*>(Bsel), static_cast<void*>(W2),
+                    static_cast<void*>(rs), static_cast<void*>(orders), static_cast<void*>(ints), work})
+        dfree(c, p);
     return s;
 }
 

@@ -37,6 +37,10 @@ cudaError_t launch_cutoff(const double* lam, int M, double eps, int absolute, do
                           cudaStream_t st);
 cudaError_t launch_select(const double* lam, int m, int n_eigs, double w, double* out, int* n_found,
                           cudaStream_t st);
+cudaError_t launch_omega(const double* mus, int rows_out, int b, double emax, double* om, cudaStream_t st);
+cudaError_t launch_select_range(const double* lam, int m, int n_eigs, double w, int* out, cudaStream_t st);
+cudaError_t launch_residual(const double* Bsel, const double* W2, int M, int count, const double* lam, double* resid,
+                            cudaStream_t st);
 cudaError_t launch_pad_columns(double* V, int M, int64_t strideV, const int* m, int m_max, int count, cudaStream_t st);
 cudaError_t launch_pad_diagonal(double* Ht, int m_max, int64_t strideH, const int* m, const double* big, int count,
                                 cudaStream_t st);

@@ -155,6 +155,80 @@ cudaError_t launch_pad_diagonal(double* Ht, int m_max, int64_t strideH, const in
     return cudaGetLastError();
 }
 
+// <psi| H^2 T_k |psi> = E_max^2 <psi| G^2 T_k |psi>, with
+// G^2 T_k = (T_{k+2} + T_k + T_{|k-1|+1} + T_{||k-1|-1|}) / 4 (two uses of
+// G T_j = (T_{j+1} + T_{|j-1|}) / 2); mus holds the symmetrised mu rows.
+__global__ void omega_kernel(const double* __restrict__ mus, int rows_out, int b, double emax,
+                             double* __restrict__ om) {
+    const int bb = b * b;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < static_cast<int64_t>(rows_out) * bb;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int k = static_cast<int>(e / bb);
+        const int pq = static_cast<int>(e % bb);
+        const int k1 = k >= 1 ? k - 1 : 1;               // |k-1|
+        const int k2 = k1 >= 1 ? k1 - 1 : 1;             // ||k-1|-1|
+        const double v = mus[static_cast<int64_t>(k + 2) * bb + pq] + mus[static_cast<int64_t>(k) * bb + pq] +
+                         mus[static_cast<int64_t>(k1 + 1) * bb + pq] + mus[static_cast<int64_t>(k2) * bb + pq];
+        om[e] = emax * emax * 0.25 * v;
+    }
+}
+
+// Index range [first, first + count) of the selected levels in ascending lam.
+__global__ void select_range_kernel(const double* __restrict__ lam, int m, int n_eigs, double w, int* out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int lo = 0, hi = m;
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (lam[mid] >= 0.0) hi = mid; else lo = mid + 1;
+    }
+    int l = lo - 1, h = lo, cnt = 0;
+    while (cnt < n_eigs) {
+        const bool okl = l >= 0 && fabs(lam[l]) <= w;
+        const bool okh = h < m && fabs(lam[h]) <= w;
+        if (!okl && !okh) break;
+        if (okl && (!okh || fabs(lam[l]) <= fabs(lam[h]))) --l; else ++h;
+        ++cnt;
+    }
+    out[0] = l + 1;
+    out[1] = cnt;
+}
+
+// resid_j = sqrt(max(0, b_j^T (H^2 b_j) - lam_j^2)); one CTA per column j.
+__global__ void residual_kernel(const double* __restrict__ Bsel, const double* __restrict__ W2, int M,
+                                const double* __restrict__ lam, double* __restrict__ resid) {
+    __shared__ double red[256];
+    const int j = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < M; i += blockDim.x)
+        s += Bsel[static_cast<int64_t>(j) * M + i] * W2[static_cast<int64_t>(j) * M + i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) resid[j] = sqrt(fmax(0.0, red[0] - lam[j] * lam[j]));
+}
+
+cudaError_t launch_omega(const double* mus, int rows_out, int b, double emax, double* om, cudaStream_t st) {
+    const int64_t n = static_cast<int64_t>(rows_out) * b * b;
+    const int grid = static_cast<int>((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    omega_kernel<<<grid, 256, 0, st>>>(mus, rows_out, b, emax, om);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_range(const double* lam, int m, int n_eigs, double w, int* out, cudaStream_t st) {
+    select_range_kernel<<<1, 32, 0, st>>>(lam, m, n_eigs, w, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double* Bsel, const double* W2, int M, int count, const double* lam, double* resid,
+                            cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    residual_kernel<<<count, 256, 0, st>>>(Bsel, W2, M, lam, resid);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_orders(int L, double a_r, int* orders, cudaStream_t st) {
     orders_kernel<<<(L + 255) / 256, 256, 0, st>>>(L, a_r, orders);
     return cudaGetLastError();

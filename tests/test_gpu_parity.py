@@ -158,6 +158,73 @@ def test_c1_eigenvalues_vs_oracle_and_dense(c1_run):
     assert abs(int(c1_run["rank"][0]) - c1_run["ref"]["rank"]) <= 2
 
 
+def test_c1_residual_norms_vs_oracle(c1_run):
+    """Moment-form residual norms (Sec. II C): the same levels as dacp_central_eigs, r_j^2
+    against the oracle's (H2 assembled from directly recorded <psi|H^2 T_k|psi>), and
+    ||r_j|| bounds each level's distance to the dense spectrum. r^2 is a difference of
+    O(lam^2 + r^2) numbers, so it is compared in units of E_max^2."""
+    d, ref, m = c1_run["d"], c1_run["ref"], c1_run["m"]
+    emax, a = c1_run["emax"], c1_run["a"]
+    eigs, resid, nf = d.residuals(0, 100)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    width = E[-1] - E[0]
+    assert nf == 100
+    assert np.abs(eigs - c1_run["eigs"]).max() < 1e-10 * width
+    om = DA.h2_moments(m, ref["psi_E"], emax, 2 * ref["kn"])
+    S, H = DA.assemble(ref["mu"], ref["nu"], ref["orders"])
+    _, H2 = DA.assemble(ref["mu"], om, ref["orders"])
+    lam, Bc = DA.ritz_pairs(S, H)
+    idx = DA.select_central_index(lam, 100, a)
+    r_or = DA.residual_norms(Bc, lam, H2)[idx]
+    assert np.abs(lam[idx] - eigs).max() < 1e-9 * width
+    assert np.abs(resid ** 2 - r_or ** 2).max() < 1e-11 * emax ** 2
+    err = np.array([np.abs(E - x).min() for x in eigs])
+    assert np.all(err <= np.sqrt(resid ** 2 + 1e-11 * emax ** 2))
+
+
+def test_residual_norms_flag_a_short_basis():
+    """With a basis too small for the window the edge levels are unconverged: the
+    moment residuals rise by orders of magnitude while still bounding the error."""
+    m = W.chain(10)
+    psi = W.start_vectors(10, 2, seed=3)
+    emax, a, K, _ = _c1_params(m, psi, 60, 2)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    out = {}
+    for n in (12, 60):
+        d = P.Dacp([m], [psi], block_b=2, precision=P.DACP_FP64)
+        try:
+            d.set_params(emax, a, K, n)
+            d.filter()
+            d.basis_moments()
+            eigs, resid, nf = d.residuals(0, 60)
+        finally:
+            d.close()
+        assert nf > 0
+        err = np.array([np.abs(E - x).min() for x in eigs])
+        assert np.all(err <= np.sqrt(resid ** 2 + 1e-11 * emax ** 2)), n
+        out[n] = resid
+    assert out[12].max() > 1e3 * out[60].max()
+
+
+def test_residuals_argument_and_state_errors():
+    m = W.chain(6)
+    d = P.Dacp([m], [W.start_vectors(6, 1, seed=0)], block_b=1, precision=P.DACP_FP64)
+    try:
+        with pytest.raises(P.DacpError) as e:
+            d.residuals(0, 4)
+        assert e.value.status == 6                      # DACP_ERR_STATE
+        d.choose_params(4)
+        d.filter()
+        d.basis_moments()
+        with pytest.raises(P.DacpError) as e:
+            d.residuals(1, 4)
+        assert e.value.status == 1                      # DACP_ERR_ARG
+        eigs, resid, nf = d.residuals(0, 4)
+        assert nf == 4 and np.all(resid >= 0.0)
+    finally:
+        d.close()
+
+
 def test_heuristic_parameters_match_oracle():
     models = [W.chain(10), W.spin_glass_shard(9, seed=3), W.random_model(8, seed=5)]
     psis = [W.start_vectors(m["N"], 2, seed=11, r=i) for i, m in enumerate(models)]
