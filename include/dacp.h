@@ -144,6 +144,22 @@ dacp_status dacp_central_eigs(dacp_handle hd, int n_eigs, double window, double 
                               double* eigs, int* n_found, int* rank);
 
 /*
+ * dacp_solve -- dacp_filter, dacp_basis_moments and dacp_central_eigs in one
+ * call, with the subspace solves overlapped with the evolution: realizations
+ * finish their evolution at different orders (k_n differs), and each group of
+ * finished realizations is solved (batched cuSOLVER / cuBLAS on a second
+ * stream, driven by a worker thread) while the rest keep evolving. Results
+ * are those of the three separate calls up to the rounding of the batched
+ * eigensolver (the batch composition sets the padded size).
+ * Arguments and per-realization failures as in dacp_central_eigs. Requires
+ * parameters; leaves the handle as dacp_basis_moments does (moments kept for
+ * dacp_get_moments / dacp_residuals). dacp_get_timings then gives T_F, T_E and
+ * the part of the subspace solves that ran after the evolution ended.
+ */
+dacp_status dacp_solve(dacp_handle hd, int n_eigs, double window, double eps, double* eigs, int* n_found,
+                       int* rank);
+
+/*
  * dacp_get_moments -- copy realization r's moments mu[j][p][q], j = 0..2k_n+1
  * (float64, (2 k_n + 2) b^2 values) into mu (capacity cap doubles).
  * *count receives the number of doubles. Test hook.

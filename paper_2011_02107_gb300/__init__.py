@@ -29,7 +29,7 @@ _STATUS = {0: "DACP_OK", 1: "DACP_ERR_ARG", 2: "DACP_ERR_CUDA", 3: "DACP_ERR_NOM
            5: "DACP_ERR_TIMEOUT", 6: "DACP_ERR_STATE", 7: "DACP_ERR_NOT_CONVERGED", 8: "DACP_ERR_LIBRARY"}
 
 EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_params", "dacp_filter",
-           "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered", "dacp_residuals",
+           "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered", "dacp_residuals", "dacp_solve",
            "dacp_apply_h", "dacp_get_timings", "dacp_get_launch_count", "dacp_last_error", "dacp_status_string",
            "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_get_weights",
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
@@ -69,6 +69,7 @@ def _load():
         "dacp_get_moments": [P, I, P, L, ctypes.POINTER(L)],
         "dacp_get_filtered": [P, I, P, L],
         "dacp_residuals": [P, I, I, D, D, P, P, P],
+        "dacp_solve": [P, I, D, D, P, P, P],
         "dacp_apply_h": [P, I, P, P],
         "dacp_get_timings": [P, P],
         "dacp_get_launch_count": [P, ctypes.POINTER(L)],
@@ -173,6 +174,14 @@ def dacp_central_eigs(hd, R, n_eigs, window=0.0, eps=0.0):
     rank = np.zeros(R, dtype=np.int32)
     _check(hd, _lib.dacp_central_eigs(hd, int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(nf),
                                       _ptr(rank)))
+    return eigs.reshape(R, n_eigs), nf, rank
+
+
+def dacp_solve(hd, R, n_eigs, window=0.0, eps=0.0):
+    eigs = np.zeros(R * n_eigs)
+    nf = np.zeros(R, dtype=np.int32)
+    rank = np.zeros(R, dtype=np.int32)
+    _check(hd, _lib.dacp_solve(hd, int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(nf), _ptr(rank)))
     return eigs.reshape(R, n_eigs), nf, rank
 
 
@@ -417,9 +426,7 @@ class Dacp:
             self.choose_params_mlp(mlp, n_eigs)
         else:
             self.choose_params(n_eigs)
-        self.filter()
-        self.basis_moments()
-        eigs, nf, rank = self.central_eigs(n_eigs, window, eps)
+        eigs, nf, rank = self.run(n_eigs, window, eps)
         redo = [r for r in range(self.R) if nf[r] < n_eigs] if mlp is not None else []
         if redo:
             sub = Dacp([self.models[r] for r in redo], [self.psi0_list[r] for r in redo], self.b, self.precision,
@@ -431,6 +438,11 @@ class Dacp:
             for j, r in enumerate(redo):
                 eigs[r], nf[r], rank[r] = e2[j], nf2[j], rk2[j]
         return eigs, nf, rank, len(redo)
+
+    def run(self, n_eigs, window=0.0, eps=0.0):
+        """Filter, evolution and subspace solves with the solves overlapped (dacp_solve)."""
+        eigs, nf, rank = dacp_solve(self.handle, self.R, n_eigs, window, eps)
+        return [eigs[r, :max(nf[r], 0)].copy() for r in range(self.R)], nf, rank
 
     def moments(self, r):
         p = self.params()

@@ -12,7 +12,11 @@
 #include <algorithm>
 #include <map>
 #include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <functional>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <thread>
 #include <vector>
@@ -114,6 +118,12 @@ struct dacp_ctx {
     cusolverDnHandle_t sol = nullptr;
     cublasHandle_t blas = nullptr;
     cusolverDnParams_t sp = nullptr;
+
+    // second solver (stream + handles) that overlaps subspace solves with the evolution
+    cudaStream_t st2 = nullptr;
+    cusolverDnHandle_t sol2 = nullptr;
+    cublasHandle_t blas2 = nullptr;
+    cusolverDnParams_t sp2 = nullptr;
 
     std::vector<Lane> lanes;
     int lane_M = 0, lane_neigs = 0;
@@ -289,7 +299,8 @@ StepArgs base_args(dacp_ctx* c) {
 // the evolution (one pass each) on the handle stream. A graph of kGraphOrders
 // orders is captured once and replayed; realizations whose run is shorter
 // skip the surplus orders inside the kernel.
-dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
+dacp_status run_orders(dacp_ctx* c, bool filter, int orders,
+                       const std::function<dacp_status(int)>& after = std::function<dacp_status(int)>()) {
     if (orders <= 0) return DACP_OK;
     CK(cudaMemsetAsync(c->step_ctr_d, 0, sizeof(int), c->st));
     const StepArgs a = base_args(c);
@@ -303,6 +314,7 @@ dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
         int grid = 0;
         CK(launch_persistent(c->prec, c->b, filter ? 0 : 1, a, ni, orders, c->smem, c->st, &grid));
         c->launches += 1;
+        if (after) TRY(after(orders));
         return DACP_OK;
     }
     auto launch_order = [&]() -> cudaError_t {
@@ -334,11 +346,13 @@ dacp_status run_orders(dacp_ctx* c, bool filter, int orders) {
         for (; done + kGraphOrders <= orders; done += kGraphOrders) {
             CK(cudaGraphLaunch(g.exec, c->st));
             c->launches += kGraphOrders * (filter ? 2 : 1);
+            if (after) TRY(after(done + kGraphOrders));
         }
     }
     for (; done < orders; ++done) {
         CK(launch_order());
         c->launches += filter ? 2 : 1;
+        if (after) TRY(after(done + 1));
     }
     return DACP_OK;
 }
@@ -491,6 +505,10 @@ void dacp_destroy(dacp_handle c) {
     if (c->ge.exec) cudaGraphExecDestroy(c->ge.exec);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->sp2) cusolverDnDestroyParams(c->sp2);
+    if (c->sol2) cusolverDnDestroy(c->sol2);
+    if (c->blas2) cublasDestroy(c->blas2);
+    if (c->st2) cudaStreamDestroy(c->st2);
     if (c->sp) cusolverDnDestroyParams(c->sp);
     if (c->sol) cusolverDnDestroy(c->sol);
     if (c->blas) cublasDestroy(c->blas);
@@ -898,138 +916,192 @@ namespace {
 constexpr double kBatchBytes = 24e9;   // device memory budget of one batched subspace group
 constexpr int kMaxBatch = 64;
 
-// Batched subspace solve. Every realization's S and H sit in the top-left
-// corner of an M x M slot (M = the largest basis size), zero elsewhere: the
-// zero rows and columns give S eigenvalues 0, which the cut-off removes, so
-// the padding changes nothing. Groups of G realizations go through one batched
-// syev of S (with vectors),
-// the cut-off, two strided-batched dgemm for H~ = U^T H U (U padded to the
-// group's largest rank with zero columns), one batched syev of H~ (values;
-// the padded directions sit on a decoupled diagonal at 3 E_max, outside every
-// window) and the central selection.
-dacp_status central_eigs_batched(dacp_ctx* c, int n_eigs, double window, double eps, double* eigs, int* n_found,
-                                 int* rank, int M, int64_t rows_max) {
-    const int b = c->b, R = c->R, L = M / b;   // L: orders of the largest basis
-    const double per = 4.0 * 8.0 * M * static_cast<double>(M) + 2.0 * 8.0 * rows_max * b * b;
-    const int G = std::max(1, std::min(std::min(R, kMaxBatch), static_cast<int>(kBatchBytes / per)));
-    const int64_t MM = static_cast<int64_t>(M) * M;
-    const int64_t mstride = rows_max * b * b;
-    double *S = nullptr, *H = nullptr, *W = nullptr, *Ht = nullptr, *lam = nullptr, *lamt = nullptr, *mus = nullptr,
-           *nus = nullptr, *sel = nullptr, *big = nullptr;
+// Streams and library handles one batched subspace solve runs on.
+struct SolveRes {
+    cudaStream_t st = nullptr;
+    cusolverDnHandle_t sol = nullptr;
+    cublasHandle_t blas = nullptr;
+    cusolverDnParams_t sp = nullptr;
+};
+
+// Device workspace of batched subspace solves: G slots of basis size <= M.
+struct BatchWs {
+    int G = 0, M = 0, L = 0, n_eigs = 0;
+    int64_t mstride = 0;
+    double *S = nullptr, *H = nullptr, *W = nullptr, *Ht = nullptr, *lam = nullptr, *lamt = nullptr,
+           *mus = nullptr, *nus = nullptr, *sel = nullptr, *big = nullptr;
     int *orders = nullptr, *mi = nullptr, *bad = nullptr, *info = nullptr, *nf = nullptr;
     void* work = nullptr;
+    size_t dbytes = 0, hbytes = 0;
     std::vector<char> work_h;
-    auto cleanup = [&]() {
-        for (void* p : {static_cast<void*>(S), static_cast<void*>(H), static_cast<void*>(W), static_cast<void*>(Ht),
-                        static_cast<void*>(lam), static_cast<void*>(lamt), static_cast<void*>(mus),
-                        static_cast<void*>(nus), static_cast<void*>(sel), static_cast<void*>(big),
-                        static_cast<void*>(orders), static_cast<void*>(mi), static_cast<void*>(bad),
-                        static_cast<void*>(info), static_cast<void*>(nf), work})
-            dfree(c, p);
-    };
-    auto run = [&]() -> dacp_status {
-        TRY(dalloc_t(c, &S, static_cast<size_t>(G) * MM));
-        TRY(dalloc_t(c, &H, static_cast<size_t>(G) * MM));
-        TRY(dalloc_t(c, &W, static_cast<size_t>(G) * MM));
-        TRY(dalloc_t(c, &Ht, static_cast<size_t>(G) * MM));
-        TRY(dalloc_t(c, &lam, static_cast<size_t>(G) * M));
-        TRY(dalloc_t(c, &lamt, static_cast<size_t>(G) * M));
-        TRY(dalloc_t(c, &mus, static_cast<size_t>(G) * mstride));
-        TRY(dalloc_t(c, &nus, static_cast<size_t>(G) * mstride));
-        TRY(dalloc_t(c, &sel, static_cast<size_t>(G) * n_eigs));
-        TRY(dalloc_t(c, &big, G));
-        TRY(dalloc_t(c, &orders, static_cast<size_t>(G) * L));
-        TRY(dalloc_t(c, &mi, G));
-        TRY(dalloc_t(c, &bad, G));
-        TRY(dalloc_t(c, &info, G));
-        TRY(dalloc_t(c, &nf, G));
-        size_t d1 = 0, h1 = 0, d2 = 0, h2 = 0;
-        CKS(cusolverDnXsyevBatched_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M,
-                                              CUDA_R_64F, S, M, CUDA_R_64F, lam, CUDA_R_64F, &d1, &h1, G));
-        CKS(cusolverDnXsyevBatched_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, M,
-                                              CUDA_R_64F, Ht, M, CUDA_R_64F, lamt, CUDA_R_64F, &d2, &h2, G));
-        const size_t dbytes = std::max(d1, d2), hbytes = std::max(h1, h2);
-        TRY(dalloc(c, &work, dbytes));
-        work_h.resize(std::max<size_t>(hbytes, 1));
-        std::vector<int> hm(G), hbad(G), hinfo(G), hnf(G);
-        std::vector<double> hbig(G), hsel(static_cast<size_t>(G) * n_eigs);
-        const double one = 1.0, zero = 0.0;
-        for (int r0 = 0; r0 < R; r0 += G) {
-            const int g = std::min(G, R - r0);
-            CK(cudaMemsetAsync(bad, 0, sizeof(int) * g, c->st));
-            bool padded = false;
-            for (int i = 0; i < g; ++i) padded = padded || b * (2 * c->n[r0 + i] + 1) != M;
-            if (padded) {
-                CK(cudaMemsetAsync(S, 0, sizeof(double) * g * MM, c->st));
-                CK(cudaMemsetAsync(H, 0, sizeof(double) * g * MM, c->st));
-            }
-            for (int i = 0; i < g; ++i) {
-                const int r = r0 + i;
-                const int rows = 2 * c->kn[r] + 2;
-                const int Lr = 2 * c->n[r] + 1;
-                CK(launch_orders(Lr, c->a[r] / c->emax[r], orders + static_cast<int64_t>(i) * L, c->st));
-                CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], mus + i * mstride,
-                                  nus + i * mstride, bad + i, c->st));
-                CK(launch_assemble(Lr, b, orders + static_cast<int64_t>(i) * L, mus + i * mstride, nus + i * mstride,
-                                   S + i * MM, H + i * MM, c->st, M));
-            }
-            CKS(cusolverDnXsyevBatched(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
-                                       S, M, CUDA_R_64F, lam, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, info,
-                                       g));
-            for (int i = 0; i < g; ++i) CK(launch_cutoff(lam + static_cast<int64_t>(i) * M, M, eps, 0, S + i * MM, mi + i, c->st));
-            c->launches += 4 * g;
-            CK(cudaMemcpyAsync(hm.data(), mi, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
-            CK(cudaMemcpyAsync(hbad.data(), bad, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
-            CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
-            CK(cudaStreamSynchronize(c->st));
-            int m_max = 0;
-            for (int i = 0; i < g; ++i)
-                if (!hbad[i] && hinfo[i] == 0) m_max = std::max(m_max, hm[i]);
-            if (m_max < 1) {
-                for (int i = 0; i < g; ++i) n_found[r0 + i] = hbad[i] ? -DACP_ERR_NUMERIC : -DACP_ERR_NOT_CONVERGED;
-                continue;
-            }
-            for (int i = 0; i < g; ++i) {
-                if (rank) rank[r0 + i] = hm[i];
-                if (hbad[i] || hinfo[i] != 0) hm[i] = m_max;     // excluded below; keep the padding a no-op
-                hbig[i] = 3.0 * c->emax[r0 + i];
-            }
-            CK(cudaMemcpyAsync(mi, hm.data(), sizeof(int) * g, cudaMemcpyHostToDevice, c->st));
-            CK(cudaMemcpyAsync(big, hbig.data(), sizeof(double) * g, cudaMemcpyHostToDevice, c->st));
-            CK(launch_pad_columns(S, M, MM, mi, m_max, g, c->st));
-            const double* U = S + static_cast<int64_t>(M - m_max) * M;
-            CKB(cublasDgemmStridedBatched(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m_max, M, &one, H, M, MM, U, M, MM,
-                                          &zero, W, M, static_cast<int64_t>(M) * m_max, g));
-            CKB(cublasDgemmStridedBatched(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, m_max, m_max, M, &one, U, M, MM, W, M,
-                                          static_cast<int64_t>(M) * m_max, &zero, Ht, m_max,
-                                          static_cast<int64_t>(m_max) * m_max, g));
-            CK(launch_pad_diagonal(Ht, m_max, static_cast<int64_t>(m_max) * m_max, mi, big, g, c->st));
-            CKS(cusolverDnXsyevBatched(c->sol, c->sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m_max,
-                                       CUDA_R_64F, Ht, m_max, CUDA_R_64F, lamt, CUDA_R_64F, work, dbytes,
-                                       work_h.data(), hbytes, info, g));
-            for (int i = 0; i < g; ++i) {
-                const double w = window > 0.0 ? window : c->a[r0 + i];
-                CK(launch_select(lamt + static_cast<int64_t>(i) * m_max, m_max, n_eigs, w, sel + static_cast<int64_t>(i) * n_eigs,
-                                 nf + i, c->st));
-            }
-            c->launches += 2 + g;
-            CK(cudaMemcpyAsync(hsel.data(), sel, sizeof(double) * g * n_eigs, cudaMemcpyDeviceToHost, c->st));
-            CK(cudaMemcpyAsync(hnf.data(), nf, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
-            CK(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * g, cudaMemcpyDeviceToHost, c->st));
-            CK(cudaStreamSynchronize(c->st));
-            for (int i = 0; i < g; ++i) {
-                const int r = r0 + i;
-                if (hbad[i]) { n_found[r] = -DACP_ERR_NUMERIC; continue; }
-                if (hinfo[i] != 0) { n_found[r] = -DACP_ERR_NOT_CONVERGED; continue; }
-                memcpy(eigs + static_cast<size_t>(r) * n_eigs, hsel.data() + static_cast<size_t>(i) * n_eigs,
-                       sizeof(double) * hnf[i]);
-                n_found[r] = hnf[i];
-            }
-        }
+};
+
+void ws_free(dacp_ctx* c, BatchWs& w) {
+    for (void* p : {static_cast<void*>(w.S), static_cast<void*>(w.H), static_cast<void*>(w.W), static_cast<void*>(w.Ht),
+                    static_cast<void*>(w.lam), static_cast<void*>(w.lamt), static_cast<void*>(w.mus),
+                    static_cast<void*>(w.nus), static_cast<void*>(w.sel), static_cast<void*>(w.big),
+                    static_cast<void*>(w.orders), static_cast<void*>(w.mi), static_cast<void*>(w.bad),
+                    static_cast<void*>(w.info), static_cast<void*>(w.nf), w.work})
+        dfree(c, p);
+    w = BatchWs();
+}
+
+// Number of slots that fit the batch budget for basis size M.
+int ws_slots(int R, int M, int64_t rows_max, int b) {
+    const double per = 4.0 * 8.0 * M * static_cast<double>(M) + 2.0 * 8.0 * rows_max * b * b;
+    return std::max(1, std::min(std::min(R, kMaxBatch), static_cast<int>(kBatchBytes / per)));
+}
+
+dacp_status ws_alloc(dacp_ctx* c, BatchWs& w, const SolveRes& s, int G, int M, int64_t rows_max, int n_eigs) {
+    const int b = c->b;
+    w.G = G;
+    w.M = M;
+    w.L = M / b;
+    w.n_eigs = n_eigs;
+    w.mstride = rows_max * b * b;
+    const size_t MM = static_cast<size_t>(M) * M;
+    TRY(dalloc_t(c, &w.S, G * MM));
+    TRY(dalloc_t(c, &w.H, G * MM));
+    TRY(dalloc_t(c, &w.W, G * MM));
+    TRY(dalloc_t(c, &w.Ht, G * MM));
+    TRY(dalloc_t(c, &w.lam, static_cast<size_t>(G) * M));
+    TRY(dalloc_t(c, &w.lamt, static_cast<size_t>(G) * M));
+    TRY(dalloc_t(c, &w.mus, static_cast<size_t>(G) * w.mstride));
+    TRY(dalloc_t(c, &w.nus, static_cast<size_t>(G) * w.mstride));
+    TRY(dalloc_t(c, &w.sel, static_cast<size_t>(G) * n_eigs));
+    TRY(dalloc_t(c, &w.big, G));
+    TRY(dalloc_t(c, &w.orders, static_cast<size_t>(G) * w.L));
+    TRY(dalloc_t(c, &w.mi, G));
+    TRY(dalloc_t(c, &w.bad, G));
+    TRY(dalloc_t(c, &w.info, G));
+    TRY(dalloc_t(c, &w.nf, G));
+    size_t d1 = 0, h1 = 0, d2 = 0, h2 = 0;
+    CKS(cusolverDnXsyevBatched_bufferSize(s.sol, s.sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
+                                          w.S, M, CUDA_R_64F, w.lam, CUDA_R_64F, &d1, &h1, G));
+    CKS(cusolverDnXsyevBatched_bufferSize(s.sol, s.sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, M,
+                                          CUDA_R_64F, w.Ht, M, CUDA_R_64F, w.lamt, CUDA_R_64F, &d2, &h2, G));
+    w.dbytes = std::max(d1, d2);
+    w.hbytes = std::max(h1, h2);
+    TRY(dalloc(c, &w.work, w.dbytes));
+    w.work_h.resize(std::max<size_t>(w.hbytes, 1));
+    return DACP_OK;
+}
+
+// Batched subspace solve of the g <= G realizations idx[0..g) on stream s.st.
+// Every realization's S and H sit in the top-left corner of an Mg x Mg slot
+// (Mg = the group's largest basis size), zero elsewhere: the zero rows and
+// columns give S eigenvalues 0, which the cut-off removes, so the padding
+// changes nothing. One batched syev of S (with vectors), the cut-off, two
+// strided-batched dgemm for H~ = U^T H U (U padded to the group's largest rank
+// with zero columns), one batched syev of H~ (values; the padded directions
+// sit on a decoupled diagonal at 3 E_max, outside every window) and the
+// central selection.
+dacp_status solve_batch(dacp_ctx* c, BatchWs& w, const SolveRes& s, const int* idx, int g, int n_eigs, double window,
+                        double eps, double* eigs, int* n_found, int* rank) {
+    const int b = c->b;
+    int Mg = 0;
+    for (int i = 0; i < g; ++i) Mg = std::max(Mg, b * (2 * c->n[idx[i]] + 1));
+    if (g > w.G || Mg > w.M || n_eigs > w.n_eigs) return fail(c, DACP_ERR_ARG, "batched solve beyond its workspace");
+    const int L = Mg / b;
+    const int64_t MM = static_cast<int64_t>(Mg) * Mg;
+    const int64_t mstride = w.mstride;
+    size_t d1 = 0, h1 = 0, d2 = 0, h2 = 0;
+    CKS(cusolverDnXsyevBatched_bufferSize(s.sol, s.sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, Mg, CUDA_R_64F,
+                                          w.S, Mg, CUDA_R_64F, w.lam, CUDA_R_64F, &d1, &h1, g));
+    if (d1 > w.dbytes || h1 > w.work_h.size()) return fail(c, DACP_ERR_CUDA, "batched eigensolver workspace grew");
+    std::vector<int> hm(g), hbad(g), hinfo(g), hnf(g);
+    std::vector<double> hbig(g), hsel(static_cast<size_t>(g) * n_eigs);
+    const double one = 1.0, zero = 0.0;
+    CK(cudaMemsetAsync(w.bad, 0, sizeof(int) * g, s.st));
+    bool padded = false;
+    for (int i = 0; i < g; ++i) padded = padded || b * (2 * c->n[idx[i]] + 1) != Mg;
+    if (padded) {
+        CK(cudaMemsetAsync(w.S, 0, sizeof(double) * g * MM, s.st));
+        CK(cudaMemsetAsync(w.H, 0, sizeof(double) * g * MM, s.st));
+    }
+    for (int i = 0; i < g; ++i) {
+        const int r = idx[i];
+        const int rows = 2 * c->kn[r] + 2;
+        const int Lr = 2 * c->n[r] + 1;
+        CK(launch_orders(Lr, c->a[r] / c->emax[r], w.orders + static_cast<int64_t>(i) * L, s.st));
+        CK(launch_moments(c->mom_d + c->info[r].mom_off * b * b, rows, b, c->emax[r], w.mus + i * mstride,
+                          w.nus + i * mstride, w.bad + i, s.st));
+        CK(launch_assemble(Lr, b, w.orders + static_cast<int64_t>(i) * L, w.mus + i * mstride, w.nus + i * mstride,
+                           w.S + i * MM, w.H + i * MM, s.st, Mg));
+    }
+    CKS(cusolverDnXsyevBatched(s.sol, s.sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, Mg, CUDA_R_64F, w.S, Mg,
+                               CUDA_R_64F, w.lam, CUDA_R_64F, w.work, w.dbytes, w.work_h.data(), w.hbytes, w.info, g));
+    for (int i = 0; i < g; ++i)
+        CK(launch_cutoff(w.lam + static_cast<int64_t>(i) * Mg, Mg, eps, 0, w.S + i * MM, w.mi + i, s.st));
+    c->launches += 4 * g;
+    CK(cudaMemcpyAsync(hm.data(), w.mi, sizeof(int) * g, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(hbad.data(), w.bad, sizeof(int) * g, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(hinfo.data(), w.info, sizeof(int) * g, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    int m_max = 0;
+    for (int i = 0; i < g; ++i)
+        if (!hbad[i] && hinfo[i] == 0) m_max = std::max(m_max, hm[i]);
+    if (m_max < 1) {
+        for (int i = 0; i < g; ++i) n_found[idx[i]] = hbad[i] ? -DACP_ERR_NUMERIC : -DACP_ERR_NOT_CONVERGED;
         return DACP_OK;
-    };
-    dacp_status st = run();
-    cleanup();
+    }
+    for (int i = 0; i < g; ++i) {
+        if (rank) rank[idx[i]] = hm[i];
+        if (hbad[i] || hinfo[i] != 0) hm[i] = m_max;     // excluded below; keep the padding a no-op
+        hbig[i] = 3.0 * c->emax[idx[i]];
+    }
+    CK(cudaMemcpyAsync(w.mi, hm.data(), sizeof(int) * g, cudaMemcpyHostToDevice, s.st));
+    CK(cudaMemcpyAsync(w.big, hbig.data(), sizeof(double) * g, cudaMemcpyHostToDevice, s.st));
+    CK(launch_pad_columns(w.S, Mg, MM, w.mi, m_max, g, s.st));
+    const double* U = w.S + static_cast<int64_t>(Mg - m_max) * Mg;
+    CKB(cublasDgemmStridedBatched(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, Mg, m_max, Mg, &one, w.H, Mg, MM, U, Mg, MM, &zero,
+                                  w.W, Mg, static_cast<int64_t>(Mg) * m_max, g));
+    CKB(cublasDgemmStridedBatched(s.blas, CUBLAS_OP_T, CUBLAS_OP_N, m_max, m_max, Mg, &one, U, Mg, MM, w.W, Mg,
+                                  static_cast<int64_t>(Mg) * m_max, &zero, w.Ht, m_max,
+                                  static_cast<int64_t>(m_max) * m_max, g));
+    CK(launch_pad_diagonal(w.Ht, m_max, static_cast<int64_t>(m_max) * m_max, w.mi, w.big, g, s.st));
+    CKS(cusolverDnXsyevBatched_bufferSize(s.sol, s.sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m_max,
+                                          CUDA_R_64F, w.Ht, m_max, CUDA_R_64F, w.lamt, CUDA_R_64F, &d2, &h2, g));
+    if (d2 > w.dbytes || h2 > w.work_h.size()) return fail(c, DACP_ERR_CUDA, "batched eigensolver workspace grew");
+    CKS(cusolverDnXsyevBatched(s.sol, s.sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m_max, CUDA_R_64F,
+                               w.Ht, m_max, CUDA_R_64F, w.lamt, CUDA_R_64F, w.work, w.dbytes, w.work_h.data(),
+                               w.hbytes, w.info, g));
+    for (int i = 0; i < g; ++i) {
+        const double wd = window > 0.0 ? window : c->a[idx[i]];
+        CK(launch_select(w.lamt + static_cast<int64_t>(i) * m_max, m_max, n_eigs, wd,
+                         w.sel + static_cast<int64_t>(i) * n_eigs, w.nf + i, s.st));
+    }
+    c->launches += 2 + g;
+    CK(cudaMemcpyAsync(hsel.data(), w.sel, sizeof(double) * g * n_eigs, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(hnf.data(), w.nf, sizeof(int) * g, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaMemcpyAsync(hinfo.data(), w.info, sizeof(int) * g, cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    for (int i = 0; i < g; ++i) {
+        const int r = idx[i];
+        if (hbad[i]) { n_found[r] = -DACP_ERR_NUMERIC; continue; }
+        if (hinfo[i] != 0) { n_found[r] = -DACP_ERR_NOT_CONVERGED; continue; }
+        memcpy(eigs + static_cast<size_t>(r) * n_eigs, hsel.data() + static_cast<size_t>(i) * n_eigs,
+               sizeof(double) * hnf[i]);
+        n_found[r] = hnf[i];
+    }
+    return DACP_OK;
+}
+
+// All realizations through batched solves on the handle's stream.
+dacp_status central_eigs_batched(dacp_ctx* c, int n_eigs, double window, double eps, double* eigs, int* n_found,
+                                 int* rank, int M, int64_t rows_max) {
+    const SolveRes s{c->st, c->sol, c->blas, c->sp};
+    const int G = ws_slots(c->R, M, rows_max, c->b);
+    BatchWs w;
+    dacp_status st = ws_alloc(c, w, s, G, M, rows_max, n_eigs);
+    std::vector<int> idx(G);
+    for (int r0 = 0; r0 < c->R && st == DACP_OK; r0 += G) {
+        const int g = std::min(G, c->R - r0);
+        for (int i = 0; i < g; ++i) idx[i] = r0 + i;
+        st = solve_batch(c, w, s, idx.data(), g, n_eigs, window, eps, eigs, n_found, rank);
+    }
+    cudaStreamSynchronize(c->st);
+    ws_free(c, w);
     return st;
 }
 
@@ -1158,6 +1230,176 @@ dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double e
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]);
     c->t_ms[2] = ms;
+    return DACP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+dacp_status ensure_solver2(dacp_ctx* c) {
+    if (c->st2) return DACP_OK;
+    CK(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    CKS(cusolverDnCreate(&c->sol2));
+    CKS(cusolverDnSetStream(c->sol2, c->st2));
+    CKS(cusolverDnCreateParams(&c->sp2));
+    CKB(cublasCreate(&c->blas2));
+    CKB(cublasSetStream(c->blas2, c->st2));
+    return DACP_OK;
+}
+
+// Realizations in rising completion order, cut into sub-batches whose basis
+// sizes stay within 25 % of the sub-batch's largest (padding beyond that
+// would cost more than it saves).
+void size_batches(const dacp_ctx* c, std::vector<int>& idx, int G, std::vector<std::pair<int, int>>& out) {
+    const int b = c->b;
+    auto M = [&](int r) { return b * (2 * c->n[r] + 1); };
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return M(x) > M(y); });
+    out.clear();
+    for (size_t p = 0; p < idx.size();) {
+        size_t q = p + 1;
+        while (q < idx.size() && static_cast<int>(q - p) < G && 4 * M(idx[q]) >= 3 * M(idx[p])) ++q;
+        out.emplace_back(static_cast<int>(p), static_cast<int>(q));
+        p = q;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+dacp_status dacp_solve(dacp_handle c, int n_eigs, double window, double eps, double* eigs, int* n_found, int* rank) {
+    TRY(check_handle(c));
+    if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_solve before parameters");
+    if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
+    if (!(eps > 0.0)) eps = c->fp32 ? kEpsFp32 : (c->prec == kPrecDF32 ? kEpsDf32 : 1e-12);
+    const int R = c->R, b = c->b;
+    int Mmax = 0, maxE = 0;
+    int64_t rows_max = 0;
+    for (int r = 0; r < R; ++r) {
+        Mmax = std::max(Mmax, b * (2 * c->n[r] + 1));
+        rows_max = std::max<int64_t>(rows_max, 2 * static_cast<int64_t>(c->kn[r]) + 2);
+        maxE = std::max(maxE, c->info[r].ne);
+        n_found[r] = 0;
+        if (rank) rank[r] = 0;
+    }
+    TRY(dacp_filter(c));
+    TRY(ensure_solver2(c));
+    const SolveRes s2{c->st2, c->sol2, c->blas2, c->sp2};
+    const int G = ws_slots(R, Mmax, rows_max, b);
+    // a job is handed to the solver once this many realizations have finished
+    const int chunk = std::max(1, std::min(G, std::max(8, R / 8)));
+
+    struct Job {
+        std::vector<int> idx;
+        cudaEvent_t ev = nullptr;
+    };
+    BatchWs w;
+    std::vector<cudaEvent_t> events;
+    std::deque<Job> queue;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool closed = false;
+    dacp_status wst = DACP_OK;
+    cudaEvent_t evD = nullptr;
+
+    // Worker: one batched solve per job (split by basis size), on the second
+    // stream, after the evolution orders that finished the job's realizations.
+    auto worker = [&]() {
+        cudaSetDevice(c->device);
+        std::vector<std::pair<int, int>> parts;
+        for (;;) {
+            Job j;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return !queue.empty() || closed; });
+                if (queue.empty()) return;
+                j = std::move(queue.front());
+                queue.pop_front();
+            }
+            if (wst != DACP_OK) continue;
+            if (cudaStreamWaitEvent(s2.st, j.ev, 0) != cudaSuccess) {
+                wst = fail(c, DACP_ERR_CUDA, "cudaStreamWaitEvent on the solver stream");
+                continue;
+            }
+            size_batches(c, j.idx, G, parts);
+            for (auto& pq : parts) {
+                if (wst != DACP_OK) break;
+                wst = solve_batch(c, w, s2, j.idx.data() + pq.first, pq.second - pq.first, n_eigs, window, eps, eigs,
+                                  n_found, rank);
+            }
+        }
+    };
+
+    std::thread th;
+    auto push = [&](const std::vector<int>& order, int from, int to) -> dacp_status {
+        cudaEvent_t ev = nullptr;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        events.push_back(ev);
+        CK(cudaEventRecord(ev, c->st));
+        Job j;
+        j.idx.assign(order.begin() + from, order.begin() + to);
+        j.ev = ev;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            queue.push_back(std::move(j));
+        }
+        cv.notify_one();
+        return DACP_OK;
+    };
+    auto run = [&]() -> dacp_status {
+        TRY(ws_alloc(c, w, s2, G, Mmax, rows_max, n_eigs));
+        CK(cudaEventCreate(&evD));
+        std::vector<int> order(R);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return c->info[x].ne < c->info[y].ne; });
+        th = std::thread(worker);
+        int dispatched = 0, complete = 0;
+        auto after = [&](int done) -> dacp_status {
+            while (complete < R && c->info[order[complete]].ne <= done) ++complete;
+            if (complete - dispatched >= chunk) {
+                TRY(push(order, dispatched, complete));
+                dispatched = complete;
+            }
+            return DACP_OK;
+        };
+        const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
+        TRY(set_evolution_coef(c, c->emax));
+        CK(cudaEventRecord(c->ev[2], c->st));
+        CK(cudaMemcpyAsync(c->A_d, c->psiE_d, vec_bytes, cudaMemcpyDeviceToDevice, c->st));
+        TRY(run_orders(c, false, maxE, after));
+        CK(cudaEventRecord(c->ev[3], c->st));
+        if (dispatched < R) TRY(push(order, dispatched, R));
+        return DACP_OK;
+    };
+    dacp_status st = run();
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        closed = true;
+    }
+    cv.notify_one();
+    if (th.joinable()) th.join();
+    if (st == DACP_OK) st = wst;
+    if (st == DACP_OK && evD) {
+        if (cudaEventRecord(evD, s2.st) != cudaSuccess) st = fail(c, DACP_ERR_CUDA, "cudaEventRecord");
+    }
+    cudaStreamSynchronize(s2.st);
+    cudaStreamSynchronize(c->st);
+    if (st == DACP_OK) st = check_device_flag(c);
+    if (st == DACP_OK) {
+        float te = 0.f, td = 0.f;
+        cudaEventElapsedTime(&te, c->ev[2], c->ev[3]);
+        cudaEventElapsedTime(&td, c->ev[3], evD);
+        c->t_ms[1] = te;
+        c->t_ms[2] = td > 0.f ? td : 0.0;   // the part of the solves not hidden under the evolution
+    }
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    if (evD) cudaEventDestroy(evD);
+    ws_free(c, w);
+    if (st != DACP_OK) return st;
+    // restore the filter coefficients for a later dacp_filter
+    TRY(apply_params(c));
+    c->state = 3;
     return DACP_OK;
 }
 

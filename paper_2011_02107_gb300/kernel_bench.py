@@ -45,7 +45,7 @@ def main():
     try:
         emax = np.array([sum(abs(m["J"][np.triu_indices(args.N, 1)])) + sum(m["gamma"]) for m in models])
         a = 0.015 * emax
-        # choose n so that k_n + 1 = orders (k_n = floor(n pi / a_r))
+        # choose n so that k_n + 1 ~ orders (k_n = floor(n pi / a_r))
         n = max(1, int(math.floor((args.orders - 1) * 0.015 / math.pi)))
         d.set_params(emax, a, args.orders, n)
         if args.mode < 0 or args.tile <= 0:
@@ -58,7 +58,7 @@ def main():
         ms = d.timings()
         p = d.params()
         vec = args.R * (1 << args.N) * args.b * esz
-        evo_orders = int(p["kn"].max()) + 1
+        evo_orders = int(p["kn"].max()) + 2          # mu up to 2 k_n + 3
         out = {"N": args.N, "R": args.R, "b": args.b, "precision": args.precision, "mode": mode, "tile_bytes": tile,
                "filter_orders": args.orders, "evolution_orders": evo_orders,
                "filter_us_per_order": 1e3 * ms[0] / args.orders, "evolution_us_per_order": 1e3 * ms[1] / evo_orders,

@@ -182,6 +182,44 @@ def test_c1_residual_norms_vs_oracle(c1_run):
     assert np.all(err <= np.sqrt(resid ** 2 + 1e-11 * emax ** 2))
 
 
+@pytest.mark.parametrize("prec", [P.DACP_FP64, P.DACP_DF32])
+def test_overlapped_solve_matches_staged_calls(prec):
+    """dacp_solve (subspace solves of finished realizations overlapped with the evolution
+    of the rest, batched by basis size) against filter / basis_moments / central_eigs,
+    on 20 realizations of uneven N and basis size; and against dense eigh."""
+    Ns = [8, 9, 10, 11] * 5
+    models = [W.spin_glass_shard(N, seed=300 + i) for i, N in enumerate(Ns)]
+    psis = [W.start_vectors(N, 2, seed=8, r=i) for i, N in enumerate(Ns)]
+    ne = 30
+    out = []
+    for mode in ("staged", "solve"):
+        d = P.Dacp(models, psis, block_b=2, precision=prec)
+        try:
+            d.choose_params(ne)
+            if mode == "staged":
+                d.filter()
+                d.basis_moments()
+                eigs, nf, rank = d.central_eigs(ne)
+            else:
+                eigs, nf, rank = d.run(ne)
+                ms = d.timings()
+                assert ms[0] > 0 and ms[1] > 0 and ms[2] >= 0
+                mu = d.moments(0)             # moments stay available after the call
+                assert mu.shape[0] == 2 * int(d.params()["kn"][0]) + 2
+            out.append((eigs, nf, rank))
+        finally:
+            d.close()
+    (e1, nf1, rk1), (e2, nf2, rk2) = out
+    for r, m in enumerate(models):
+        E = np.linalg.eigvalsh(Hm.dense_h(m))
+        width = E[-1] - E[0]
+        assert nf1[r] == ne and nf2[r] == ne, r
+        assert abs(int(rk1[r]) - int(rk2[r])) <= 2
+        assert np.abs(np.asarray(e1[r]) - np.asarray(e2[r])).max() < 1e-9 * width, r
+        tol = 1e-9 if prec == P.DACP_FP64 else 1e-8
+        assert np.abs(np.asarray(e2[r]) - MT.central_exact(E, ne)).max() < tol * width, r
+
+
 def test_residual_norms_flag_a_short_basis():
     """With a basis too small for the window the edge levels are unconverged: the
     moment residuals rise by orders of magnitude while still bounding the error."""
