@@ -272,6 +272,11 @@ typedef struct dacp_mlp_ctx* dacp_mlp;
  * stream: cudaStream_t or NULL (private stream). */
 dacp_status dacp_mlp_create(dacp_mlp* out, int n_in, int n_hidden, int hidden_layers, int n_out,
                             const float* weights, uint64_t seed, void* stream);
+/* dacp_mlp_set_output_range -- clamp every denormalised output y_i to
+ * [lo[i], hi[i]] (n_out floats each, host; lo <= hi, else DACP_ERR_ARG).
+ * Default: no clamp. A trained network is kept to the range of its labels,
+ * so that it never extrapolates to knobs it was not trained on. */
+dacp_status dacp_mlp_set_output_range(dacp_mlp m, const float* lo, const float* hi);
 /* dacp_mlp_set_normalization -- feature and target standardisation:
  * z = (x - in_mean) / in_std into the network, y = z_out * out_std + out_mean. */
 dacp_status dacp_mlp_set_normalization(dacp_mlp m, const float* in_mean, const float* in_std,

@@ -31,7 +31,7 @@ _STATUS = {0: "DACP_OK", 1: "DACP_ERR_ARG", 2: "DACP_ERR_CUDA", 3: "DACP_ERR_NOM
 EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_params", "dacp_filter",
            "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered", "dacp_residuals", "dacp_solve",
            "dacp_apply_h", "dacp_get_timings", "dacp_get_launch_count", "dacp_last_error", "dacp_status_string",
-           "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_get_weights",
+           "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_set_output_range", "dacp_mlp_get_weights",
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
@@ -75,6 +75,7 @@ def _load():
         "dacp_get_launch_count": [P, ctypes.POINTER(L)],
         "dacp_mlp_create": [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64, P],
         "dacp_mlp_set_normalization": [P, P, P, P, P],
+        "dacp_mlp_set_output_range": [P, P, P],
         "dacp_mlp_get_weights": [P, P, L, ctypes.POINTER(L)],
         "dacp_mlp_set_weights": [P, P, L],
         "dacp_mlp_forward": [P, P, I, P],
@@ -258,6 +259,11 @@ def dacp_mlp_create(n_in, n_hidden, hidden_layers, n_out, weights=None, seed=0, 
 def dacp_mlp_set_normalization(m, in_mean, in_std, out_mean, out_std):
     a, b, c_, d = _f32(in_mean), _f32(in_std), _f32(out_mean), _f32(out_std)
     _mcheck(m, _lib.dacp_mlp_set_normalization(m, _ptr(a), _ptr(b), _ptr(c_), _ptr(d)))
+
+
+def dacp_mlp_set_output_range(m, lo, hi):
+    a, b = _f32(lo), _f32(hi)
+    _mcheck(m, _lib.dacp_mlp_set_output_range(m, _ptr(a), _ptr(b)))
 
 
 def dacp_mlp_get_weights(m):

@@ -9,6 +9,7 @@
 // Loss: sum (y - t)^2 / (2 B) on standardised inputs and targets.
 // Adam (Kingma & Ba 2015) with bias correction.
 
+#include <float.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -118,13 +119,14 @@ __global__ void gather_norm_kernel(const float* __restrict__ x, const int* __res
     }
 }
 
-// y = z * std + mean
+// y = clamp(z * std + mean, lo, hi)
 __global__ void denorm_kernel(const float* __restrict__ z, int B, int F, const float* __restrict__ mean,
-                              const float* __restrict__ sd, float* __restrict__ y) {
+                              const float* __restrict__ sd, const float* __restrict__ lo,
+                              const float* __restrict__ hi, float* __restrict__ y) {
     const int n = B * F;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int f = i % F;
-        y[i] = z[i] * sd[f] + mean[f];
+        y[i] = fminf(fmaxf(z[i] * sd[f] + mean[f], lo[f]), hi[f]);
     }
 }
 
@@ -150,6 +152,7 @@ struct dacp_mlp_ctx {
     int device = 0;
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
     float *in_mean = nullptr, *in_std = nullptr, *out_mean = nullptr, *out_std = nullptr;
+    float *out_lo = nullptr, *out_hi = nullptr;   // range the outputs are clamped to
     std::vector<float*> act;             // activations per layer, capacity cap_b rows
     float* delta[2] = {nullptr, nullptr};
     float *xb = nullptr, *tb = nullptr, *yb = nullptr;
@@ -292,15 +295,20 @@ dacp_status dacp_mlp_create(dacp_mlp* out, int n_in, int n_hidden, int hidden_la
         cudaMalloc(&c->in_std, sizeof(float) * n_in) != cudaSuccess ||
         cudaMalloc(&c->out_mean, sizeof(float) * n_out) != cudaSuccess ||
         cudaMalloc(&c->out_std, sizeof(float) * n_out) != cudaSuccess ||
+        cudaMalloc(&c->out_lo, sizeof(float) * n_out) != cudaSuccess ||
+        cudaMalloc(&c->out_hi, sizeof(float) * n_out) != cudaSuccess ||
         cudaMalloc(&c->loss_d, sizeof(double)) != cudaSuccess)
         return bail(DACP_ERR_NOMEM);
     std::vector<float> zeros_in(n_in, 0.f), ones_in(n_in, 1.f), zeros_out(n_out, 0.f), ones_out(n_out, 1.f);
+    std::vector<float> lo_out(n_out, -FLT_MAX), hi_out(n_out, FLT_MAX);
     bool ok = cudaMemcpy(c->p, h.data(), pb, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemset(c->m, 0, pb) == cudaSuccess && cudaMemset(c->v, 0, pb) == cudaSuccess &&
               cudaMemcpy(c->in_mean, zeros_in.data(), 4 * n_in, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(c->in_std, ones_in.data(), 4 * n_in, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(c->out_mean, zeros_out.data(), 4 * n_out, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(c->out_std, ones_out.data(), 4 * n_out, cudaMemcpyHostToDevice) == cudaSuccess;
+              cudaMemcpy(c->out_std, ones_out.data(), 4 * n_out, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->out_lo, lo_out.data(), 4 * n_out, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(c->out_hi, hi_out.data(), 4 * n_out, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return bail(DACP_ERR_CUDA);
     *out = c;
     return DACP_OK;
@@ -313,7 +321,8 @@ void dacp_mlp_destroy(dacp_mlp c) {
     for (float* a : c->act) cudaFree(a);
     for (void* q : {static_cast<void*>(c->p), static_cast<void*>(c->g), static_cast<void*>(c->m),
                     static_cast<void*>(c->v), static_cast<void*>(c->in_mean), static_cast<void*>(c->in_std),
-                    static_cast<void*>(c->out_mean), static_cast<void*>(c->out_std), static_cast<void*>(c->delta[0]),
+                    static_cast<void*>(c->out_mean), static_cast<void*>(c->out_std), static_cast<void*>(c->out_lo),
+                    static_cast<void*>(c->out_hi), static_cast<void*>(c->delta[0]),
                     static_cast<void*>(c->delta[1]), static_cast<void*>(c->xb), static_cast<void*>(c->tb),
                     static_cast<void*>(c->yb), static_cast<void*>(c->loss_d)})
         cudaFree(q);
@@ -361,6 +370,18 @@ dacp_status dacp_mlp_set_normalization(dacp_mlp c, const float* in_mean, const f
     return DACP_OK;
 }
 
+dacp_status dacp_mlp_set_output_range(dacp_mlp c, const float* lo, const float* hi) {
+    if (!c || !lo || !hi) return DACP_ERR_ARG;
+    cudaSetDevice(c->device);
+    const int no = c->sizes.back();
+    for (int i = 0; i < no; ++i)
+        if (!(lo[i] <= hi[i])) return mfail(c, DACP_ERR_ARG, "output range %d: lo > hi or NaN", i);
+    MCK(cudaMemcpyAsync(c->out_lo, lo, 4 * no, cudaMemcpyHostToDevice, c->st));
+    MCK(cudaMemcpyAsync(c->out_hi, hi, 4 * no, cudaMemcpyHostToDevice, c->st));
+    MCK(cudaStreamSynchronize(c->st));
+    return DACP_OK;
+}
+
 dacp_status dacp_mlp_forward(dacp_mlp c, const float* x, int batch, float* y) {
     if (!c || !x || !y || batch < 1) return DACP_ERR_ARG;
     cudaSetDevice(c->device);
@@ -370,7 +391,8 @@ dacp_status dacp_mlp_forward(dacp_mlp c, const float* x, int batch, float* y) {
     MCK(cudaMemcpyAsync(c->xb, x, sizeof(float) * batch * ni, cudaMemcpyHostToDevice, c->st));
     gather_norm_kernel<<<grid1(batch * ni), 256, 0, c->st>>>(c->xb, nullptr, batch, ni, c->in_mean, c->in_std, c->act[0]);
     forward_dev(c, batch);
-    denorm_kernel<<<grid1(batch * no), 256, 0, c->st>>>(c->act[L], batch, no, c->out_mean, c->out_std, c->yb);
+    denorm_kernel<<<grid1(batch * no), 256, 0, c->st>>>(c->act[L], batch, no, c->out_mean, c->out_std, c->out_lo,
+                                                         c->out_hi, c->yb);
     c->launches += 2;
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(y, c->yb, sizeof(float) * batch * no, cudaMemcpyDeviceToHost, c->st));
@@ -478,7 +500,8 @@ cudaError_t mlp_forward_device(dacp_mlp c, const float* feats, int B, float* out
     c->st = st;
     gather_norm_kernel<<<grid1(B * ni), 256, 0, st>>>(feats, nullptr, B, ni, c->in_mean, c->in_std, c->act[0]);
     forward_dev(c, B);
-    denorm_kernel<<<grid1(B * no), 256, 0, st>>>(c->act[L], B, no, c->out_mean, c->out_std, out);
+    denorm_kernel<<<grid1(B * no), 256, 0, st>>>(c->act[L], B, no, c->out_mean, c->out_std, c->out_lo, c->out_hi,
+                                                 out);
     c->st = keep;
     if (launches) *launches += L + 2;
     return cudaGetLastError();

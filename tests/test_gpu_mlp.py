@@ -59,6 +59,24 @@ def test_normalisation_is_applied():
         P.dacp_mlp_destroy(m)
 
 
+def test_output_range_clamps_outputs():
+    """dacp_mlp_set_output_range: each denormalised output is clamped to [lo, hi];
+    inside the range the outputs are unchanged; lo > hi is rejected."""
+    m, params = _net(seed=3)
+    try:
+        x = np.random.default_rng(4).standard_normal((64, 40)).astype(np.float32)
+        y0 = P.dacp_mlp_forward(m, x, 3)
+        lo = np.quantile(y0, 0.25, axis=0).astype(np.float32)
+        hi = np.quantile(y0, 0.75, axis=0).astype(np.float32)
+        P.dacp_mlp_set_output_range(m, lo, hi)
+        y = P.dacp_mlp_forward(m, x, 3)
+        assert np.array_equal(y, np.clip(y0, lo, hi))
+        with pytest.raises(P.DacpError):
+            P.dacp_mlp_set_output_range(m, hi + 1.0, lo)
+    finally:
+        P.dacp_mlp_destroy(m)
+
+
 def test_one_full_batch_adam_step_matches_oracle():
     m, params = _net(seed=5)
     try:
