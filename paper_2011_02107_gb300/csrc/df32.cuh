@@ -103,12 +103,18 @@ __device__ __forceinline__ df32 dot2_final(Dot2 acc) { return df_fast_two_sum(ac
 template <typename T> struct Accum {
     using type = T;
     __device__ static T zero() { return T(0); }
+    __device__ static T prod(T a, T b) { return a * b; }
     __device__ static void mad(T& acc, T a, T b) { acc = fma(a, b, acc); }
     __device__ static T final(T acc) { return acc; }
 };
 template <> struct Accum<df32> {
     using type = Dot2;
     __device__ static Dot2 zero() { return dot2_zero(); }
+    // an accumulator started at a * b: the exact TwoProduct and the cross terms
+    __device__ static Dot2 prod(df32 a, df32 b) {
+        const df32 p = df_two_prod(a.hi, b.hi);
+        return Dot2{p.hi, __fadd_rn(p.lo, __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi)))};
+    }
     __device__ static void mad(Dot2& acc, df32 a, df32 b) { dot2_mad(acc, a, b); }
     __device__ static df32 final(Dot2 acc) { return dot2_final(acc); }
 };

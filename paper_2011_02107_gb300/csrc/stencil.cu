@@ -220,6 +220,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
     if (MODE != kApply && a.nsteps_override > 0) nsteps = a.nsteps_override;
     const bool active = step < nsteps;
     const bool want_mom = (MODE == kEvolve) || (MODE == kApply && a.apply_moments);
+    constexpr bool kSymOX = MODE == kEvolve;     // <w_{k+1}, w_k> symmetric in the columns
 
     using MO = MomOps<T>;
     using AC = Accum<T>;
@@ -261,7 +262,8 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
         const int64_t gbase = R.off * B;                                  // first value of the realization
         const T* xg = x + gbase;
         const T* dg = static_cast<const T*>(a.diag) + R.off;
-        if (tid < R.N) gam_s[tid] = static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
+        // c_h folds into the x-fields and the diagonal: acc = c_h H x directly
+        if (tid < R.N) gam_s[tid] = ch * static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
 
         if (tstates >= SU) {
             // ---- unit path: stage the tile with one bulk copy -------------------
@@ -296,7 +298,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                         if (kEarlyY && use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
                         if (kEarlyY && use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
 #pragma unroll
-                        for (int j = 0; j < SU; ++j) dv[k][j] = ld_ro(dg + s0 + j);
+                        for (int j = 0; j < SU; ++j) dv[k][j] = ch * ld_ro(dg + s0 + j);
                     }
                 }
 #pragma unroll
@@ -304,10 +306,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                     for (int j = 0; j < SU; ++j)
 #pragma unroll
-                        for (int p = 0; p < B; ++p) {
-                            acc[k][j * B + p] = AC::zero();
-                            AC::mad(acc[k][j * B + p], dv[k][j], xv[k][j * B + p]);
-                        }
+                        for (int p = 0; p < B; ++p) acc[k][j * B + p] = AC::prod(dv[k][j], xv[k][j * B + p]);
                 // flips inside the unit
 #pragma unroll
                 for (int i = 0; i < LS; ++i) {
@@ -377,8 +376,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     T o[VU];
 #pragma unroll
                     for (int v = 0; v < VU; ++v) {
-                        typename AC::type t = AC::zero();
-                        AC::mad(t, ch, AC::final(acc[k][v]));
+                        typename AC::type t = acc[k][v];
                         if (use1) AC::mad(t, c1, yv[k][v]);
                         if (use2) AC::mad(t, c2, zv[k][v]);
                         o[v] = AC::final(t);
@@ -393,9 +391,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                                 for (int q = 0; q < B; ++q) {
                                     const T xq = xv[k][j * B + q];
-                                    // <x_p, x_q> is symmetric: only q >= p is accumulated
+                                    // <x_p, x_q> is symmetric, and so is <T_{k+1} psi_p, T_k psi_q>
+                                    // (T_{k+1} T_k is a symmetric polynomial in H): only q >= p
                                     if (q >= p) MO::mad(xx[p][q], xv[k][j * B + p], xq);
-                                    MO::mad(ox[p][q], o[j * B + p], xq);
+                                    if (q >= p || !kSymOX) MO::mad(ox[p][q], o[j * B + p], xq);
                                 }
                     }
                 }
@@ -408,7 +407,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                 const int64_t s = tile0 + sl;
                 T xv[B], acc[B];
                 load_vals<T, B>(tile + sl * B, xv);
-                const T d = dg[s];
+                const T d = ch * dg[s];
 #pragma unroll
                 for (int p = 0; p < B; ++p) acc[p] = d * xv[p];
                 for (int i = 0; i < R.tbits; ++i) {
@@ -420,7 +419,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                 T o[B];
 #pragma unroll
                 for (int p = 0; p < B; ++p) {
-                    T t = ch * acc[p];
+                    T t = acc[p];
                     if (use1) t = fma(c1, COHERENT ? ld_cg(y1 + gbase + s * B + p) : y1[gbase + s * B + p], t);
                     if (use2) t = fma(c2, COHERENT ? ld_cg(y2 + gbase + s * B + p) : y2[gbase + s * B + p], t);
                     o[p] = t;
@@ -433,7 +432,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                         for (int q = 0; q < B; ++q) {
                             if (q >= p) MO::mad(xx[p][q], xv[p], xv[q]);
-                            MO::mad(ox[p][q], o[p], xv[q]);
+                            if (q >= p || !kSymOX) MO::mad(ox[p][q], o[p], xv[q]);
                         }
                 }
             }
@@ -448,7 +447,7 @@ reduce:
 #pragma unroll
             for (int q = 0; q < B; ++q) {
                 const double v1 = warp_sum(MO::to_double(xx[p < q ? p : q][p < q ? q : p]));
-                const double v2 = warp_sum(MO::to_double(ox[p][q]));
+                const double v2 = warp_sum(MO::to_double(kSymOX ? ox[p < q ? p : q][p < q ? q : p] : ox[p][q]));
                 if (lane == 0) { red_s[warp][p * B + q] = v1; red_s[warp][B * B + p * B + q] = v2; }
             }
         __syncthreads();
