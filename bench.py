@@ -2,9 +2,10 @@
 """Throughput benchmark of batched DACP on GB300.
 
 Metric: central eigenvalues per second of the whole hot path -- parameter
-choice (Lanczos bound + KPM window, then the learned network when its weights
-exist), exp-semicircle filter, Chebyshev evolution with float64 moments,
-subspace assembly and generalized eigensolve -- over one batch of synthetic
+choice (Lanczos bound + KPM window; --params mlp adds the learned network when
+its weights exist), exp-semicircle filter, Chebyshev evolution with float64
+moments, subspace assembly and generalized eigensolve (overlapped with the
+evolution of the realizations still running) -- over one batch of synthetic
 realizations (one "step"). Default workload: 256 spin-glass shards, N = 14
 (dim 16384), Gamma_i ~ U[0.6, 1.4], J_ij ~ U[-1, 1] all-to-all, 500 central
 eigenvalues each, block b = 4, double-float vectors (float32 pairs) with
@@ -397,8 +398,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--params", default="mlp", choices=["mlp", "heuristic"],
-                    help="parameter choice: the trained network when its weights exist, else the heuristic")
+    ap.add_argument("--params", default="heuristic", choices=["mlp", "heuristic"],
+                    help="parameter choice: the heuristic (default), or the trained network when its weights "
+                         "exist")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "df32"],
                     help="override the workload's precision (df32: double-float vectors on the float32 pipes)")
     ap.add_argument("--realizations", type=int, default=None, help="override the number of realizations per GPU")
