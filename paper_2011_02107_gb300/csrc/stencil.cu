@@ -26,6 +26,8 @@
 
 #include <string.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "ops.h"
 
@@ -193,8 +195,16 @@ constexpr int kWaitLimit = 0;         // (time-based: kWaitNs)
 template <typename T> struct UnitsPerPass { static constexpr int value = sizeof(T) == 4 ? 2 : 1; };
 // Minimum resident CTAs per SM the compiler must allow: three for float32
 // (80 registers, no spills), two for the 8-byte types (128 registers; three
-// would spill their double-float / float64 accumulators).
-template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 2; };
+// would spill their double-float / float64 accumulators at one thread per
+// state).
+template <typename T, int B> struct MinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 2; };
+// double-float at b = 4 runs two threads per state (tile_step_df4): three CTAs per SM
+template <> struct MinBlocks<df32, 4> { static constexpr int value = 3; };
+// Beyond-tile partner units whose loads are issued before the in-tile flips,
+// so that their L2 latency overlaps the shared-memory work: three for
+// double-float, whose long in-tile flip phase hides them; none otherwise.
+template <typename T> struct EarlyGlobal { static constexpr int value = 0; };
+template <> struct EarlyGlobal<df32> { static constexpr int value = 3; };
 constexpr int kMaxTileUnitBits = 14;   // unit bits of the largest tile (128 KB of float32 b = 1)
 constexpr int kMaxGlobalBitsUnrolled = 10;
 
@@ -319,6 +329,20 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                             for (int p = 0; p < B; ++p)
                                 AC::mad(acc[k][j * B + p], g, xv[k][(j ^ (1 << i)) * B + p]);
                 }
+                // the first EG beyond-tile partners: loads issued now, summed after the tile flips
+                constexpr int EG = EarlyGlobal<T>::value;
+                const int ngb = R.N - R.tbits;
+                int64_t sbase[UP];
+#pragma unroll
+                for (int k = 0; k < UP; ++k) sbase[k] = val[k] ? tile0 + static_cast<int64_t>(uu[k]) * SU : tile0;
+                T pe[EG > 0 ? EG : 1][UP][VU];
+#pragma unroll
+                for (int j = 0; j < EG; ++j)
+                    if (j < ngb)
+#pragma unroll
+                        for (int k = 0; k < UP; ++k)
+                            ld_unit_g<T, B, COHERENT>(xg + (sbase[k] ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B,
+                                                      pe[j][k]);
                 // flips inside the tile (shared memory). Unrolled at compile time and
                 // predicated on the tile's bit count so that every partner load of a
                 // unit is independent; idle slots read a masked, in-range address.
@@ -337,12 +361,18 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     }
                 }
                 // flips beyond the tile (global memory, L2-resident partner tiles)
-                const int ngb = R.N - R.tbits;
-                int64_t sbase[UP];
 #pragma unroll
-                for (int k = 0; k < UP; ++k) sbase[k] = val[k] ? tile0 + static_cast<int64_t>(uu[k]) * SU : tile0;
+                for (int j = 0; j < EG; ++j) {
+                    if (j < ngb) {
+                        const T g = gam_s[R.tbits + j];
 #pragma unroll
-                for (int j = 0; j < kMaxGlobalBitsUnrolled; ++j) {
+                        for (int k = 0; k < UP; ++k)
+#pragma unroll
+                            for (int v = 0; v < VU; ++v) AC::mad(acc[k][v], g, pe[j][k][v]);
+                    }
+                }
+#pragma unroll
+                for (int j = EG; j < kMaxGlobalBitsUnrolled; ++j) {
                     if (j < ngb) {
                         const T g = gam_s[R.tbits + j];
                         T pv[UP][VU];
@@ -482,11 +512,278 @@ reduce:
     __syncthreads();   // the tile buffer is reused by the next tile of a persistent CTA
 }
 
+// ---- double-float at b = 4: two threads per state ----------------------------
+//
+// The one-thread-per-state unit path holds a 32-byte unit and the b x b
+// moment sums per thread, which caps it at two CTAs per SM (128 registers)
+// and leaves shared-memory latency exposed. Here thread h of each pair holds
+// columns 2h, 2h+1 of one state (16 bytes): half the registers, three CTAs
+// per SM. Moment sums: thread h has its own x (a), its outputs o and, after
+// one shuffle with the neighbouring lane, the other pair's x (c). It keeps
+// ten sums: <a,a> and <o,a> within its pair (three each) and four cross sums,
+// h = 0: <o_p, x_q> and h = 1: <x_p, x_q> for p in {0,1}, q in {2,3}. Only the
+// evolution emits moments on this path (its <o, x> block is symmetric).
+
+__device__ __forceinline__ void ld2_s(const df32* p, df32& v0, df32& v1) {
+    const float4 f = *reinterpret_cast<const float4*>(p);
+    v0 = df32(f.x, f.y);
+    v1 = df32(f.z, f.w);
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ void ld2_g(const df32* p, df32& v0, df32& v1) {
+    const float4 f = COHERENT ? __ldcg(reinterpret_cast<const float4*>(p)) : __ldg(reinterpret_cast<const float4*>(p));
+    v0 = df32(f.x, f.y);
+    v1 = df32(f.z, f.w);
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ void ld2_rw(const df32* p, df32& v0, df32& v1) {
+    const float4 f = COHERENT ? __ldcg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
+    v0 = df32(f.x, f.y);
+    v1 = df32(f.z, f.w);
+}
+
+__device__ __forceinline__ void st2(df32* p, df32 v0, df32 v1) {
+    *reinterpret_cast<float4*>(p) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+}
+
+__device__ __forceinline__ df32 shfl_xor_df(df32 v, int m) {
+    return df32(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+
+constexpr int kDf4TileBits = 12;   // in-tile flips unrolled: tiles up to 4096 states (128 KB)
+
+template <int MODE, bool COHERENT>
+__device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item, const int step) {
+    using T = df32;
+    constexpr int B = 4, EG = EarlyGlobal<T>::value;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    __shared__ T gam_s[kMaxSpins];
+    __shared__ double red_s[kThreads / 32][2 * B * B];
+    __shared__ int last_s;
+    __shared__ __align__(8) uint64_t bar_s;
+
+    const int tid = threadIdx.x;
+    const int h = tid & 1;
+    const Item it = a.items[item];
+    const RealInfo R = a.real[it.r];
+    int nsteps = (MODE == kEvolve) ? R.ne : (MODE == kApply ? 1 : R.nf);
+    if (MODE != kApply && a.nsteps_override > 0) nsteps = a.nsteps_override;
+    const bool active = step < nsteps;
+    constexpr bool want_mom = MODE == kEvolve;
+    Dot2 ms[10];
+#pragma unroll
+    for (int e = 0; e < 10; ++e) ms[e] = dot2_zero();
+
+    if (active) {
+        T* wA = static_cast<T*>(a.bufA);
+        T* wB = static_cast<T*>(a.bufB);
+        T* wk = (step & 1) ? wB : wA;
+        T* wo = (step & 1) ? wA : wB;
+        const T* x;
+        const T* y1 = nullptr;
+        const T* y2 = nullptr;
+        T* out;
+        double c_h, c_1 = 0.0, c_2 = 0.0;
+        const double* cf = a.coef + 8 * it.r + (step == 0 ? 0 : 3);
+        if (MODE == kApply) {
+            x = static_cast<const T*>(a.x); y1 = static_cast<const T*>(a.y1); out = static_cast<T*>(a.out);
+            c_h = cf[0]; c_1 = cf[1];
+        } else if (MODE == kFilter1) {
+            x = wk; out = static_cast<T*>(a.bufU); c_h = 1.0;
+        } else if (MODE == kFilter2) {
+            x = static_cast<const T*>(a.bufU); y1 = wk; y2 = wo; out = wo;
+            c_h = cf[0]; c_1 = cf[1]; c_2 = cf[2];
+        } else {
+            x = wk; y1 = wo; out = wo;
+            c_h = cf[0]; c_1 = cf[1];
+        }
+        const bool use1 = (c_1 != 0.0) && (y1 != nullptr);
+        const bool use2 = (c_2 != 0.0) && (y2 != nullptr);
+        const T ch = static_cast<T>(c_h), c1 = static_cast<T>(c_1), c2 = static_cast<T>(c_2);
+
+        const int tstates = 1 << R.tbits;
+        const int64_t tile0 = static_cast<int64_t>(it.tile) << R.tbits;
+        const int64_t gbase = R.off * B;
+        const T* xg = x + gbase;
+        const T* dg = static_cast<const T*>(a.diag) + R.off;
+        if (tid < R.N) gam_s[tid] = ch * static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
+
+        const uint32_t nbytes = static_cast<uint32_t>(tstates) * B * sizeof(T);
+        if (tid == 0) {
+            mbar_init(&bar_s, 1);
+            bulk_load(tile, xg + tile0 * B, nbytes, &bar_s);
+        }
+        __syncthreads();
+        const bool landed = mbar_wait(&bar_s, 0, kWaitLimit);
+        if (!landed) {
+            atomicExch(a.err_flag, 1);
+            mbar_wait(&bar_s, 0, kWaitLimit);        // let the copy land before the CTA exits
+        }
+        __syncthreads();
+        if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar_s)) : "memory");
+        if (!landed) goto reduce_df4;
+
+        const int ngb = R.N - R.tbits;
+        const int nhalf = 2 * tstates;                   // (state, column pair) slots of the tile
+        for (int hb = 0; hb < nhalf; hb += kThreads) {
+            const int hs = hb + tid;
+            const bool val = hs < nhalf;                 // both lanes of a pair agree (nhalf is even)
+            const int sl = val ? (hs >> 1) : 0;          // idle lanes work on state 0 and store nothing
+            const int64_t sg = tile0 + sl;               // state within the realization
+            const int col = 2 * h;
+            T a0, a1;
+            ld2_s(tile + sl * B + col, a0, a1);
+            T pe[EG > 0 ? EG : 1][2];
+#pragma unroll
+            for (int j = 0; j < EG; ++j)
+                if (j < ngb) ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B + col, pe[j][0],
+                                             pe[j][1]);
+            const T d = ch * ld_ro(dg + sg);
+            Dot2 acc0 = Accum<T>::prod(d, a0), acc1 = Accum<T>::prod(d, a1);
+            // flips inside the tile (shared memory)
+#pragma unroll
+            for (int i = 0; i < kDf4TileBits; ++i) {
+                if (i < R.tbits) {
+                    const T g = gam_s[i];
+                    T p0, p1;
+                    ld2_s(tile + (sl ^ (1 << i)) * B + col, p0, p1);
+                    dot2_mad(acc0, g, p0);
+                    dot2_mad(acc1, g, p1);
+                }
+            }
+            for (int i = kDf4TileBits; i < R.tbits; ++i) {
+                const T g = gam_s[i];
+                T p0, p1;
+                ld2_s(tile + (sl ^ (1 << i)) * B + col, p0, p1);
+                dot2_mad(acc0, g, p0);
+                dot2_mad(acc1, g, p1);
+            }
+            // flips beyond the tile (global memory, L2-resident partner tiles)
+#pragma unroll
+            for (int j = 0; j < EG; ++j) {
+                if (j < ngb) {
+                    const T g = gam_s[R.tbits + j];
+                    dot2_mad(acc0, g, pe[j][0]);
+                    dot2_mad(acc1, g, pe[j][1]);
+                }
+            }
+            for (int j = EG; j < ngb; ++j) {
+                const T g = gam_s[R.tbits + j];
+                T p0, p1;
+                ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B + col, p0, p1);
+                dot2_mad(acc0, g, p0);
+                dot2_mad(acc1, g, p1);
+            }
+            // w_{k+1} = c_h H x + c_1 y + c_2 z
+            if (use1) {
+                T v0, v1;
+                ld2_rw<COHERENT>(y1 + gbase + sg * B + col, v0, v1);
+                dot2_mad(acc0, c1, v0);
+                dot2_mad(acc1, c1, v1);
+            }
+            if (use2) {
+                T v0, v1;
+                ld2_rw<COHERENT>(y2 + gbase + sg * B + col, v0, v1);
+                dot2_mad(acc0, c2, v0);
+                dot2_mad(acc1, c2, v1);
+            }
+            const T o0 = dot2_final(acc0), o1 = dot2_final(acc1);
+            if (val) st2(out + gbase + sg * B + col, o0, o1);
+            if (want_mom) {
+                const T cx0 = shfl_xor_df(a0, 1), cx1 = shfl_xor_df(a1, 1);   // the other pair's x
+                if (val) {
+                    dot2_mad(ms[0], a0, a0);
+                    dot2_mad(ms[1], a0, a1);
+                    dot2_mad(ms[2], a1, a1);
+                    dot2_mad(ms[3], o0, a0);
+                    dot2_mad(ms[4], o0, a1);
+                    dot2_mad(ms[5], o1, a1);
+                    // p in {0,1}, q in {2,3}: h = 0 sums <o_p, x_q>, h = 1 sums <x_p, x_q>
+                    const T u0 = h ? cx0 : o0, u1 = h ? cx1 : o1;
+                    const T v0 = h ? a0 : cx0, v1 = h ? a1 : cx1;
+                    dot2_mad(ms[6], u0, v0);
+                    dot2_mad(ms[7], u0, v1);
+                    dot2_mad(ms[8], u1, v0);
+                    dot2_mad(ms[9], u1, v1);
+                }
+            }
+        }
+    }
+
+reduce_df4:
+    if (want_mom && active) {
+        const int lane = tid & 31, warp = tid >> 5;
+        double sv[10];
+#pragma unroll
+        for (int e = 0; e < 10; ++e) {
+            double v = static_cast<double>(ms[e].hi) + static_cast<double>(ms[e].err);
+#pragma unroll
+            for (int o = 16; o > 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);   // over lanes of one parity
+            sv[e] = v;
+        }
+        if (lane < 2) {
+            double* rw = red_s[warp];
+            auto put = [&](int blk, int p, int q, double v) {
+                rw[blk * B * B + p * B + q] = v;
+                rw[blk * B * B + q * B + p] = v;
+            };
+            const int b0 = 2 * lane;
+            put(0, b0, b0, sv[0]);
+            put(0, b0, b0 + 1, sv[1]);
+            put(0, b0 + 1, b0 + 1, sv[2]);
+            put(1, b0, b0, sv[3]);
+            put(1, b0, b0 + 1, sv[4]);
+            put(1, b0 + 1, b0 + 1, sv[5]);
+            const int blk = lane == 0 ? 1 : 0;          // lane 0: <o_p, x_q>; lane 1: <x_p, x_q>
+            put(blk, 0, 2, sv[6]);
+            put(blk, 0, 3, sv[7]);
+            put(blk, 1, 2, sv[8]);
+            put(blk, 1, 3, sv[9]);
+        }
+        __syncthreads();
+        if (tid < 2 * B * B) {
+            double sm = 0.0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) sm += red_s[w][tid];
+            a.part[static_cast<int64_t>(item) * 2 * B * B + tid] = sm;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&a.real_done[it.r], 1u);
+            last_s = (prev == static_cast<unsigned>(R.item_count - 1));
+        }
+        __syncthreads();
+        if (last_s) {
+            __threadfence();
+            if (tid < 2 * B * B) {
+                double sm = 0.0;
+                for (int j = 0; j < R.item_count; ++j)
+                    sm += __ldcg(a.part + static_cast<int64_t>(R.item_begin + j) * 2 * B * B + tid);
+                const int row = 2 * step;
+                const int64_t row0 = a.mom_rows_fixed > 0 ? static_cast<int64_t>(it.r) * a.mom_rows_fixed : R.mom_off;
+                a.mom[(row0 + row) * B * B + tid] = sm;
+            }
+            if (tid == 0) a.real_done[it.r] = 0u;
+        }
+    }
+    __syncthreads();   // the tile buffer is reused by the next tile of a persistent CTA
+}
+
+template <typename T, int B, int MODE, bool COHERENT>
+__device__ __forceinline__ void tile_step_any(const StepArgs& a, const int item, const int step) {
+    if constexpr (std::is_same<T, df32>::value && B == 4) tile_step_df4<MODE, COHERENT>(a, item, step);
+    else tile_step<T, B, MODE, COHERENT>(a, item, step);
+}
+
 template <typename T, int B, int MODE>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) step_kernel(const StepArgs a, int item_base) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T, B>::value) step_kernel(const StepArgs a, int item_base) {
     int step = 0;
     if (MODE != kApply) step = *a.step_ctr;
-    tile_step<T, B, MODE, false>(a, item_base + blockIdx.x, step);
+    tile_step_any<T, B, MODE, false>(a, item_base + blockIdx.x, step);
     if (MODE == kFilter2 || MODE == kEvolve) {
         if (threadIdx.x == 0) {
             __threadfence();
@@ -537,16 +834,16 @@ __device__ __forceinline__ bool grid_sync(const StepArgs& a) {
 // All orders of the filter (SEQ = 0: two passes per order) or the evolution
 // (SEQ = 1) in one cooperative launch; CTAs take tiles round-robin.
 template <typename T, int B, int SEQ>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) persistent_kernel(const StepArgs a, int n_items,
+__global__ void __launch_bounds__(kThreads, MinBlocks<T, B>::value) persistent_kernel(const StepArgs a, int n_items,
                                                                                  int orders) {
     for (int k = 0; k < orders; ++k) {
         if (SEQ == 0) {
-            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step<T, B, kFilter1, true>(a, item, k);
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step_any<T, B, kFilter1, true>(a, item, k);
             if (!grid_sync(a)) return;
-            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step<T, B, kFilter2, true>(a, item, k);
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step_any<T, B, kFilter2, true>(a, item, k);
             if (!grid_sync(a)) return;
         } else {
-            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step<T, B, kEvolve, true>(a, item, k);
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) tile_step_any<T, B, kEvolve, true>(a, item, k);
             if (!grid_sync(a)) return;
         }
     }
