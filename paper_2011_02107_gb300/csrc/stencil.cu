@@ -230,7 +230,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
     if (MODE != kApply && a.nsteps_override > 0) nsteps = a.nsteps_override;
     const bool active = step < nsteps;
     const bool want_mom = (MODE == kEvolve) || (MODE == kApply && a.apply_moments);
-    constexpr bool kSymOX = MODE == kEvolve;     // <w_{k+1}, w_k> symmetric in the columns
+    // <w_{k+1}, w_k> is symmetric in the columns; float32 storage rounding makes
+    // the computed block asymmetric at 1e-7, and averaging both triangles (the
+    // moments kernel symmetrises) halves that noise, so float32 keeps both.
+    constexpr bool kSymOX = MODE == kEvolve && sizeof(T) != 4;
 
     using MO = MomOps<T>;
     using AC = Accum<T>;
