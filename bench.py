@@ -69,7 +69,9 @@ def make_inputs(wl, rank=0):
 
 # float32 instructions per double-float fused multiply-add in the library's
 # arithmetic (TwoProduct 2, cross terms 2, TwoSum 6, folding 3, Fast2Sum 3)
-DF_FMA_INSTR = 16
+# One error-free double-float multiply-add (the Dot2 step): TwoProduct 2,
+# cross terms 2, TwoSum 6, error adds 3 float32 instructions.
+DF_FMA_INSTR = 13
 SMS, FP32_LANES_PER_SM = 152, 128
 
 
@@ -79,11 +81,13 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk):
     float32: HBM-bound; algorithmic bytes = 3 * 2^N * b * 4 per order (read
     w_k, read w_{k-1}, write w_{k+1}) against the measured copy bandwidth.
     double-float: float32-issue bound; algorithmic work per state and order =
-    (N b flips + b diagonal + 2b recurrence + b(b+1)/2 + b^2 moment products)
-    double-float FMAs x DF_FMA_INSTR float32 instructions, against
-    152 SMs x 128 lanes x the SM clock sampled during the run.
-    float64: FP64-pipe bound; same FMA count against the measured float64
-    dgemm rate (1.10 TFLOP/s = 0.55 T FMA/s on this GB300).
+    (N b flips + b diagonal + b recurrence + b(b+1)/2 <w_k, w_k> + b(b+1)/2
+    <w_{k+1}, w_k> products; c_h is folded into the fields and both moment
+    blocks are symmetric) double-float multiply-adds x DF_FMA_INSTR float32
+    instructions, against 152 SMs x 128 lanes x the SM clock sampled during
+    the run.
+    float64: FP64-pipe bound; same multiply-add count against the measured
+    float64 dgemm rate (1.10 TFLOP/s = 0.55 T FMA/s on this GB300).
     """
     peaks = {}
     try:
@@ -94,7 +98,7 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk):
     t_e = phase[1] / 1e3
     b = wl["b"]
     N = wl["N"]
-    fma_per_state = N * b + 3 * b + b * (b + 1) // 2 + b * b
+    fma_per_state = N * b + 2 * b + b * (b + 1)
     kern = {"fp32": "step_kernel<float,4,kEvolve>", "df32": "step_kernel<df32,4,kEvolve>",
             "fp64": "step_kernel<double,4,kEvolve>"}[wl["prec"]]
     if wl["prec"] == "fp32":
