@@ -187,6 +187,25 @@ dacp_status dacp_get_moments(dacp_handle hd, int r, double* mu, int64_t cap, int
 dacp_status dacp_residuals(dacp_handle hd, int r, int n_eigs, double window, double eps, double* eigs,
                            double* resid, int* n_found);
 
+/*
+ * dacp_eigenvectors -- the central levels of realization r and their Ritz
+ * vectors phi_j = sum_(i,p) b_j[i,p] T_{x_i}(G) psi_p (Appendix C: the
+ * eigenvectors of H B = S B Lambda mapped back to the Hilbert space), the
+ * eigenvector half of the error check of Sec. II C. The evolution of r is
+ * replayed on the GPU and the 2n+1 basis orders T_{x_i}(G) psi_E are kept
+ * as one float64 matrix V (2^N x b(2n+1)); Phi = V B_sel is one dgemm.
+ *   r, n_eigs, window, eps  as in dacp_residuals (same selection).
+ *   eigs     host array of n_eigs doubles (ascending).
+ *   phi_dev  device array, column-major 2^N x n_found float64 with leading
+ *            dimension ld >= 2^N, 8-byte aligned; column j is phi_j, with
+ *            b_j^T S b_j = 1, i.e. unit norm up to rounding. Caller-owned.
+ *   n_found  count written, or -dacp_status for a failed realization.
+ * Workspace: V (8 * 2^N * b(2n+1) bytes) plus O(M^2), allocated and freed
+ * here. Needs dacp_basis_moments first (else DACP_ERR_STATE).
+ */
+dacp_status dacp_eigenvectors(dacp_handle hd, int r, int n_eigs, double window, double eps, double* eigs,
+                              double* phi_dev, int64_t ld, int* n_found);
+
 /* dacp_get_filtered -- copy realization r's psi_E (2^N_r x b, float64) into
  * psi (capacity cap doubles). Test hook. */
 dacp_status dacp_get_filtered(dacp_handle hd, int r, double* psi, int64_t cap);

@@ -29,7 +29,7 @@ _STATUS = {0: "DACP_OK", 1: "DACP_ERR_ARG", 2: "DACP_ERR_CUDA", 3: "DACP_ERR_NOM
            5: "DACP_ERR_TIMEOUT", 6: "DACP_ERR_STATE", 7: "DACP_ERR_NOT_CONVERGED", 8: "DACP_ERR_LIBRARY"}
 
 EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_params", "dacp_filter",
-           "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered", "dacp_residuals", "dacp_solve",
+           "dacp_basis_moments", "dacp_central_eigs", "dacp_get_moments", "dacp_get_filtered", "dacp_residuals", "dacp_solve", "dacp_eigenvectors",
            "dacp_apply_h", "dacp_get_timings", "dacp_get_launch_count", "dacp_last_error", "dacp_status_string",
            "dacp_destroy", "dacp_mlp_create", "dacp_mlp_set_normalization", "dacp_mlp_set_output_range", "dacp_mlp_get_weights",
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
@@ -70,6 +70,7 @@ def _load():
         "dacp_get_filtered": [P, I, P, L],
         "dacp_residuals": [P, I, I, D, D, P, P, P],
         "dacp_solve": [P, I, D, D, P, P, P],
+        "dacp_eigenvectors": [P, I, I, D, D, P, P, L, P],
         "dacp_apply_h": [P, I, P, P],
         "dacp_get_timings": [P, P],
         "dacp_get_launch_count": [P, ctypes.POINTER(L)],
@@ -207,6 +208,16 @@ def dacp_residuals(hd, r, n_eigs, window=0.0, eps=0.0):
                                    ctypes.byref(nf)))
     n = max(nf.value, 0)
     return eigs[:n], resid[:n], nf.value
+
+
+def dacp_eigenvectors(hd, r, n_eigs, phi_dev_ptr, ld, window=0.0, eps=0.0):
+    """Central levels of r and their Ritz vectors into the device buffer at
+    phi_dev_ptr (column-major, leading dimension ld); returns (eigs, n_found)."""
+    eigs = np.zeros(n_eigs)
+    nf = ctypes.c_int(0)
+    _check(hd, _lib.dacp_eigenvectors(hd, int(r), int(n_eigs), float(window), float(eps), _ptr(eigs),
+                                      ctypes.c_void_p(phi_dev_ptr), int(ld), ctypes.byref(nf)))
+    return eigs[:max(nf.value, 0)], nf.value
 
 
 def dacp_apply_h(hd, r, x_dev_ptr, y_dev_ptr):
@@ -459,6 +470,17 @@ class Dacp:
     def residuals(self, r, n_eigs, window=0.0, eps=0.0):
         """Central levels of realization r and their residual norms (Sec. II C)."""
         return dacp_residuals(self.handle, r, n_eigs, window, eps)
+
+    def eigenvectors(self, r, n_eigs, window=0.0, eps=0.0):
+        """Central levels of r and their Ritz vectors (torch float64 tensor on the
+        device, 2^N x n_found)."""
+        import torch
+        D = 1 << self.N[r]
+        phi = torch.empty((n_eigs, D), dtype=torch.float64, device="cuda")   # column-major D x n_eigs
+        torch.cuda.synchronize()                   # the library writes it on its own stream
+        eigs, nf = dacp_eigenvectors(self.handle, r, n_eigs, phi.data_ptr(), D, window, eps)
+        torch.cuda.synchronize()
+        return eigs, phi[:max(nf, 0)].T, nf
 
     def filtered(self, r):
         n = (1 << self.N[r]) * self.b

@@ -1453,6 +1453,118 @@ dacp_status dacp_get_filtered(dacp_handle c, int r, double* psi, int64_t cap) {
     return s;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Selected Ritz pairs of realization r (device): the coefficients
+// Bsel = U Y[:, first:first+cnt] (M x cnt, column-major) of the Ritz vectors
+// phi_j = sum_(i,p) Bsel[i*b+p, j] T_{x_i}(G) psi_p, their eigenvalues lam
+// (cnt, ascending) and, when want_h2, the H^2 matrix H2 (M x M) assembled
+// from omega_k = <psi|H^2 T_k|psi>. cnt < 0 is -dacp_status of a failed
+// realization. The buffers are the caller's to free (ritz_free).
+struct Ritz {
+    int M = 0, cnt = 0;
+    double *Bsel = nullptr, *lam = nullptr, *H2 = nullptr;
+    std::vector<void*> tmp;
+};
+
+void ritz_free(dacp_ctx* c, Ritz& z) {
+    cudaStreamSynchronize(c->st);
+    for (void* p : z.tmp) dfree(c, p);
+    z = Ritz();
+}
+
+dacp_status ritz_select(dacp_ctx* c, int r, int n_eigs, double window, double eps, bool want_h2, Ritz& z) {
+    const int b = c->b, Ln = 2 * c->n[r] + 1, M = b * Ln;
+    const int rows = 2 * c->kn[r] + 4;          // mu_0 .. mu_{2 k_n + 3}
+    const int64_t bb = static_cast<int64_t>(b) * b, MM = static_cast<int64_t>(M) * M;
+    z.M = M;
+    auto get = [&](auto** p, size_t count) -> dacp_status {
+        TRY(dalloc_t(c, p, count));
+        z.tmp.push_back(*p);
+        return DACP_OK;
+    };
+    double *mus, *nus, *om, *S, *H, *W, *Ht, *lam, *lamt;
+    int *orders, *ints;
+    TRY(get(&mus, static_cast<size_t>(rows * bb)));
+    TRY(get(&nus, static_cast<size_t>(rows * bb)));
+    TRY(get(&S, static_cast<size_t>(MM)));
+    TRY(get(&H, static_cast<size_t>(MM)));
+    TRY(get(&W, static_cast<size_t>(MM)));
+    TRY(get(&Ht, static_cast<size_t>(MM)));
+    TRY(get(&lam, M));
+    TRY(get(&lamt, M));
+    TRY(get(&orders, Ln));
+    TRY(get(&ints, 8));                          // bad, m, info, first, count
+    if (want_h2) {
+        TRY(get(&om, static_cast<size_t>(rows * bb)));
+        TRY(get(&z.H2, static_cast<size_t>(MM)));
+    }
+    size_t d1 = 0, h1 = 0;
+    CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, S,
+                                    M, CUDA_R_64F, lam, CUDA_R_64F, &d1, &h1));
+    void* work = nullptr;
+    TRY(dalloc(c, &work, std::max<size_t>(d1, 8)));
+    z.tmp.push_back(work);
+    std::vector<char> work_h(std::max<size_t>(h1, 1));
+    CK(cudaMemsetAsync(ints, 0, 8 * sizeof(int), c->st));
+    CK(launch_orders(Ln, c->a[r] / c->emax[r], orders, c->st));
+    CK(launch_moments(c->mom_d + c->info[r].mom_off * bb, rows, b, c->emax[r], mus, nus, ints + 0, c->st));
+    CK(launch_assemble(Ln, b, orders, mus, nus, S, H, c->st));
+    if (want_h2) {
+        // H2 from omega (S is written again with the same values)
+        CK(launch_omega(mus, rows - 2, b, c->emax[r], om, c->st));
+        CK(launch_assemble(Ln, b, orders, mus, om, S, z.H2, c->st));
+    }
+    CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, S, M,
+                         CUDA_R_64F, lam, CUDA_R_64F, work, d1, work_h.data(), h1, ints + 2));
+    CK(launch_cutoff(lam, M, eps, 0, S, ints + 1, c->st));
+    c->launches += want_h2 ? 6 : 4;
+    int hv[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(hv, ints, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (hv[0]) { z.cnt = -DACP_ERR_NUMERIC; return DACP_OK; }
+    if (hv[2] != 0 || hv[1] < 1) { z.cnt = -DACP_ERR_NOT_CONVERGED; return DACP_OK; }
+    const int m = hv[1];
+    const double* U = S + static_cast<int64_t>(M - m) * M;
+    const double one = 1.0, zero = 0.0;
+    CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m, M, &one, H, M, U, M, &zero, W, M));
+    CKB(cublasDgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, M, &one, U, M, W, M, &zero, Ht, m));
+    size_t d2 = 0, h2 = 0;
+    CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, Ht,
+                                    m, CUDA_R_64F, lamt, CUDA_R_64F, &d2, &h2));
+    if (d2 > d1) {
+        CK(cudaStreamSynchronize(c->st));
+        TRY(dalloc(c, &work, d2));
+        z.tmp.push_back(work);
+        d1 = d2;
+    }
+    if (h2 > work_h.size()) work_h.resize(h2);
+    // H~ = Y diag(lamt) Y^T; Y overwrites Ht
+    CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, Ht, m,
+                         CUDA_R_64F, lamt, CUDA_R_64F, work, d1, work_h.data(), h2, ints + 2));
+    const double w = window > 0.0 ? window : c->a[r];
+    CK(launch_select_range(lamt, m, n_eigs, w, ints + 3, c->st));
+    c->launches += 1;
+    CK(cudaMemcpyAsync(hv, ints + 2, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (hv[0] != 0) { z.cnt = -DACP_ERR_NOT_CONVERGED; return DACP_OK; }
+    const int first = hv[1], cnt = hv[2];
+    z.cnt = cnt;
+    if (cnt < 1) return DACP_OK;
+    TRY(get(&z.Bsel, static_cast<size_t>(M) * cnt));
+    // b_j = U y_j for the selected columns of Y
+    CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, cnt, m, &one, U, M, Ht + static_cast<int64_t>(first) * m, m,
+                    &zero, z.Bsel, M));
+    z.lam = lamt + first;
+    return DACP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 dacp_status dacp_residuals(dacp_handle c, int r, int n_eigs, double window, double eps, double* eigs, double* resid,
                            int* n_found) {
     TRY(check_handle(c));
@@ -1460,98 +1572,103 @@ dacp_status dacp_residuals(dacp_handle c, int r, int n_eigs, double window, doub
     if (r < 0 || r >= c->R || n_eigs < 1 || !eigs || !resid || !n_found)
         return fail(c, DACP_ERR_ARG, "bad realization or output arguments");
     if (!(eps > 0.0)) eps = c->fp32 ? kEpsFp32 : (c->prec == kPrecDF32 ? kEpsDf32 : 1e-12);
-    const int b = c->b, Ln = 2 * c->n[r] + 1, M = b * Ln;
-    const int rows = 2 * c->kn[r] + 4;          // mu_0 .. mu_{2 k_n + 3}
-    const int64_t bb = static_cast<int64_t>(b) * b, MM = static_cast<int64_t>(M) * M;
-    double *mus = nullptr, *nus = nullptr, *om = nullptr, *S = nullptr, *H = nullptr, *H2 = nullptr, *W = nullptr,
-           *Ht = nullptr, *lam = nullptr, *lamt = nullptr, *Bsel = nullptr, *W2 = nullptr, *rs = nullptr;
-    int *orders = nullptr, *ints = nullptr;      // ints: bad, m, info, first, count
-    void* work = nullptr;
+    Ritz z;
     auto run = [&]() -> dacp_status {
-        TRY(dalloc_t(c, &mus, static_cast<size_t>(rows * bb)));
-        TRY(dalloc_t(c, &nus, static_cast<size_t>(rows * bb)));
-        TRY(dalloc_t(c, &om, static_cast<size_t>(rows * bb)));
-        TRY(dalloc_t(c, &S, static_cast<size_t>(MM)));
-        TRY(dalloc_t(c, &H, static_cast<size_t>(MM)));
-        TRY(dalloc_t(c, &H2, static_cast<size_t>(MM)));
-        TRY(dalloc_t(c, &W, static_cast<size_t>(MM)));
-        TRY(dalloc_t(c, &Ht, static_cast<size_t>(MM)));
-        TRY(dalloc_t(c, &lam, M));
-        TRY(dalloc_t(c, &lamt, M));
-        TRY(dalloc_t(c, &orders, Ln));
-        TRY(dalloc_t(c, &ints, 8));
-        size_t d1 = 0, h1 = 0;
-        CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F,
-                                        S, M, CUDA_R_64F, lam, CUDA_R_64F, &d1, &h1));
-        TRY(dalloc(c, &work, std::max<size_t>(d1, 8)));
-        std::vector<char> work_h(std::max<size_t>(h1, 1));
-        CK(cudaMemsetAsync(ints, 0, 8 * sizeof(int), c->st));
-        CK(launch_orders(Ln, c->a[r] / c->emax[r], orders, c->st));
-        CK(launch_moments(c->mom_d + c->info[r].mom_off * bb, rows, b, c->emax[r], mus, nus, ints + 0, c->st));
-        CK(launch_omega(mus, rows - 2, b, c->emax[r], om, c->st));
-        // S and H, then H2 from omega (S is written twice with the same values)
-        CK(launch_assemble(Ln, b, orders, mus, nus, S, H, c->st));
-        CK(launch_assemble(Ln, b, orders, mus, om, S, H2, c->st));
-        CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, CUDA_R_64F, S, M,
-                             CUDA_R_64F, lam, CUDA_R_64F, work, d1, work_h.data(), h1, ints + 2));
-        CK(launch_cutoff(lam, M, eps, 0, S, ints + 1, c->st));
-        c->launches += 6;
-        int hv[3] = {0, 0, 0};
-        CK(cudaMemcpyAsync(hv, ints, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        if (hv[0]) { *n_found = -DACP_ERR_NUMERIC; return DACP_OK; }
-        if (hv[2] != 0 || hv[1] < 1) { *n_found = -DACP_ERR_NOT_CONVERGED; return DACP_OK; }
-        const int m = hv[1];
-        const double* U = S + static_cast<int64_t>(M - m) * M;
-        const double one = 1.0, zero = 0.0;
-        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, m, M, &one, H, M, U, M, &zero, W, M));
-        CKB(cublasDgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, m, m, M, &one, U, M, W, M, &zero, Ht, m));
-        size_t d2 = 0, h2 = 0;
-        CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F,
-                                        Ht, m, CUDA_R_64F, lamt, CUDA_R_64F, &d2, &h2));
-        if (d2 > d1) {
-            CK(cudaStreamSynchronize(c->st));
-            dfree(c, work);
-            work = nullptr;
-            TRY(dalloc(c, &work, d2));
-            d1 = d2;
-        }
-        if (h2 > work_h.size()) work_h.resize(h2);
-        // H~ = Y diag(lamt) Y^T; Y overwrites Ht
-        CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, m, CUDA_R_64F, Ht, m,
-                             CUDA_R_64F, lamt, CUDA_R_64F, work, d1, work_h.data(), h2, ints + 2));
-        const double w = window > 0.0 ? window : c->a[r];
-        CK(launch_select_range(lamt, m, n_eigs, w, ints + 3, c->st));
-        c->launches += 1;
-        CK(cudaMemcpyAsync(hv, ints + 2, 3 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        if (hv[0] != 0) { *n_found = -DACP_ERR_NOT_CONVERGED; return DACP_OK; }
-        const int first = hv[1], cnt = hv[2];
-        *n_found = cnt;
-        if (cnt < 1) return DACP_OK;
-        TRY(dalloc_t(c, &Bsel, static_cast<size_t>(M) * cnt));
+        TRY(ritz_select(c, r, n_eigs, window, eps, true, z));
+        *n_found = z.cnt;
+        if (z.cnt < 1) return DACP_OK;
+        const int M = z.M, cnt = z.cnt;
+        double *W2 = nullptr, *rs = nullptr;
         TRY(dalloc_t(c, &W2, static_cast<size_t>(M) * cnt));
+        z.tmp.push_back(W2);
         TRY(dalloc_t(c, &rs, cnt));
-        // coefficients of the selected Ritz vectors, b_j = U y_j, then H2 b_j
-        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, cnt, m, &one, U, M, Ht + static_cast<int64_t>(first) * m,
-                        m, &zero, Bsel, M));
-        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, cnt, M, &one, H2, M, Bsel, M, &zero, W2, M));
-        CK(launch_residual(Bsel, W2, M, cnt, lamt + first, rs, c->st));
+        z.tmp.push_back(rs);
+        const double one = 1.0, zero = 0.0;
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, M, cnt, M, &one, z.H2, M, z.Bsel, M, &zero, W2, M));
+        CK(launch_residual(z.Bsel, W2, M, cnt, z.lam, rs, c->st));
         c->launches += 1;
-        CK(cudaMemcpyAsync(eigs, lamt + first, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(eigs, z.lam, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(resid, rs, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
         return DACP_OK;
     };
     dacp_status s = run();
-    cudaStreamSynchronize(c->st);
-    for (void* p : {static_cast<void*>(mus), static_cast<void*>(nus), static_cast<void*>(om), static_cast<void*>(S),
-                    static_cast<void*>(H), static_cast<void*>(H2), static_cast<void*>(W), static_cast<void*>(Ht),
-                    static_cast<void*>(lam), static_cast<void*>(lamt), static_cast<void*>(Bsel), static_cast<void*>(W2),
-                    static_cast<void*>(rs), static_cast<void*>(orders), static_cast<void*>(ints), work})
-        dfree(c, p);
+    ritz_free(c, z);
     return s;
 }
+
+dacp_status dacp_eigenvectors(dacp_handle c, int r, int n_eigs, double window, double eps, double* eigs,
+                              double* phi_dev, int64_t ld, int* n_found) {
+    TRY(check_handle(c));
+    if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_eigenvectors before dacp_basis_moments");
+    if (r < 0 || r >= c->R || n_eigs < 1 || !eigs || !phi_dev || !n_found)
+        return fail(c, DACP_ERR_ARG, "bad realization or output arguments");
+    const int64_t D = static_cast<int64_t>(1) << c->N[r];
+    if (ld < D) return fail(c, DACP_ERR_ARG, "ld %lld < 2^N = %lld", (long long)ld, (long long)D);
+    if (reinterpret_cast<uintptr_t>(phi_dev) & 7) return fail(c, DACP_ERR_ARG, "phi_dev must be 8-byte aligned");
+    if (!(eps > 0.0)) eps = c->fp32 ? kEpsFp32 : (c->prec == kPrecDF32 ? kEpsDf32 : 1e-12);
+    const int b = c->b, Ln = 2 * c->n[r] + 1;
+    Ritz z;
+    double* V = nullptr;
+    auto run = [&]() -> dacp_status {
+        TRY(ritz_select(c, r, n_eigs, window, eps, false, z));
+        *n_found = z.cnt;
+        if (z.cnt < 1) return DACP_OK;
+        const int M = z.M, cnt = z.cnt;
+        // basis orders x_i on the host (the same list the device kernel builds)
+        std::vector<int> x(Ln);
+        {
+            int* od = nullptr;
+            TRY(dalloc_t(c, &od, Ln));
+            z.tmp.push_back(od);
+            CK(launch_orders(Ln, c->a[r] / c->emax[r], od, c->st));
+            CK(cudaMemcpyAsync(x.data(), od, sizeof(int) * Ln, cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+        }
+        // V = [T_{x_0} psi_E, T_{x_1} psi_E, ...], float64, column (i*b + p) of length 2^N
+        TRY(dalloc_t(c, &V, static_cast<size_t>(D) * M));
+        z.tmp.push_back(V);
+        const size_t shift = static_cast<size_t>(c->info[r].off) * b * c->esz;
+        char* A = static_cast<char*>(c->A_d) + shift;
+        char* Bv = static_cast<char*>(c->B_d) + shift;
+        const size_t bytes = static_cast<size_t>(D) * b * c->esz;
+        // replay the evolution of realization r alone, w_0 = psi_E
+        TRY(set_evolution_coef(c, c->emax));
+        CK(cudaMemcpyAsync(A, static_cast<const char*>(c->psiE_d) + shift, bytes, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemsetAsync(c->step_ctr_d, 0, sizeof(int), c->st));
+        int next = 0;
+        if (x[0] == 0) {
+            CK(launch_gather_basis(c->prec, b, A, D, V, D, 0, c->st));
+            next = 1;
+        }
+        StepArgs a = base_args(c);
+        const int i0 = c->info[r].item_begin, ni = c->info[r].item_count;
+        for (int k = 0; next < Ln; ++k) {
+            CK(launch_step(c->prec, b, kEvolve, a, i0, ni, c->smem, c->st));   // w_{k+1}
+            c->launches += 1;
+            while (next < Ln && x[next] == k + 1) {
+                CK(launch_gather_basis(c->prec, b, (k & 1) ? A : Bv, D, V, D, next * b, c->st));
+                c->launches += 1;
+                ++next;
+            }
+        }
+        const double one = 1.0, zero = 0.0;
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, static_cast<int>(D), cnt, M, &one, V, static_cast<int>(D),
+                        z.Bsel, M, &zero, phi_dev, static_cast<int>(ld)));
+        CK(cudaMemcpyAsync(eigs, z.lam, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        TRY(check_device_flag(c));
+        return DACP_OK;
+    };
+    dacp_status s = run();
+    ritz_free(c, z);
+    if (s != DACP_OK) return s;
+    // restore the filter coefficients; the moments of r were rewritten with the same values
+    TRY(apply_params(c));
+    c->state = 3;
+    return DACP_OK;
+}
+
 
 dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
     TRY(check_handle(c));

@@ -1143,6 +1143,29 @@ cudaError_t launch_extract_col(int prec, int b, const void* src, void* dst, int6
     return cudaErrorInvalidValue;
 }
 
+// Columns col0 .. col0 + b - 1 of the column-major float64 basis matrix V
+// (leading dimension ldv) from one [state][b] vector of D states.
+template <typename T>
+__global__ void gather_basis_kernel(const T* __restrict__ src, int b, int64_t D, double* __restrict__ V, int64_t ldv,
+                                    int col0) {
+    const int64_t n = D * b;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int p = static_cast<int>(i / D);
+        const int64_t s = i % D;
+        V[(col0 + p) * ldv + s] = static_cast<double>(src[s * b + p]);
+    }
+}
+
+cudaError_t launch_gather_basis(int prec, int b, const void* src, int64_t D, double* V, int64_t ldv, int col0,
+                                cudaStream_t st) {
+    const int64_t n = D * b;
+    const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+    DACP_FOR_PREC(prec, gather_basis_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(src), b, D, V, ldv, col0);
+                        return cudaGetLastError());
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, cudaStream_t st) {
     const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
     if (n == 0) return cudaSuccess;

@@ -222,6 +222,65 @@ def test_overlapped_solve_matches_staged_calls(prec):
         assert mt["n_unmatched"] == 0 and mt["spacing_err"].max() < 1e-3, r
 
 
+def test_c1_eigenvectors_vs_oracle(c1_run):
+    """Ritz vectors (Appendix C, Sec. II C): the same levels as dacp_central_eigs; each
+    phi_j equals the oracle's explicit sum_(i,p) b_j T_{x_i} psi_p up to sign, has unit
+    norm, overlaps the exact eigenvector, and ||H phi_j - lam_j phi_j|| agrees with the
+    moment-form residual. The retained rank of S may differ by 2 between the two sides,
+    which moves a Ritz vector by ~3e-6 (oracle with eps 1e-12 vs 3e-12 on this case)."""
+    d, ref, m = c1_run["d"], c1_run["ref"], c1_run["m"]
+    emax, a = c1_run["emax"], c1_run["a"]
+    eigs, phi, nf = d.eigenvectors(0, 100)
+    assert nf == 100
+    Hd = Hm.dense_h(m)
+    E = np.linalg.eigvalsh(Hd)
+    width = E[-1] - E[0]
+    assert np.abs(eigs - c1_run["eigs"]).max() < 1e-10 * width
+    phi = phi.cpu().numpy()
+    S, H = DA.assemble(ref["mu"], ref["nu"], ref["orders"])
+    lam, Bc = DA.ritz_pairs(S, H)
+    idx = DA.select_central_index(lam, 100, a)
+    vecs = DA.chebyshev_vectors(m, ref["psi_E"], emax, int(ref["orders"][-1]))
+    basis = np.concatenate([vecs[x] for x in ref["orders"]], axis=1)
+    phi_ref = basis @ Bc[:, idx]
+    sign = np.sign(np.einsum("ij,ij->j", phi, phi_ref))
+    assert np.abs(phi * sign - phi_ref).max() < 2e-5
+    assert np.abs(np.linalg.norm(phi, axis=0) - 1.0).max() < 1e-9
+    Ex, Vx = np.linalg.eigh(Hd)
+    ix = np.array([np.argmin(np.abs(Ex - x)) for x in eigs])
+    assert np.abs(np.einsum("ij,ij->j", Vx[:, ix], phi)).min() > 1 - 1e-8
+    r_ex = np.linalg.norm(Hd @ phi - phi * eigs, axis=0)
+    _, resid, _ = d.residuals(0, 100)
+    assert np.abs(r_ex ** 2 - resid ** 2).max() < 1e-11 * emax ** 2
+    # the run keeps its state: moments and levels unchanged afterwards
+    e2, nf2, _ = d.central_eigs(100)
+    assert np.array_equal(e2[0], c1_run["eigs"])
+
+
+def test_eigenvectors_double_float_batch():
+    """Double-float handle, realization 2 of an uneven batch: Ritz vectors against dense
+    eigenvectors (|<phi_j, v_j>| ~ 1 for every level) and small explicit residuals."""
+    models = [W.spin_glass_shard(9, seed=1), W.chain(8), W.random_model(10, seed=2)]
+    psis = [W.start_vectors(m["N"], 4, seed=5, r=i) for i, m in enumerate(models)]
+    d = P.Dacp(models, psis, block_b=4, precision=P.DACP_DF32)
+    try:
+        d.choose_params(40)
+        d.filter()
+        d.basis_moments()
+        eigs, phi, nf = d.eigenvectors(2, 40)
+        assert nf == 40
+        Hd = Hm.dense_h(models[2])
+        E, V = np.linalg.eigh(Hd)
+        phi = phi.cpu().numpy()
+        idx = np.array([np.argmin(np.abs(E - x)) for x in eigs])
+        ov = np.abs(np.einsum("ij,ij->j", V[:, idx], phi))
+        assert ov.min() > 1 - 1e-8
+        r_ex = np.linalg.norm(Hd @ phi - phi * eigs, axis=0)
+        assert r_ex.max() < 1e-5 * (E[-1] - E[0])
+    finally:
+        d.close()
+
+
 def test_residual_norms_flag_a_short_basis():
     """With a basis too small for the window the edge levels are unconverged: the
     moment residuals rise by orders of magnitude while still bounding the error."""
