@@ -1056,9 +1056,11 @@ dacp_status solve_batch(dacp_ctx* c, BatchWs& w, const SolveRes& s, const int* i
     const double* U = w.S + static_cast<int64_t>(Mg - m_max) * Mg;
     CKB(cublasDgemmStridedBatched(s.blas, CUBLAS_OP_N, CUBLAS_OP_N, Mg, m_max, Mg, &one, w.H, Mg, MM, U, Mg, MM, &zero,
                                   w.W, Mg, static_cast<int64_t>(Mg) * m_max, g));
-    CKB(cublasDgemmStridedBatched(s.blas, CUBLAS_OP_T, CUBLAS_OP_N, m_max, m_max, Mg, &one, U, Mg, MM, w.W, Mg,
-                                  static_cast<int64_t>(Mg) * m_max, &zero, w.Ht, m_max,
-                                  static_cast<int64_t>(m_max) * m_max, g));
+    // H~ = U^T W is symmetric: its lower triangle alone (what the eigensolver reads), half the flops
+    for (int i = 0; i < g; ++i)
+        CKB(cublasDsyrkx(s.blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, m_max, Mg, &one, U + i * MM, Mg,
+                         w.W + static_cast<int64_t>(i) * Mg * m_max, Mg, &zero,
+                         w.Ht + static_cast<int64_t>(i) * m_max * m_max, m_max));
     CK(launch_pad_diagonal(w.Ht, m_max, static_cast<int64_t>(m_max) * m_max, w.mi, w.big, g, s.st));
     CKS(cusolverDnXsyevBatched_bufferSize(s.sol, s.sp, CUSOLVER_EIG_MODE_NOVECTOR, CUBLAS_FILL_MODE_LOWER, m_max,
                                           CUDA_R_64F, w.Ht, m_max, CUDA_R_64F, w.lamt, CUDA_R_64F, &d2, &h2, g));
