@@ -1241,7 +1241,10 @@ namespace {
 
 dacp_status ensure_solver2(dacp_ctx* c) {
     if (c->st2) return DACP_OK;
-    CK(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    // highest priority: the solves' kernels take SM slots as the stencil's CTAs retire
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&c->st2, cudaStreamNonBlocking, greatest));
     CKS(cusolverDnCreate(&c->sol2));
     CKS(cusolverDnSetStream(c->sol2, c->st2));
     CKS(cusolverDnCreateParams(&c->sp2));

@@ -275,8 +275,14 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
         const int64_t gbase = R.off * B;                                  // first value of the realization
         const T* xg = x + gbase;
         const T* dg = static_cast<const T*>(a.diag) + R.off;
-        // c_h folds into the x-fields and the diagonal: acc = c_h H x directly
-        if (tid < R.N) gam_s[tid] = ch * static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
+        // float64 / double-float: c_h folds into the x-fields and the diagonal,
+        // acc = c_h H x directly. float32 scales the sum once at the end instead:
+        // folding moves its rounding enough to tip the float32 moment floor.
+        constexpr bool kFold = sizeof(T) != 4;
+        if (tid < R.N) {
+            const T g = static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
+            gam_s[tid] = kFold ? ch * g : g;
+        }
 
         if (tstates >= SU) {
             // ---- unit path: stage the tile with one bulk copy -------------------
@@ -311,7 +317,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                         if (kEarlyY && use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
                         if (kEarlyY && use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
 #pragma unroll
-                        for (int j = 0; j < SU; ++j) dv[k][j] = ch * ld_ro(dg + s0 + j);
+                        for (int j = 0; j < SU; ++j) dv[k][j] = kFold ? ch * ld_ro(dg + s0 + j) : ld_ro(dg + s0 + j);
                     }
                 }
 #pragma unroll
@@ -336,8 +342,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                 constexpr int EG = EarlyGlobal<T>::value;
                 const int ngb = R.N - R.tbits;
                 int64_t sbase[UP];
+                if (EG > 0) {   // (without early loads, set after the in-tile flips: fewer live registers)
 #pragma unroll
-                for (int k = 0; k < UP; ++k) sbase[k] = val[k] ? tile0 + static_cast<int64_t>(uu[k]) * SU : tile0;
+                    for (int k = 0; k < UP; ++k) sbase[k] = val[k] ? tile0 + static_cast<int64_t>(uu[k]) * SU : tile0;
+                }
                 T pe[EG > 0 ? EG : 1][UP][VU];
 #pragma unroll
                 for (int j = 0; j < EG; ++j)
@@ -364,6 +372,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     }
                 }
                 // flips beyond the tile (global memory, L2-resident partner tiles)
+                if (EG == 0) {
+#pragma unroll
+                    for (int k = 0; k < UP; ++k) sbase[k] = val[k] ? tile0 + static_cast<int64_t>(uu[k]) * SU : tile0;
+                }
 #pragma unroll
                 for (int j = 0; j < EG; ++j) {
                     if (j < ngb) {
@@ -410,6 +422,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                     for (int v = 0; v < VU; ++v) {
                         typename AC::type t = acc[k][v];
+                        if (!kFold) t = AC::prod(ch, AC::final(acc[k][v]));
                         if (use1) AC::mad(t, c1, yv[k][v]);
                         if (use2) AC::mad(t, c2, zv[k][v]);
                         o[v] = AC::final(t);
@@ -440,7 +453,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                 const int64_t s = tile0 + sl;
                 T xv[B], acc[B];
                 load_vals<T, B>(tile + sl * B, xv);
-                const T d = ch * dg[s];
+                const T d = kFold ? ch * dg[s] : dg[s];
 #pragma unroll
                 for (int p = 0; p < B; ++p) acc[p] = d * xv[p];
                 for (int i = 0; i < R.tbits; ++i) {
@@ -452,7 +465,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                 T o[B];
 #pragma unroll
                 for (int p = 0; p < B; ++p) {
-                    T t = acc[p];
+                    T t = kFold ? acc[p] : ch * acc[p];
                     if (use1) t = fma(c1, COHERENT ? ld_cg(y1 + gbase + s * B + p) : y1[gbase + s * B + p], t);
                     if (use2) t = fma(c2, COHERENT ? ld_cg(y2 + gbase + s * B + p) : y2[gbase + s * B + p], t);
                     o[p] = t;
