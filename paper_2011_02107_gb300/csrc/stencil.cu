@@ -657,11 +657,23 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
             for (int j = 0; j < EG; ++j)
                 if (j < ngb) ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B + col, pe[j][0],
                                              pe[j][1]);
-            const T d = ch * ld_ro(dg + sg);
-            Dot2 acc0 = Accum<T>::prod(d, a0), acc1 = Accum<T>::prod(d, a1);
-            // flips inside the tile (shared memory)
+            // the diagonal and w_{k-1} are loaded now and used last, so their
+            // latency hides under the in-tile flips
+            const T dr = ld_ro(dg + sg);
+            T y0 = T(0), y1v = T(0), z0 = T(0), z1 = T(0);
+            if (use1) ld2_rw<COHERENT>(y1 + gbase + sg * B + col, y0, y1v);
+            if (use2) ld2_rw<COHERENT>(y2 + gbase + sg * B + col, z0, z1);
+            // flips inside the tile (shared memory); bit 0 starts the sums (tbits >= 1)
+            Dot2 acc0, acc1;
+            {
+                const T g = gam_s[0];
+                T p0, p1;
+                ld2_s(tile + (sl ^ 1) * B + col, p0, p1);
+                acc0 = Accum<T>::prod(g, p0);
+                acc1 = Accum<T>::prod(g, p1);
+            }
 #pragma unroll
-            for (int i = 0; i < kDf4TileBits; ++i) {
+            for (int i = 1; i < kDf4TileBits; ++i) {
                 if (i < R.tbits) {
                     const T g = gam_s[i];
                     T p0, p1;
@@ -693,18 +705,17 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
                 dot2_mad(acc0, g, p0);
                 dot2_mad(acc1, g, p1);
             }
-            // w_{k+1} = c_h H x + c_1 y + c_2 z
+            // diagonal term, then w_{k+1} = c_h H x + c_1 y + c_2 z
+            const T d = ch * dr;
+            dot2_mad(acc0, d, a0);
+            dot2_mad(acc1, d, a1);
             if (use1) {
-                T v0, v1;
-                ld2_rw<COHERENT>(y1 + gbase + sg * B + col, v0, v1);
-                dot2_mad(acc0, c1, v0);
-                dot2_mad(acc1, c1, v1);
+                dot2_mad(acc0, c1, y0);
+                dot2_mad(acc1, c1, y1v);
             }
             if (use2) {
-                T v0, v1;
-                ld2_rw<COHERENT>(y2 + gbase + sg * B + col, v0, v1);
-                dot2_mad(acc0, c2, v0);
-                dot2_mad(acc1, c2, v1);
+                dot2_mad(acc0, c2, z0);
+                dot2_mad(acc1, c2, z1);
             }
             const T o0 = dot2_final(acc0), o1 = dot2_final(acc1);
             if (val) st2(out + gbase + sg * B + col, o0, o1);
