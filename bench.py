@@ -2,8 +2,8 @@
 """Throughput benchmark of batched DACP on GB300.
 
 Metric: central eigenvalues per second of the whole hot path -- parameter
-choice (Lanczos bound + KPM window; --params mlp adds the learned network when
-its weights exist), exp-semicircle filter, Chebyshev evolution with float64
+choice (Lanczos bound + KPM window, then the learned network when weights for
+the precision exist; --params heuristic skips it), exp-semicircle filter, Chebyshev evolution with float64
 moments, subspace assembly and generalized eigensolve (overlapped with the
 evolution of the realizations still running) -- over one batch of synthetic
 realizations (one "step"). Default workload: 256 spin-glass shards, N = 14
@@ -326,11 +326,38 @@ def run_gpu(args, wl, rank, world):
     clk = clocks.stop()
     launches = d.launch_count() - l0
     ms = ev0.elapsed_time(ev1)
+    last_eigs = eigs
     ms_all = dist_max(ms)
     found_all = dist_sum(found)
     value = found_all / (ms_all / 1e3)
     params = d.params()
     d.close()
+
+    # ---- accuracy of the timed path (outside the timed region): sampled realizations
+    # against float64 DACP with the paper's parameters (c = 18, window ratio 2, basis
+    # ratio 1.5), whose own agreement with the CPU oracle and dense spectra the GPU tests
+    # pin; error in units of the judge's local mean level spacing
+    accuracy = None
+    if not args.no_accuracy_check and R > 0:
+        from paper_2011_02107_gb300 import train_mlp
+        pick = sorted({0, R // 4, R // 2, (3 * R) // 4})
+        dj = P.Dacp([models[r] for r in pick], [psis[r] for r in pick], block_b=wl["b"], precision=P.DACP_FP64,
+                    stream=stream.cuda_stream)
+        try:
+            dj.choose_params(n_eigs, c_order=18.0)
+            ref, nf_ref, _ = dj.run(n_eigs)
+        finally:
+            dj.close()
+        errs = []
+        for j, r in enumerate(pick):
+            got = np.asarray(last_eigs[r])
+            if nf_ref[j] < n_eigs or len(got) < n_eigs:
+                errs.append(float("inf"))
+                continue
+            errs.append(train_mlp.accurate(got[:n_eigs], np.asarray(ref[j])[:n_eigs])[1])
+        accuracy = {"sampled_realizations": pick, "judge": "float64 DACP, paper parameters (GPU)",
+                    "max_spacing_err": max(errs), "within_1e-2": int(sum(e <= 1e-2 for e in errs)),
+                    "n_eigs": n_eigs}
 
     # ---- e2e: public API from pinned host buffers, H2D and D2H inside the timed region
     n_spins, J, h, g = W.pack_models(models)
@@ -387,6 +414,7 @@ def run_gpu(args, wl, rank, world):
                 "steps": e2e_steps},
         "gpu_launches": int(launches),
         "parameter_choice": "learned network (heuristic fallback)" if mlp is not None else "heuristic",
+        "accuracy": accuracy,
         "fallback_realizations": fallbacks[0],
         "tile_bytes": tile_bytes,
         "roofline": roof,
@@ -403,9 +431,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--params", default="heuristic", choices=["mlp", "heuristic"],
-                    help="parameter choice: the heuristic (default), or the trained network when its weights "
-                         "exist")
+    ap.add_argument("--params", default="mlp", choices=["mlp", "heuristic"],
+                    help="parameter choice: the trained network when weights for the precision exist "
+                         "(heuristic fallback per realization), else the heuristic")
+    ap.add_argument("--no-accuracy-check", action="store_true",
+                    help="skip the float64 judge run on sampled realizations after the timed steps")
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "df32"],
                     help="override the workload's precision (df32: double-float vectors on the float32 pipes)")
     ap.add_argument("--realizations", type=int, default=None, help="override the number of realizations per GPU")
