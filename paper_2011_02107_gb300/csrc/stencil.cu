@@ -536,9 +536,9 @@ reduce:
 // columns 2h, 2h+1 of one state (16 bytes): half the registers, three CTAs
 // per SM. Moment sums: thread h has its own x (a), its outputs o and, after
 // one shuffle with the neighbouring lane, the other pair's x (c). It keeps
-// ten sums: <a,a> and <o,a> within its pair (three each) and four cross sums
-// of its own o (h = 0) or own x (h = 1) with c. Only the evolution emits
-// moments on this path (its <o, x> block is symmetric).
+// ten sums: <a,a> and <o,a> within its pair (three each) and four cross sums,
+// h = 0: <o_p, x_q> and h = 1: <x_p, x_q> for p in {0,1}, q in {2,3}. Only the
+// evolution emits moments on this path (its <o, x> block is symmetric).
 
 __device__ __forceinline__ void ld2_s(const df32* p, df32& v0, df32& v1) {
     const float4 f = *reinterpret_cast<const float4*>(p);
@@ -576,7 +576,7 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
     constexpr int B = 4, EG = EarlyGlobal<T>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
-    __shared__ __align__(16) T gam_s[kMaxSpins];   // read two at a time by the in-tile flips
+    __shared__ T gam_s[kMaxSpins];
     __shared__ double red_s[kThreads / 32][2 * B * B];
     __shared__ int last_s;
     __shared__ __align__(8) uint64_t bar_s;
@@ -665,19 +665,17 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
             if (use2) ld2_rw<COHERENT>(y2 + gbase + sg * B + col, z0, z1);
             // flips inside the tile (shared memory); bit 0 starts the sums (tbits >= 1)
             Dot2 acc0, acc1;
-            T ga, gb;                                    // x-fields of bits i, i+1 (i even), one 16-byte load
-            ld2_s(gam_s, ga, gb);
             {
+                const T g = gam_s[0];
                 T p0, p1;
                 ld2_s(tile + (sl ^ 1) * B + col, p0, p1);
-                acc0 = Accum<T>::prod(ga, p0);
-                acc1 = Accum<T>::prod(ga, p1);
+                acc0 = Accum<T>::prod(g, p0);
+                acc1 = Accum<T>::prod(g, p1);
             }
 #pragma unroll
             for (int i = 1; i < kDf4TileBits; ++i) {
                 if (i < R.tbits) {
-                    if (!(i & 1)) ld2_s(gam_s + i, ga, gb);
-                    const T g = (i & 1) ? gb : ga;
+                    const T g = gam_s[i];
                     T p0, p1;
                     ld2_s(tile + (sl ^ (1 << i)) * B + col, p0, p1);
                     dot2_mad(acc0, g, p0);
@@ -730,10 +728,9 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
                     dot2_mad(ms[3], o0, a0);
                     dot2_mad(ms[4], o0, a1);
                     dot2_mad(ms[5], o1, a1);
-                    // across the pairs: h = 0 sums <o_p, x_q> (own o, other x), h = 1 sums
-                    // <x_q, x_p> (own x, other x), p in {0,1}, q in {2,3}
-                    const T u0 = h ? a0 : o0, u1 = h ? a1 : o1;
-                    const T v0 = cx0, v1 = cx1;
+                    // p in {0,1}, q in {2,3}: h = 0 sums <o_p, x_q>, h = 1 sums <x_p, x_q>
+                    const T u0 = h ? cx0 : o0, u1 = h ? cx1 : o1;
+                    const T v0 = h ? a0 : cx0, v1 = h ? a1 : cx1;
                     dot2_mad(ms[6], u0, v0);
                     dot2_mad(ms[7], u0, v1);
                     dot2_mad(ms[8], u1, v0);
@@ -767,11 +764,10 @@ reduce_df4:
             put(1, b0, b0, sv[3]);
             put(1, b0, b0 + 1, sv[4]);
             put(1, b0 + 1, b0 + 1, sv[5]);
-            // lane 0: <o_p, x_q> as (0,2), (0,3), (1,2), (1,3); lane 1: <x_q, x_p> as (0,2), (1,2), (0,3), (1,3)
-            const int blk = lane == 0 ? 1 : 0;
+            const int blk = lane == 0 ? 1 : 0;          // lane 0: <o_p, x_q>; lane 1: <x_p, x_q>
             put(blk, 0, 2, sv[6]);
-            put(blk, lane ? 1 : 0, lane ? 2 : 3, sv[7]);
-            put(blk, lane ? 0 : 1, lane ? 3 : 2, sv[8]);
+            put(blk, 0, 3, sv[7]);
+            put(blk, 1, 2, sv[8]);
             put(blk, 1, 3, sv[9]);
         }
         __syncthreads();

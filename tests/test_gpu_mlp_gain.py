@@ -12,7 +12,8 @@ beyond the training range) are solved three ways on the GPU:
 The learned run must keep every requested level within 1e-2 of the local
 mean spacing of the reference, and cost less than the heuristic run: at
 least 10 % less in the GB300 cost model (stencil value-orders + M^3 subspace
-term), and less in the measured T_E + T_D of the library's own CUDA events.
+term), and less in the measured T_F + T_E + T_D of the library's own CUDA
+events.
 """
 
 import os
@@ -68,6 +69,8 @@ def test_learned_parameters_keep_accuracy_and_cut_cost():
             # the eligible knob settings all keep the basis ratio 1.5: the gain comes from the
             # window and the filter order (at most ~25 %)
             assert cost_l < 0.9 * cost_h, (N, cost_l, cost_h)
-            assert ms_l[1] + ms_l[2] < ms_h[1] + ms_h[2], (N, ms_l, ms_h)
+            # whole measured path: the learned knobs keep the basis ratio (so T_E is alike) and
+            # save in the filter and the subspace solve
+            assert sum(ms_l) < sum(ms_h), (N, ms_l, ms_h)
     finally:
         P.dacp_mlp_destroy(mlp)
