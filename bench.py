@@ -392,6 +392,18 @@ def run_gpu(args, wl, rank, world):
 
     # ---- roofline of the dominant kernel (evolution stencil), per vector precision
     roof = roofline(wl, models, phase, bytes_evo, states_evo, clk)
+    # H.v HBM bandwidth of the evolution (algorithmic bytes: read w_k, read w_{k-1},
+    # write w_{k+1}) against the measured copy bandwidth, for every precision
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = json.load(f).get("hbm_gbs") or 6800.0
+    except OSError:
+        hbm_peak = 6800.0
+    t_e = phase[1] / 1e3
+    hbm_gbs = bytes_evo / t_e / 1e9 if t_e > 0 else None
+    hbm = {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak if hbm_gbs else None,
+           "bytes": "3 * 2^N * b * value size per realization and order, over T_E",
+           "bound_here": roof["bound"]}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -418,6 +430,7 @@ def run_gpu(args, wl, rank, world):
         "fallback_realizations": fallbacks[0],
         "tile_bytes": tile_bytes,
         "roofline": roof,
+        "hbm": hbm,
         "clocks": clk,
     }
     return out
