@@ -86,6 +86,7 @@ struct dacp_ctx {
     int64_t Dtot = 0;
     int smem = 0;
     int tile_bytes = 0;
+    int tb_uniform = 0;                 // tile bits shared by every realization, else 0
     std::vector<double> J_h, h_h, g_h;   // [R][kMaxSpins(^2)]
     std::vector<double> pnorm;
 
@@ -292,6 +293,7 @@ StepArgs base_args(dacp_ctx* c) {
     a.err_flag = c->err_d;
     a.bar_count = c->bar_d;
     a.bar_gen = c->bar_d + 1;
+    a.tbits_uniform = c->tb_uniform;
     return a;
 }
 
@@ -373,6 +375,9 @@ void tile_geometry(dacp_ctx* c, int tile_bytes) {
     }
     c->smem = static_cast<int>(max_tstates * c->b * c->esz);
     c->tile_bytes = tile_bytes;
+    c->tb_uniform = c->R > 0 ? c->info[0].tbits : 0;
+    for (int r = 1; r < c->R; ++r)
+        if (c->info[r].tbits != c->tb_uniform) c->tb_uniform = 0;
 }
 
 // Partial-sum slots for the smallest tile the autotuner may pick.

@@ -89,6 +89,8 @@ struct StepArgs {
     int* err_flag;           // set to 1 when a bounded device wait gives up
     unsigned* bar_count;     // grid barrier of the persistent launch: arrivals
     unsigned* bar_gen;       // and generation
+    int tbits_uniform;       // > 0: every realization's tile has this many bits (lets a launch pick a
+                             // kernel specialised on it); 0: mixed
 };
 
 }  // namespace dacp

@@ -570,7 +570,9 @@ __device__ __forceinline__ df32 shfl_xor_df(df32 v, int m) {
 
 constexpr int kDf4TileBits = 12;   // in-tile flips unrolled: tiles up to 4096 states (128 KB)
 
-template <int MODE, bool COHERENT>
+// TB > 0: the tile has TB bits in every realization of the launch (compile-time
+// flip loop); TB = 0: read from RealInfo.
+template <int MODE, bool COHERENT, int TB = 0>
 __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item, const int step) {
     using T = df32;
     constexpr int B = 4, EG = EarlyGlobal<T>::value;
@@ -673,8 +675,8 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
                 acc1 = Accum<T>::prod(g, p1);
             }
 #pragma unroll
-            for (int i = 1; i < kDf4TileBits; ++i) {
-                if (i < R.tbits) {
+            for (int i = 1; i < (TB > 0 ? TB : kDf4TileBits); ++i) {
+                if (TB > 0 || i < R.tbits) {
                     const T g = gam_s[i];
                     T p0, p1;
                     ld2_s(tile + (sl ^ (1 << i)) * B + col, p0, p1);
@@ -682,7 +684,7 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
                     dot2_mad(acc1, g, p1);
                 }
             }
-            for (int i = kDf4TileBits; i < R.tbits; ++i) {
+            for (int i = kDf4TileBits; TB == 0 && i < R.tbits; ++i) {
                 const T g = gam_s[i];
                 T p0, p1;
                 ld2_s(tile + (sl ^ (1 << i)) * B + col, p0, p1);
@@ -806,6 +808,26 @@ __device__ __forceinline__ void tile_step_any(const StepArgs& a, const int item,
     else tile_step<T, B, MODE, COHERENT>(a, item, step);
 }
 
+// Double-float b = 4 with a tile of TB bits in every realization.
+template <int MODE, int TB>
+__global__ void __launch_bounds__(kThreads, MinBlocks<df32, 4>::value) step_kernel_df4tb(const StepArgs a,
+                                                                                         int item_base) {
+    int step = 0;
+    if (MODE != kApply) step = *a.step_ctr;
+    tile_step_df4<MODE, false, TB>(a, item_base + blockIdx.x, step);
+    if (MODE == kFilter2 || MODE == kEvolve) {
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(a.launch_done, 1u);
+            if (prev == gridDim.x - 1) {
+                *a.launch_done = 0u;
+                __threadfence();
+                atomicAdd(a.step_ctr, 1);
+            }
+        }
+    }
+}
+
 template <typename T, int B, int MODE>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T, B>::value) step_kernel(const StepArgs a, int item_base) {
     int step = 0;
@@ -878,8 +900,24 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T, B>::value) persistent_k
 
 template <typename T, int B, int MODE>
 static cudaError_t launch_one(const StepArgs& a, int item_base, int n_items, int smem, cudaStream_t st) {
+    if constexpr (std::is_same<T, df32>::value && B == 4) {
+        switch (a.tbits_uniform) {
+            case 10: step_kernel_df4tb<MODE, 10><<<n_items, kThreads, smem, st>>>(a, item_base); return cudaGetLastError();
+            case 11: step_kernel_df4tb<MODE, 11><<<n_items, kThreads, smem, st>>>(a, item_base); return cudaGetLastError();
+            case 12: step_kernel_df4tb<MODE, 12><<<n_items, kThreads, smem, st>>>(a, item_base); return cudaGetLastError();
+            default: break;
+        }
+    }
     step_kernel<T, B, MODE><<<n_items, kThreads, smem, st>>>(a, item_base);
     return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t prepare_df4tb(int smem) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(step_kernel_df4tb<MODE, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(step_kernel_df4tb<MODE, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_kernel_df4tb<MODE, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 template <typename T, int B>
@@ -888,6 +926,12 @@ static cudaError_t prepare_tb(int smem) {
     if ((e = cudaFuncSetAttribute(step_kernel<T, B, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(step_kernel<T, B, kFilter1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(step_kernel<T, B, kFilter2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if constexpr (std::is_same<T, df32>::value && B == 4) {
+        if ((e = prepare_df4tb<kApply>(smem)) != cudaSuccess) return e;
+        if ((e = prepare_df4tb<kFilter1>(smem)) != cudaSuccess) return e;
+        if ((e = prepare_df4tb<kFilter2>(smem)) != cudaSuccess) return e;
+        if ((e = prepare_df4tb<kEvolve>(smem)) != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(step_kernel<T, B, kEvolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
