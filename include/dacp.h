@@ -249,11 +249,13 @@ dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);
 /*
  * dacp_set_solver -- how dacp_central_eigs runs the dense float64 algebra:
  * 1 (default) = one batched cuSOLVER syev call per group for S and one for
- * H~, with strided-batched dgemm between them; smaller bases are zero-padded
- * to the largest (the padding only adds S eigenvalues 0, which the cut-off
- * removes). Used when there are several realizations and every basis is at
- * least 3/4 of the largest. 0 = concurrent lanes (own stream, handles and
- * host thread each) solving the realizations one by one.
+ * H~, with a strided-batched dgemm (W = H U) and a syrkx per realization
+ * (the lower triangle of H~ = U^T W) between them; smaller bases are
+ * zero-padded to the largest (the padding only adds S eigenvalues 0, which
+ * the cut-off removes). Used when there are several realizations and every
+ * basis is at least 3/4 of the largest. 0 = concurrent lanes (own stream,
+ * handles and host thread each) solving the realizations one by one.
+ * dacp_solve always uses the batched form, in groups of similar basis size.
  */
 dacp_status dacp_set_solver(dacp_handle hd, int mode);
 
