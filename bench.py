@@ -69,6 +69,7 @@ def make_inputs(wl, rank=0):
 
 # float32 instructions per double-float fused multiply-add in the library's
 # arithmetic (TwoProduct 2, cross terms 2, TwoSum 6, folding 3, Fast2Sum 3)
+DF32_EVOLVE_TRAFFIC = 302280960 + 103473408   # bytes, step_kernel_df4tb<kEvolve, 11>, one launch
 # One error-free double-float multiply-add (the Dot2 step): TwoProduct 2,
 # cross terms 2, TwoSum 6, error adds 3 float32 instructions.
 DF_FMA_INSTR = 13
@@ -99,7 +100,7 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk):
     b = wl["b"]
     N = wl["N"]
     fma_per_state = N * b + 2 * b + b * (b + 1)
-    kern = {"fp32": "step_kernel<float,4,kEvolve>", "df32": "step_kernel<df32,4,kEvolve>",
+    kern = {"fp32": "step_kernel<float,4,kEvolve>", "df32": "step_kernel_df4tb<kEvolve,11> (double-float, b = 4)",
             "fp64": "step_kernel<double,4,kEvolve>"}[wl["prec"]]
     if wl["prec"] == "fp32":
         peak = peaks.get("hbm_gbs") or 6800.0
@@ -109,11 +110,17 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic": "3 * 2^N * b * 4 B per realization and order"}
     if wl["prec"] == "df32":
+        # DRAM bytes of one evolution launch with all 256 realizations of the default workload
+        # active, from one ncu capture of the current kernel (profiles/); other workloads: none
+        traffic = DF32_EVOLVE_TRAFFIC if (N, b, len(models)) == (14, 4, 256) else None
         mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
         peak = SMS * FP32_LANES_PER_SM * mhz * 1e6 / 1e12            # T instr/s
         achieved = states_evo * fma_per_state * DF_FMA_INSTR / t_e / 1e12 if t_e > 0 else None
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T float32 instr/s",
-                "frac": achieved / peak if achieved else None, "traffic": None, "kernel": kern,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one full evolution launch "
+                                "(all 256 realizations active); algorithmic 402.7 MB + 33.6 MB diagonal"
+                                if traffic else None, "kernel": kern,
                 "peak_source": f"152 SMs x 128 float32 lanes x {mhz:.0f} MHz (sampled)",
                 "algorithmic": f"{fma_per_state} double-float FMA x {DF_FMA_INSTR} instr per state and order"}
     peak = 0.55                                                         # T FMA/s, measured dgemm

@@ -622,8 +622,9 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
         const bool use2 = (c_2 != 0.0) && (y2 != nullptr);
         const T ch = static_cast<T>(c_h), c1 = static_cast<T>(c_1), c2 = static_cast<T>(c_2);
 
-        const int tstates = 1 << R.tbits;
-        const int64_t tile0 = static_cast<int64_t>(it.tile) << R.tbits;
+        const int tbits = TB > 0 ? TB : R.tbits;           // compile-time when specialised
+        const int tstates = 1 << tbits;
+        const int64_t tile0 = static_cast<int64_t>(it.tile) << tbits;
         const int64_t gbase = R.off * B;
         const T* xg = x + gbase;
         const T* dg = static_cast<const T*>(a.diag) + R.off;
@@ -644,11 +645,12 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
         if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar_s)) : "memory");
         if (!landed) goto reduce_df4;
 
-        const int ngb = R.N - R.tbits;
+        const int ngb = R.N - tbits;
         const int nhalf = 2 * tstates;                   // (state, column pair) slots of the tile
         for (int hb = 0; hb < nhalf; hb += kThreads) {
             const int hs = hb + tid;
-            const bool val = hs < nhalf;                 // both lanes of a pair agree (nhalf is even)
+            // both lanes of a pair agree (nhalf is even); a specialised tile of >= 128 states fills every pass
+            const bool val = (TB >= 7) || hs < nhalf;
             const int sl = val ? (hs >> 1) : 0;          // idle lanes work on state 0 and store nothing
             const int64_t sg = tile0 + sl;               // state within the realization
             const int col = 2 * h;
@@ -657,7 +659,7 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
             T pe[EG > 0 ? EG : 1][2];
 #pragma unroll
             for (int j = 0; j < EG; ++j)
-                if (j < ngb) ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B + col, pe[j][0],
+                if (j < ngb) ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (tbits + j))) * B + col, pe[j][0],
                                              pe[j][1]);
             // the diagonal and w_{k-1} are loaded now and used last, so their
             // latency hides under the in-tile flips
@@ -695,15 +697,15 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
 #pragma unroll
             for (int j = 0; j < EG; ++j) {
                 if (j < ngb) {
-                    const T g = gam_s[R.tbits + j];
+                    const T g = gam_s[tbits + j];
                     dot2_mad(acc0, g, pe[j][0]);
                     dot2_mad(acc1, g, pe[j][1]);
                 }
             }
             for (int j = EG; j < ngb; ++j) {
-                const T g = gam_s[R.tbits + j];
+                const T g = gam_s[tbits + j];
                 T p0, p1;
-                ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (R.tbits + j))) * B + col, p0, p1);
+                ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (tbits + j))) * B + col, p0, p1);
                 dot2_mad(acc0, g, p0);
                 dot2_mad(acc1, g, p1);
             }
