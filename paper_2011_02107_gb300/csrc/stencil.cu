@@ -568,6 +568,8 @@ __device__ __forceinline__ df32 shfl_xor_df(df32 v, int m) {
     return df32(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
 }
 
+static_assert((static_cast<int64_t>(1) << kMaxSpins) * 4 < (static_cast<int64_t>(1) << 31),
+              "per-state offsets of the double-float b = 4 pass are 32-bit");
 constexpr int kDf4TileBits = 12;   // in-tile flips unrolled: tiles up to 4096 states (128 KB)
 
 // TB > 0: the tile has TB bits in every realization of the launch (compile-time
@@ -627,6 +629,9 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
         const int64_t tile0 = static_cast<int64_t>(it.tile) << tbits;
         const int64_t gbase = R.off * B;
         const T* xg = x + gbase;
+        const T* y1g = (MODE != kFilter1 && y1) ? y1 + gbase : nullptr;   // kFilter1 has no y
+        const T* y2g = (MODE == kFilter2 && y2) ? y2 + gbase : nullptr;   // only kFilter2 has a z
+        T* outg = out + gbase;
         const T* dg = static_cast<const T*>(a.diag) + R.off;
         if (tid < R.N) gam_s[tid] = ch * static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
 
@@ -652,21 +657,23 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
             // both lanes of a pair agree (nhalf is even); a specialised tile of >= 128 states fills every pass
             const bool val = (TB >= 7) || hs < nhalf;
             const int sl = val ? (hs >> 1) : 0;          // idle lanes work on state 0 and store nothing
-            const int64_t sg = tile0 + sl;               // state within the realization
+            // state within the realization: N <= kMaxSpins keeps sg * B below 2^31, so the
+            // per-state offsets are 32-bit and only the realization's base pointers are 64-bit
+            const uint32_t sg = static_cast<uint32_t>(tile0) + static_cast<uint32_t>(sl);
             const int col = 2 * h;
             T a0, a1;
             ld2_s(tile + sl * B + col, a0, a1);
             T pe[EG > 0 ? EG : 1][2];
 #pragma unroll
             for (int j = 0; j < EG; ++j)
-                if (j < ngb) ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (tbits + j))) * B + col, pe[j][0],
+                if (j < ngb) ld2_g<COHERENT>(xg + ((sg ^ (1u << (tbits + j))) * B + col), pe[j][0],
                                              pe[j][1]);
             // the diagonal and w_{k-1} are loaded now and used last, so their
             // latency hides under the in-tile flips
             const T dr = ld_ro(dg + sg);
             T y0 = T(0), y1v = T(0), z0 = T(0), z1 = T(0);
-            if (use1) ld2_rw<COHERENT>(y1 + gbase + sg * B + col, y0, y1v);
-            if (use2) ld2_rw<COHERENT>(y2 + gbase + sg * B + col, z0, z1);
+            if (MODE != kFilter1 && use1) ld2_rw<COHERENT>(y1g + (sg * B + col), y0, y1v);
+            if (MODE == kFilter2 && use2) ld2_rw<COHERENT>(y2g + (sg * B + col), z0, z1);
             // flips inside the tile (shared memory); bit 0 starts the sums (tbits >= 1)
             Dot2 acc0, acc1;
             {
@@ -705,7 +712,7 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
             for (int j = EG; j < ngb; ++j) {
                 const T g = gam_s[tbits + j];
                 T p0, p1;
-                ld2_g<COHERENT>(xg + (sg ^ (static_cast<int64_t>(1) << (tbits + j))) * B + col, p0, p1);
+                ld2_g<COHERENT>(xg + ((sg ^ (1u << (tbits + j))) * B + col), p0, p1);
                 dot2_mad(acc0, g, p0);
                 dot2_mad(acc1, g, p1);
             }
@@ -713,16 +720,16 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
             const T d = ch * dr;
             dot2_mad(acc0, d, a0);
             dot2_mad(acc1, d, a1);
-            if (use1) {
+            if (MODE != kFilter1 && use1) {
                 dot2_mad(acc0, c1, y0);
                 dot2_mad(acc1, c1, y1v);
             }
-            if (use2) {
+            if (MODE == kFilter2 && use2) {
                 dot2_mad(acc0, c2, z0);
                 dot2_mad(acc1, c2, z1);
             }
             const T o0 = dot2_final(acc0), o1 = dot2_final(acc1);
-            if (val) st2(out + gbase + sg * B + col, o0, o1);
+            if (val) st2(outg + (sg * B + col), o0, o1);
             if (want_mom) {
                 const T cx0 = shfl_xor_df(a0, 1), cx1 = shfl_xor_df(a1, 1);   // the other pair's x
                 if (val) {
