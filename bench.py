@@ -69,7 +69,7 @@ def make_inputs(wl, rank=0):
 
 # float32 instructions per double-float fused multiply-add in the library's
 # arithmetic (TwoProduct 2, cross terms 2, TwoSum 6, folding 3, Fast2Sum 3)
-DF32_EVOLVE_TRAFFIC = 302280960 + 103473408   # bytes, step_kernel_df4tb<kEvolve, 11>, one launch
+DF32_EVOLVE_TRAFFIC = 302351616 + 104981760   # bytes, step_kernel_df4tb<kEvolve, 11>, one launch
 # One error-free double-float multiply-add (the Dot2 step): TwoProduct 2,
 # cross terms 2, TwoSum 6, error adds 3 float32 instructions.
 DF_FMA_INSTR = 13
