@@ -229,8 +229,10 @@ dacp_status dacp_get_timings(dacp_handle hd, double* ms);
  * dacp_autotune -- pick how the recurrences are launched by timing `orders`
  * evolution orders of this handle's own realizations for every candidate:
  * tile size (8 to 128 KB of the vector per CTA) x launch mode (per-order
- * launches replayed from a CUDA graph, or one persistent cooperative launch
- * with a grid barrier per order). The fastest is kept and cached for the
+ * launches replayed from a CUDA graph, one persistent cooperative launch
+ * with a grid barrier per order, or -- float32 vectors, where the staged
+ * tiles fit shared memory -- graph-replayed launches with staged tiles, mode 2
+ * of dacp_set_launch). The fastest is kept and cached for the
  * process, keyed by (sorted N list, b, precision). Needs parameters; resets
  * filter and moment results (run dacp_filter again). *tile_bytes_out may be
  * NULL.
@@ -239,9 +241,14 @@ dacp_status dacp_autotune(dacp_handle hd, int orders, int* tile_bytes_out);
 
 /*
  * dacp_set_launch / dacp_get_launch -- set or read the launch mode (0 = graph
- * replay of per-order launches, 1 = persistent cooperative launch) and tile
- * size in bytes (power of two, 1 KB to 128 KB). Setting resets filter and
- * moment results.
+ * replay of per-order launches, 1 = persistent cooperative launch, 2 = as 0
+ * with every HBM read of a tile -- the vector tile H acts on, the recurrence's
+ * previous vectors and the diagonal -- staged in shared memory by bulk copies
+ * at the start of the CTA; float32 vectors only) and tile size in bytes (power
+ * of two, 1 KB to 128 KB). Mode 2 needs (1 + recurrence terms) tiles plus the
+ * tile's diagonal in shared memory, so tiles above 64 KB are refused there
+ * (DACP_ERR_ARG), as is mode 2 on float64 or double-float vectors. Setting
+ * resets filter and moment results.
  */
 dacp_status dacp_set_launch(dacp_handle hd, int mode, int tile_bytes);
 dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);

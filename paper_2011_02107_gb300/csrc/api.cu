@@ -103,7 +103,8 @@ struct dacp_ctx {
     int* step_ctr_d = nullptr;
     int* err_d = nullptr;               // set by a stencil CTA whose bounded wait gave up
     unsigned* bar_d = nullptr;          // grid barrier (count, generation) of the persistent launch
-    int launch_mode = 0;                // 0: per-order launches replayed from a CUDA graph, 1: persistent
+    int launch_mode = 0;                // 0: per-order launches replayed from a CUDA graph, 1: persistent,
+                                        // 2: as 0 with every HBM read of a tile staged (float32 only)
     bool poison_barrier = false;        // test hook: the next persistent launch's barrier never opens
     bool batched_solve = true;          // equal basis sizes: batched cuSOLVER instead of lanes
     double* mom_d = nullptr;
@@ -319,13 +320,17 @@ dacp_status run_orders(dacp_ctx* c, bool filter, int orders,
         if (after) TRY(after(orders));
         return DACP_OK;
     }
+    auto pass = [&](int mode) -> cudaError_t {
+        return c->launch_mode == 2 ? launch_step_staged(c->b, mode, a, 0, ni, c->smem, c->st)
+                                   : launch_step(c->prec, c->b, mode, a, 0, ni, c->smem, c->st);
+    };
     auto launch_order = [&]() -> cudaError_t {
         cudaError_t e;
         if (filter) {
-            if ((e = launch_step(c->prec, c->b, kFilter1, a, 0, ni, c->smem, c->st)) != cudaSuccess) return e;
-            return launch_step(c->prec, c->b, kFilter2, a, 0, ni, c->smem, c->st);
+            if ((e = pass(kFilter1)) != cudaSuccess) return e;
+            return pass(kFilter2);
         }
-        return launch_step(c->prec, c->b, kEvolve, a, 0, ni, c->smem, c->st);
+        return pass(kEvolve);
     };
     Graph& g = filter ? c->gf : c->ge;
     if (!g.exec && orders >= kGraphOrders) {
@@ -396,6 +401,8 @@ dacp_status retile(dacp_ctx* c, int tile_bytes) {
     tile_geometry(c, tile_bytes);
     if (prepare_step(c->prec, c->b, c->smem) != cudaSuccess || prepare_step(c->prec, 1, c->smem) != cudaSuccess)
         return fail(c, DACP_ERR_CUDA, "shared-memory attribute for %d bytes", c->smem);
+    if (c->launch_mode == 2 && prepare_step_staged(c->b, c->smem) != cudaSuccess)
+        return fail(c, DACP_ERR_CUDA, "staged shared-memory attribute for a %d-byte tile", c->smem);
     dfree(c, c->items_d);
     c->items_d = nullptr;
     TRY(dalloc_t(c, &c->items_d, c->items.size()));
@@ -1698,6 +1705,20 @@ dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
     return check_device_flag(c);
 }
 
+// Bytes of the largest vector tile at tile_bytes (as tile_geometry sets c->smem).
+static int tile_smem_for(const dacp_ctx* c, int tile_bytes) {
+    int tb_cap = 0;
+    while ((static_cast<int64_t>(2) << tb_cap) * c->b * static_cast<int64_t>(c->esz) <= tile_bytes) ++tb_cap;
+    int max_tstates = 1;
+    for (int r = 0; r < c->R; ++r) max_tstates = std::max(max_tstates, 1 << std::min(c->info[r].N, tb_cap));
+    return static_cast<int>(max_tstates * c->b * c->esz);
+}
+
+// Launch mode 2 (staged tiles) runs float32 vectors whose staged tiles fit shared memory.
+static bool staged_possible(const dacp_ctx* c, int tile_bytes) {
+    return c->prec == kPrecF32 && staged_fits(c->b, tile_smem_for(c, tile_bytes));
+}
+
 // Tile sizes the autotuner tries, and its cache keyed by (sizes, b, precision).
 static const int kTileCandidates[] = {8192, 16384, 32768, 65536, 131072};
 static const int kNumTiles = 5;
@@ -1721,8 +1742,9 @@ dacp_status dacp_autotune(dacp_handle c, int orders, int* tile_bytes_out) {
     if (best < 0) {
         const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
         double best_ms = 1e300;
-        for (int cand = 0; cand < 2 * kNumTiles; ++cand) {
+        for (int cand = 0; cand < 3 * kNumTiles; ++cand) {
             const int tb = kTileCandidates[cand % kNumTiles];
+            if (cand / kNumTiles == 2 && !staged_possible(c, tb)) continue;
             c->launch_mode = cand / kNumTiles;
             TRY(retile(c, tb));
             TRY(set_evolution_coef(c, c->emax));
@@ -1753,9 +1775,12 @@ dacp_status dacp_autotune(dacp_handle c, int orders, int* tile_bytes_out) {
 
 dacp_status dacp_set_launch(dacp_handle c, int mode, int tile_bytes) {
     TRY(check_handle(c));
-    if (mode != 0 && mode != 1) return fail(c, DACP_ERR_ARG, "launch mode must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(c, DACP_ERR_ARG, "launch mode must be 0, 1 or 2");
     if (tile_bytes < 1024 || tile_bytes > 131072 || (tile_bytes & (tile_bytes - 1)))
         return fail(c, DACP_ERR_ARG, "tile_bytes must be a power of two in [1 KB, 128 KB]");
+    if (mode == 2 && c->prec != kPrecF32) return fail(c, DACP_ERR_ARG, "launch mode 2 runs float32 vectors only");
+    if (mode == 2 && !staged_possible(c, tile_bytes))
+        return fail(c, DACP_ERR_ARG, "staged tiles of %d bytes exceed shared memory", tile_bytes);
     c->launch_mode = mode;
     TRY(retile(c, tile_bytes));
     if (c->state > 1) c->state = 1;

@@ -14,6 +14,12 @@ cudaError_t launch_persistent(int prec, int b, int seq, const StepArgs& a, int n
                               cudaStream_t st, int* grid_out);
 cudaError_t launch_step(int prec, int b, int mode, const StepArgs& a, int item_base, int n_items, int smem,
                         cudaStream_t st);
+// float32 only: recurrence passes with the tile's x, y and diagonal staged by bulk copies
+int staged_smem_bytes(int mode, int b, int tile_smem);
+bool staged_fits(int b, int tile_smem);
+cudaError_t prepare_step_staged(int b, int tile_smem);
+cudaError_t launch_step_staged(int b, int mode, const StepArgs& a, int item_base, int n_items, int tile_smem,
+                               cudaStream_t st);
 cudaError_t launch_diag(int prec, const RealInfo* real, int r, int N, const double* J, const double* h,
                         void* diag, cudaStream_t st);
 cudaError_t launch_diag_all(int prec, const RealInfo* real, int R, int max_N, const double* J, const double* h,

@@ -41,12 +41,14 @@ template <typename T> struct MomOps {
     __device__ static acc zero() { return T(0); }
     __device__ static void mad(acc& s, T a, T b) { s = fma(a, b, s); }
     __device__ static double to_double(acc s) { return static_cast<double>(s); }
+    __device__ static df32 to_df(acc s) { return df32(static_cast<float>(s), 0.f); }   // float32 only
 };
 template <> struct MomOps<df32> {
     using acc = Dot2;
     __device__ static acc zero() { return dot2_zero(); }
     __device__ static void mad(acc& s, df32 a, df32 b) { dot2_mad(s, a, b); }
     __device__ static double to_double(acc s) { return static_cast<double>(s.hi) + static_cast<double>(s.err); }
+    __device__ static df32 to_df(acc s) { return dot2_final(s); }
 };
 
 // L2-coherent scalar load, and read-only scalar load.
@@ -80,6 +82,40 @@ __device__ __forceinline__ void load_vals_ro(const T* __restrict__ p, T (&v)[B])
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ df32 shfl_xor_df(df32 v, int o) {
+    return df32(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+// Sums V = 2^v double-float values per lane over the lanes of a warp and
+// scatters the totals (a reduce-scatter butterfly): at each of the first v
+// levels (lane offsets 16, 8, ...) a lane keeps the half of its values that its
+// lane bit selects and adds the partner's copy of that half; the offsets left,
+// down to OMIN, sum the one value kept. On return (OMIN = 1) lane L holds the
+// total of value L / (32 / V), every lane of a group of 32 / V the same; with
+// OMIN > 1 lanes that differ below OMIN keep separate sums. For V = 32 this is
+// 31 double-float additions per lane on the float32 pipes, where a float64
+// butterfly per value takes 5 V float64 additions: GB300 issues float64 at
+// 1/64 of the float32 rate, and that once-per-tile reduction used to bound the
+// float32 evolution kernel.
+template <int V, int OMIN = 1>
+__device__ __forceinline__ df32 warp_reduce_scatter(df32 (&x)[V], const int lane) {
+    static_assert((V & (V - 1)) == 0 && V <= 32 / OMIN, "V a power of two, at most the lanes summed over");
+#pragma unroll
+    for (int half = V / 2, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const df32 send = up ? x[i] : x[i + half];
+            const df32 keep = up ? x[i + half] : x[i];
+            x[i] = keep + shfl_xor_df(send, o);
+        }
+    }
+    df32 v = x[0];
+#pragma unroll
+    for (int o = 16 / V; o >= OMIN; o >>= 1) v = v + shfl_xor_df(v, o);
     return v;
 }
 
@@ -166,6 +202,21 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// Several bulk copies completing on one barrier phase: one arrive that announces
+// the bytes of all of them, then the copies themselves.
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -210,8 +261,12 @@ constexpr int kMaxGlobalBitsUnrolled = 10;
 
 // One tile of one realization at order `step`. COHERENT = the vectors may have
 // been rewritten earlier in the same (persistent) launch: global reads then
-// bypass L1.
-template <typename T, int B, int MODE, bool COHERENT>
+// bypass L1. STAGED = every HBM read of the tile (x, the recurrence's y1 / y2
+// and the diagonal) lands in shared memory through bulk copies on one barrier
+// phase at the start, so a CTA has its whole input in flight at once instead
+// of a few 16-byte loads per thread; dynamic shared memory then holds
+// [x | y1 | y2 (kFilter2) | diagonal] (see staged_smem_bytes).
+template <typename T, int B, int MODE, bool COHERENT, bool STAGED = false>
 __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, const int step) {
     using U = Unit<T, B>;
     constexpr int VU = U::kVals, SU = U::kStates, LS = U::kLog, UP = UnitsPerPass<T>::value;
@@ -287,9 +342,24 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
         if (tstates >= SU) {
             // ---- unit path: stage the tile with one bulk copy -------------------
             const uint32_t nbytes = static_cast<uint32_t>(tstates) * B * sizeof(T);
+            // staged reads need a diagonal tile of whole 16-byte lines (4 float32 states)
+            const bool stg = STAGED && (static_cast<uint32_t>(tstates) * sizeof(T)) % 16u == 0u;
+            const T* ys1 = tile + static_cast<int64_t>(tstates) * B;        // staged y1
+            const T* ys2 = tile + 2 * static_cast<int64_t>(tstates) * B;    // staged y2 (kFilter2)
+            constexpr int kNY = MODE == kFilter2 ? 2 : (MODE == kFilter1 ? 0 : 1);
+            const T* dsg = tile + (1 + kNY) * static_cast<int64_t>(tstates) * B;   // staged diagonal
             if (tid == 0) {
                 mbar_init(&bar_s, 1);
-                bulk_load(tile, xg + tile0 * B, nbytes, &bar_s);
+                if (stg) {
+                    const uint32_t dbytes = static_cast<uint32_t>(tstates) * sizeof(T);
+                    mbar_expect(&bar_s, nbytes * (1u + (use1 ? 1u : 0u) + (use2 ? 1u : 0u)) + dbytes);
+                    bulk_copy(tile, xg + tile0 * B, nbytes, &bar_s);
+                    if (use1) bulk_copy(const_cast<T*>(ys1), y1 + gbase + tile0 * B, nbytes, &bar_s);
+                    if (use2) bulk_copy(const_cast<T*>(ys2), y2 + gbase + tile0 * B, nbytes, &bar_s);
+                    bulk_copy(const_cast<T*>(dsg), dg + tile0, dbytes, &bar_s);
+                } else {
+                    bulk_load(tile, xg + tile0 * B, nbytes, &bar_s);
+                }
             }
             __syncthreads();
             const bool landed = mbar_wait(&bar_s, 0, kWaitLimit);
@@ -314,10 +384,19 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
                     if (val[k]) {
                         ld_unit<T, B>(tile + uu[k] * VU, xv[k]);
-                        if (kEarlyY && use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
-                        if (kEarlyY && use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
+                        if (STAGED && stg) {
+                            if (use1) ld_unit<T, B>(ys1 + uu[k] * VU, yv[k]);
+                            if (use2) ld_unit<T, B>(ys2 + uu[k] * VU, zv[k]);
 #pragma unroll
-                        for (int j = 0; j < SU; ++j) dv[k][j] = kFold ? ch * ld_ro(dg + s0 + j) : ld_ro(dg + s0 + j);
+                            for (int j = 0; j < SU; ++j)
+                                dv[k][j] = kFold ? ch * dsg[uu[k] * SU + j] : dsg[uu[k] * SU + j];
+                        } else {
+                            if (kEarlyY && use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + s0 * B, yv[k]);
+                            if (kEarlyY && use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + s0 * B, zv[k]);
+#pragma unroll
+                            for (int j = 0; j < SU; ++j)
+                                dv[k][j] = kFold ? ch * ld_ro(dg + s0 + j) : ld_ro(dg + s0 + j);
+                        }
                     }
                 }
 #pragma unroll
@@ -413,7 +492,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 #pragma unroll
                 for (int k = 0; k < UP; ++k) {
                     if (!val[k]) continue;
-                    if (!kEarlyY) {
+                    if (!kEarlyY && !(STAGED && stg)) {
                         const int64_t sy = tile0 + static_cast<int64_t>(uu[k]) * SU;
                         if (use1) ld_unit_rw<T, B, COHERENT>(y1 + gbase + sy * B, yv[k]);
                         if (use2) ld_unit_rw<T, B, COHERENT>(y2 + gbase + sy * B, zv[k]);
@@ -488,14 +567,29 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
 reduce:
     if (want_mom && active) {
         const int lane = tid & 31, warp = tid >> 5;
+        if constexpr (std::is_same<T, double>::value) {
 #pragma unroll
-        for (int p = 0; p < B; ++p)
+            for (int p = 0; p < B; ++p)
 #pragma unroll
-            for (int q = 0; q < B; ++q) {
-                const double v1 = warp_sum(MO::to_double(xx[p < q ? p : q][p < q ? q : p]));
-                const double v2 = warp_sum(MO::to_double(kSymOX ? ox[p < q ? p : q][p < q ? q : p] : ox[p][q]));
-                if (lane == 0) { red_s[warp][p * B + q] = v1; red_s[warp][B * B + p * B + q] = v2; }
-            }
+                for (int q = 0; q < B; ++q) {
+                    const double v1 = warp_sum(MO::to_double(xx[p < q ? p : q][p < q ? q : p]));
+                    const double v2 = warp_sum(MO::to_double(kSymOX ? ox[p < q ? p : q][p < q ? q : p] : ox[p][q]));
+                    if (lane == 0) { red_s[warp][p * B + q] = v1; red_s[warp][B * B + p * B + q] = v2; }
+                }
+        } else {
+            // float32 / double-float partials: the warp sum runs in double-float arithmetic
+            constexpr int V = 2 * B * B, G = 32 / V;
+            df32 xv[V];
+#pragma unroll
+            for (int p = 0; p < B; ++p)
+#pragma unroll
+                for (int q = 0; q < B; ++q) {
+                    xv[p * B + q] = MO::to_df(xx[p < q ? p : q][p < q ? q : p]);
+                    xv[B * B + p * B + q] = MO::to_df(kSymOX ? ox[p < q ? p : q][p < q ? q : p] : ox[p][q]);
+                }
+            const df32 t = warp_reduce_scatter<V>(xv, lane);
+            if (lane % G == 0) red_s[warp][lane / G] = static_cast<double>(t);
+        }
         __syncthreads();
         if (tid < 2 * B * B) {
             double s = 0.0;
@@ -562,10 +656,6 @@ __device__ __forceinline__ void ld2_rw(const df32* p, df32& v0, df32& v1) {
 
 __device__ __forceinline__ void st2(df32* p, df32 v0, df32 v1) {
     *reinterpret_cast<float4*>(p) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
-}
-
-__device__ __forceinline__ df32 shfl_xor_df(df32 v, int m) {
-    return df32(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
 }
 
 static_assert((static_cast<int64_t>(1) << kMaxSpins) * 4 < (static_cast<int64_t>(1) << 31),
@@ -754,32 +844,30 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
 reduce_df4:
     if (want_mom && active) {
         const int lane = tid & 31, warp = tid >> 5;
-        double sv[10];
+        // the ten sums of each pair half, over the 16 lanes of one parity, in
+        // double-float arithmetic (reduce-scatter: lane L keeps sum (L >> 1) & 15)
+        df32 xs[16];
 #pragma unroll
-        for (int e = 0; e < 10; ++e) {
-            double v = static_cast<double>(ms[e].hi) + static_cast<double>(ms[e].err);
-#pragma unroll
-            for (int o = 16; o > 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);   // over lanes of one parity
-            sv[e] = v;
-        }
-        if (lane < 2) {
+        for (int e = 0; e < 16; ++e) xs[e] = e < 10 ? dot2_final(ms[e]) : df32(0.f, 0.f);
+        const df32 t = warp_reduce_scatter<16, 2>(xs, lane);
+        const int e = (lane >> 1) & 15;          // h = lane & 1 is the thread's pair half
+        if (e < 10) {
+            // h = 0 holds columns 0, 1 and <o_p, x_q> across the pairs; h = 1 columns 2, 3 and <x_p, x_q>
+            int blk, p, q;
+            if (e < 6) {
+                blk = e / 3;
+                const int k = e % 3;
+                p = 2 * h + (k == 2 ? 1 : 0);
+                q = 2 * h + (k >= 1 ? 1 : 0);
+            } else {
+                blk = h == 0 ? 1 : 0;
+                p = (e - 6) >> 1;
+                q = 2 + ((e - 6) & 1);
+            }
+            const double v = static_cast<double>(t);
             double* rw = red_s[warp];
-            auto put = [&](int blk, int p, int q, double v) {
-                rw[blk * B * B + p * B + q] = v;
-                rw[blk * B * B + q * B + p] = v;
-            };
-            const int b0 = 2 * lane;
-            put(0, b0, b0, sv[0]);
-            put(0, b0, b0 + 1, sv[1]);
-            put(0, b0 + 1, b0 + 1, sv[2]);
-            put(1, b0, b0, sv[3]);
-            put(1, b0, b0 + 1, sv[4]);
-            put(1, b0 + 1, b0 + 1, sv[5]);
-            const int blk = lane == 0 ? 1 : 0;          // lane 0: <o_p, x_q>; lane 1: <x_p, x_q>
-            put(blk, 0, 2, sv[6]);
-            put(blk, 0, 3, sv[7]);
-            put(blk, 1, 2, sv[8]);
-            put(blk, 1, 3, sv[9]);
+            rw[blk * B * B + p * B + q] = v;
+            rw[blk * B * B + q * B + p] = v;
         }
         __syncthreads();
         if (tid < 2 * B * B) {
@@ -842,6 +930,26 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T, B>::value) step_kernel(
     int step = 0;
     if (MODE != kApply) step = *a.step_ctr;
     tile_step_any<T, B, MODE, false>(a, item_base + blockIdx.x, step);
+    if (MODE == kFilter2 || MODE == kEvolve) {
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(a.launch_done, 1u);
+            if (prev == gridDim.x - 1) {
+                *a.launch_done = 0u;
+                __threadfence();
+                atomicAdd(a.step_ctr, 1);
+            }
+        }
+    }
+}
+
+// float32 recurrences with every HBM read of a tile staged in shared memory by
+// bulk copies (tile_step STAGED); per-order launches, replayed from a graph.
+template <int B, int MODE>
+__global__ void __launch_bounds__(kThreads, MinBlocks<float, B>::value) step_kernel_staged(const StepArgs a,
+                                                                                          int item_base) {
+    const int step = *a.step_ctr;
+    tile_step<float, B, MODE, false, true>(a, item_base + blockIdx.x, step);
     if (MODE == kFilter2 || MODE == kEvolve) {
         if (threadIdx.x == 0) {
             __threadfence();
@@ -970,6 +1078,97 @@ static cudaError_t launch_b(int b, int mode, const StepArgs& a, int item_base, i
         case 1: return launch_mode<T, 1>(mode, a, item_base, n_items, smem, st);
         case 2: return launch_mode<T, 2>(mode, a, item_base, n_items, smem, st);
         case 4: return launch_mode<T, 4>(mode, a, item_base, n_items, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---- staged float32 launches ------------------------------------------------
+
+// Dynamic shared memory of a staged launch whose largest tile takes tile_smem
+// bytes: the x tile, one y tile per recurrence term (kEvolve 1, kFilter2 2) and
+// the tile's float32 diagonal (tile_smem / b bytes).
+int staged_smem_bytes(int mode, int b, int tile_smem) {
+    const int ny = mode == kFilter2 ? 2 : (mode == kFilter1 ? 0 : 1);
+    return tile_smem * (1 + ny) + tile_smem / b;
+}
+
+template <int B, int MODE>
+static bool staged_mode_fits(int tile_smem, int optin) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, step_kernel_staged<B, MODE>) != cudaSuccess) return false;
+    return staged_smem_bytes(MODE, B, tile_smem) + static_cast<int>(fa.sharedSizeBytes) <= optin;
+}
+
+template <int B>
+static bool staged_fits_b(int tile_smem) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    return staged_mode_fits<B, kFilter1>(tile_smem, optin) && staged_mode_fits<B, kFilter2>(tile_smem, optin) &&
+           staged_mode_fits<B, kEvolve>(tile_smem, optin);
+}
+
+// Whether the staged kernels' shared memory fits the device for this tile.
+bool staged_fits(int b, int tile_smem) {
+    switch (b) {
+        case 1: return staged_fits_b<1>(tile_smem);
+        case 2: return staged_fits_b<2>(tile_smem);
+        case 4: return staged_fits_b<4>(tile_smem);
+    }
+    return false;
+}
+
+template <int B>
+static cudaError_t prepare_staged_b(int tile_smem) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(step_kernel_staged<B, kFilter1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  staged_smem_bytes(kFilter1, B, tile_smem))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(step_kernel_staged<B, kFilter2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  staged_smem_bytes(kFilter2, B, tile_smem))) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_kernel_staged<B, kEvolve>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                staged_smem_bytes(kEvolve, B, tile_smem));
+}
+
+// Allow the staged kernels' dynamic shared memory (call staged_fits first);
+// once per handle and tile size, outside any stream capture.
+cudaError_t prepare_step_staged(int b, int tile_smem) {
+    if (!staged_fits(b, tile_smem)) return cudaErrorInvalidValue;
+    switch (b) {
+        case 1: return prepare_staged_b<1>(tile_smem);
+        case 2: return prepare_staged_b<2>(tile_smem);
+        case 4: return prepare_staged_b<4>(tile_smem);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int B>
+static cudaError_t launch_staged_b(int mode, const StepArgs& a, int item_base, int n_items, int tile_smem,
+                                   cudaStream_t st) {
+    switch (mode) {
+        case kFilter1:
+            step_kernel_staged<B, kFilter1><<<n_items, kThreads, staged_smem_bytes(kFilter1, B, tile_smem), st>>>(
+                a, item_base);
+            return cudaGetLastError();
+        case kFilter2:
+            step_kernel_staged<B, kFilter2><<<n_items, kThreads, staged_smem_bytes(kFilter2, B, tile_smem), st>>>(
+                a, item_base);
+            return cudaGetLastError();
+        case kEvolve:
+            step_kernel_staged<B, kEvolve><<<n_items, kThreads, staged_smem_bytes(kEvolve, B, tile_smem), st>>>(
+                a, item_base);
+            return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+// One staged float32 recurrence pass (kFilter1, kFilter2 or kEvolve) over items
+// [item_base, item_base + n_items); tile_smem = bytes of the largest vector tile.
+cudaError_t launch_step_staged(int b, int mode, const StepArgs& a, int item_base, int n_items, int tile_smem,
+                               cudaStream_t st) {
+    switch (b) {
+        case 1: return launch_staged_b<1>(mode, a, item_base, n_items, tile_smem, st);
+        case 2: return launch_staged_b<2>(mode, a, item_base, n_items, tile_smem, st);
+        case 4: return launch_staged_b<4>(mode, a, item_base, n_items, tile_smem, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -7,7 +7,8 @@ launch-mode studies and as a short, fixed-length command for profiler captures.
 
   python -m paper_2011_02107_gb300.kernel_bench [--N 14] [--R 256] [--b 4]
       [--precision fp32] [--orders 200] [--mode -1] [--tile 0]
-mode -1 / tile 0: let dacp_autotune choose.
+mode 0: graph replay of per-order launches, 1: persistent launch, 2: graph
+replay with staged tiles (float32); mode -1 / tile 0: let dacp_autotune choose.
 """
 
 from __future__ import annotations

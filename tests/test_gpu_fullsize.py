@@ -10,7 +10,7 @@ sampled outputs and properties that hold at any size:
     on the oracle's own filtered state (doubling identities against direct products, at full size);
   * |mu_j| <= mu_0 and the requested count, for sampled realizations;
   * sampled realizations' levels against float64 DACP with the paper's parameters, within 1e-2 of the
-    local mean spacing. That judge is itself pinned to the oracle and to dense spectra by the other
+    local mean spacing. That float64 run is itself pinned to the oracle and to dense spectra by the other
     parity tests.
 """
 
