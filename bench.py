@@ -67,12 +67,11 @@ def make_inputs(wl, rank=0):
     return models, psis
 
 
-# float32 instructions per double-float fused multiply-add in the library's
-# arithmetic (TwoProduct 2, cross terms 2, TwoSum 6, folding 3, Fast2Sum 3)
-DF32_EVOLVE_TRAFFIC = None   # bytes of one step_kernel_df4tb<kEvolve, 11> launch (ncu); None until re-captured
+DF32_EVOLVE_TRAFFIC = 302504192 + 104424448   # bytes, step_kernel_df4tb<kEvolve, 11>, one launch (ncu)
 # One error-free double-float multiply-add (the Dot2 step): TwoProduct 2,
-# cross terms 2, TwoSum 6, error adds 3 float32 instructions.
-DF_FMA_INSTR = 13
+# TwoSum 6, and 4 float32 instructions that fold the cross terms and the two
+# rounding errors into the error term.
+DF_FMA_INSTR = 12
 SMS, FP32_LANES_PER_SM = 152, 128
 
 
