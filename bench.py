@@ -494,9 +494,12 @@ def main():
         v = float(np.mean(vals[args.warmup:]))
         print(json.dumps({
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wl["R"] * wl["n_eigs"] / v,      # the whole batch, extrapolated
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "fp64", "data": "synthetic",
-            "config": {"workload": wl["desc"]},
+            "config": {"workload": wl["desc"], "realizations_per_gpu": wl["R"], "N": wl["N"],
+                       "n_eigs": wl["n_eigs"], "block_b": wl["b"], "precision": "fp64 (oracle)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }), flush=True)

@@ -50,6 +50,30 @@ def apply_h(model, x: np.ndarray, diag: np.ndarray | None = None) -> np.ndarray:
     return y
 
 
+def apply_h_rows(model, x: np.ndarray, states, with_abs: bool = False):
+    """Rows `states` of y = H x, one row at a time from the definition: y[s] =
+    diag(s) x[s] + sum_i Gamma_i x[s XOR 2^i]. Only the listed states' diagonal
+    is formed, so this reaches any N the vectors fit in memory (the full
+    ``diagonal`` is O(2^N N^2)). With ``with_abs`` also returns sum_k |term_k|
+    per row, the scale of the round-off a summation of those terms can make."""
+    N = model["N"]
+    st = np.asarray(states, dtype=np.int64)
+    z = 1.0 - 2.0 * ((st[:, None] >> np.arange(N)[None, :]) & 1)          # z_i(s)
+    Ju = np.triu(model["J"], 1)
+    d = z @ model["h"] + np.einsum("si,ij,sj->s", z, Ju, z)
+    xs = x[st]
+    dd = d if x.ndim == 1 else d[:, None]
+    y = dd * xs
+    a = np.abs(dd * xs)
+    for i in range(N):
+        g = model["gamma"][i]
+        if g != 0.0:
+            t = g * x[st ^ (1 << i)]
+            y = y + t
+            a = a + np.abs(t)
+    return (y, a) if with_abs else y
+
+
 _I2 = np.eye(2)
 _X = np.array([[0.0, 1.0], [1.0, 0.0]])
 _Z = np.array([[1.0, 0.0], [0.0, -1.0]])

@@ -113,3 +113,17 @@ def test_planted_mistake_is_caught():
     bad["J"] = Jb
     x = np.random.default_rng(3).standard_normal(1 << 6)
     assert np.abs(Hm.apply_h(bad, x) - Hm.dense_h(m) @ x).max() > 1e-3
+
+
+def test_row_apply_matches_full_apply():
+    """The row-wise apply used for sampled parity at large N equals the full
+    apply (itself pinned to the Kronecker builder) on every row it is given,
+    including the first and last state, for one and several columns."""
+    m = W.random_model(9, seed=11)
+    rng = np.random.default_rng(4)
+    for x in (rng.standard_normal(1 << 9), rng.standard_normal((1 << 9, 3))):
+        full = Hm.apply_h(m, x)
+        rows = np.concatenate([[0, (1 << 9) - 1], rng.integers(0, 1 << 9, size=60)])
+        y, a = Hm.apply_h_rows(m, x, rows, with_abs=True)
+        assert np.abs(y - full[rows]).max() < 1e-13 * np.abs(full).max()
+        assert (a >= np.abs(y) - 1e-12).all()
