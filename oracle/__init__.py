@@ -10,11 +10,13 @@ eye. Library primitives used as single steps: numpy fancy indexing, matrix
 products and LAPACK ``eigh``/``eigvalsh``/``svd``.
 
 Modules
-  hamiltonian    matrix-free H.v (Sec. II intro, Sec. III) and the dense matrix
+  hamiltonian    matrix-free H.v (Sec. II intro, Sec. III) and the dense matrix,
+                 with optional XX / YY pair couplings (XXZ, Heisenberg chains)
   chebyshev      T_k scalar definitions (Appendix A, Eqs. cheb, cheb2, rec)
   dacp           filter, evolution with directly recorded moments, assembly,
                  generalized eigensolve with rank removal (Sec. II, App. B-C)
-  jordan_wigner  closed-form spectrum of the h_z = 0 open chain (Sec. III)
+  jordan_wigner  closed-form spectra: the h_z = 0 open Ising chain (Sec. III) and
+                 the open XX chain in z-fields (free fermions)
   params         E_max upper bound (Lanczos) and DOS-based window (Sec. III)
   metrics        matching against an exact spectrum, local mean spacing
   mlp            plain forward/backward of the parameter MLP

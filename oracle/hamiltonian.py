@@ -2,6 +2,11 @@
 
 H = sum_{i<j} J_ij Z_i Z_j + sum_i h_i Z_i + sum_i Gamma_i X_i on 2^N basis
 states s; Z_i acts on bit i with z_i(s) = 1 - 2*bit_i(s) and X_i flips bit i.
+Models may also carry two-body flip couplings ``Jxx`` and ``Jyy`` (N x N, i<j
+used): + sum_{i<j} (Jxx_ij X_i X_j + Jyy_ij Y_i Y_j). Both flip bits i and j;
+with Y|b> = i z(b) |b XOR 1>, the pair Y_i Y_j carries -z_i(s) z_j(s), which is
+real, so every such H stays a real symmetric matrix (XXZ and Heisenberg chains,
+the paper's native sigma^x sigma^x couplings of Sec. III without rotation).
 
 The paper works in matrix-free mode (Sec. II intro): H is a function taking a
 state to a state, each Pauli term "represented by a specific function"
@@ -19,6 +24,15 @@ def z_signs(N: int) -> np.ndarray:
     """z_i(s) = 1 - 2*bit_i(s) as an (N, 2^N) float64 array."""
     s = np.arange(1 << N)
     return np.stack([1.0 - 2.0 * ((s >> i) & 1) for i in range(N)])
+
+
+def pair_couplings(model):
+    """(Jxx, Jyy) as upper-triangular N x N arrays; zeros when the model has none."""
+    N = model["N"]
+    z = np.zeros((N, N))
+    Jxx = np.triu(np.asarray(model.get("Jxx", z), dtype=np.float64), 1)
+    Jyy = np.triu(np.asarray(model.get("Jyy", z), dtype=np.float64), 1)
+    return Jxx, Jyy
 
 
 def diagonal(model) -> np.ndarray:
@@ -47,6 +61,14 @@ def apply_h(model, x: np.ndarray, diag: np.ndarray | None = None) -> np.ndarray:
         g = model["gamma"][i]
         if g != 0.0:
             y = y + g * x[s ^ (1 << i)]
+    Jxx, Jyy = pair_couplings(model)
+    for i in range(N):
+        for j in range(i + 1, N):
+            if Jxx[i, j] != 0.0 or Jyy[i, j] != 0.0:
+                # <s| (Jxx X_i X_j + Jyy Y_i Y_j) |s'> with s' = s XOR (2^i + 2^j)
+                zz = (1.0 - 2.0 * ((s >> i) & 1)) * (1.0 - 2.0 * ((s >> j) & 1))
+                c = Jxx[i, j] - Jyy[i, j] * zz
+                y = y + (c if x.ndim == 1 else c[:, None]) * x[s ^ ((1 << i) | (1 << j))]
     return y
 
 
@@ -71,11 +93,20 @@ def apply_h_rows(model, x: np.ndarray, states, with_abs: bool = False):
             t = g * x[st ^ (1 << i)]
             y = y + t
             a = a + np.abs(t)
+    Jxx, Jyy = pair_couplings(model)
+    for i in range(N):
+        for j in range(i + 1, N):
+            if Jxx[i, j] != 0.0 or Jyy[i, j] != 0.0:
+                c = Jxx[i, j] - Jyy[i, j] * z[:, i] * z[:, j]
+                t = (c if x.ndim == 1 else c[:, None]) * x[st ^ ((1 << i) | (1 << j))]
+                y = y + t
+                a = a + np.abs(t)
     return (y, a) if with_abs else y
 
 
 _I2 = np.eye(2)
 _X = np.array([[0.0, 1.0], [1.0, 0.0]])
+_Y = np.array([[0.0, -1.0j], [1.0j, 0.0]])
 _Z = np.array([[1.0, 0.0], [0.0, -1.0]])
 
 
@@ -105,6 +136,15 @@ def dense_h(model) -> np.ndarray:
         for j in range(i + 1, N):
             if model["J"][i, j] != 0.0:
                 H += model["J"][i, j] * _site_op(N, {i: _Z, j: _Z})
+    Jxx, Jyy = pair_couplings(model)
+    for i in range(N):
+        for j in range(i + 1, N):
+            if Jxx[i, j] != 0.0:
+                H += Jxx[i, j] * _site_op(N, {i: _X, j: _X})
+            if Jyy[i, j] != 0.0:
+                yy = _site_op(N, {i: _Y, j: _Y})          # complex Kronecker product
+                assert np.abs(yy.imag).max() == 0.0
+                H += Jyy[i, j] * yy.real
     return H
 
 
@@ -112,13 +152,15 @@ def pauli_norm_bound(model) -> float:
     """sum |J| + sum |h| + sum |Gamma|: a rigorous bound on the spectral radius."""
     N = model["N"]
     iu = np.triu_indices(N, 1)
+    Jxx, Jyy = pair_couplings(model)
     return float(np.abs(model["J"][iu]).sum() + np.abs(model["h"]).sum()
-                 + np.abs(model["gamma"]).sum())
+                 + np.abs(model["gamma"]).sum() + np.abs(Jxx).sum() + np.abs(Jyy).sum())
 
 
 def trace_h2_per_state(model) -> float:
     """Tr(H^2)/2^N = sum J_ij^2 + sum h_i^2 + sum Gamma_i^2 (Pauli strings are orthonormal)."""
     N = model["N"]
     iu = np.triu_indices(N, 1)
+    Jxx, Jyy = pair_couplings(model)
     return float((model["J"][iu] ** 2).sum() + (model["h"] ** 2).sum()
-                 + (model["gamma"] ** 2).sum())
+                 + (model["gamma"] ** 2).sum() + (Jxx ** 2).sum() + (Jyy ** 2).sum())

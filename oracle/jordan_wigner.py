@@ -47,3 +47,28 @@ def spectrum(model) -> np.ndarray:
     for s in sig:
         levels = np.concatenate([levels + s, levels - s])
     return np.sort(levels)
+
+
+def hopping_chain_spectrum(t, hz) -> np.ndarray:
+    """All 2^N levels of the open XX chain in a z-field (free fermions).
+
+    H = sum_i t_i (X_i X_{i+1} + Y_i Y_{i+1}) + sum_i hz_i Z_i. With
+    sigma^+- = (X +- iY)/2, t (XX + YY) = 2t (sigma^+_i sigma^-_{i+1} + h.c.),
+    and the Jordan-Wigner map turns it into nearest-neighbour hopping of
+    amplitude 2 t_i (the string cancels between neighbours; the sign of a
+    hopping on an open chain is a gauge choice). With n_i = (1 - Z_i)/2,
+    hz_i Z_i = hz_i - 2 hz_i n_i. So H = sum_i hz_i + c^T A c with A the
+    tridiagonal matrix (A_ii = -2 hz_i, A_{i,i+1} = 2 t_i), and every level is
+    sum_i hz_i + the sum of a subset of A's eigenvalues.
+    """
+    t = np.asarray(t, dtype=np.float64)
+    hz = np.asarray(hz, dtype=np.float64)
+    N = len(hz)
+    A = np.diag(-2.0 * hz)
+    for i in range(N - 1):
+        A[i, i + 1] = A[i + 1, i] = 2.0 * t[i]
+    eps = np.linalg.eigvalsh(A)
+    levels = np.zeros(1)
+    for e in eps:
+        levels = np.concatenate([levels, levels + e])
+    return np.sort(levels + hz.sum())

@@ -232,3 +232,22 @@ def test_residual_norms_flag_a_poor_basis(ritz_case):
     err = np.array([np.abs(rc["E"] - l).min() for l in lam[idx]])
     assert r.max() > 1e3 * DA.residual_norms(rc["Bc"], rc["lam"], rc["H2"])[rc["idx"]].max()
     assert np.all(err <= np.sqrt(r ** 2 + 1e-12 * emax ** 2))
+
+
+def test_end_to_end_random_field_heisenberg_vs_dense():
+    """N=10 random-field Heisenberg chain (XX + YY + ZZ couplings, the many-body
+    localization model), 80 central eigenvalues with b = 4: DACP through the
+    pair-flip apply meets the float64 target against dense eigh."""
+    m = W.heisenberg_chain(10, seed=4, W=2.0)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    psi = W.start_vectors(10, 4, seed=5)
+    emax = P.emax_bound(m, psi[:, 0])
+    assert emax >= np.abs(E).max()
+    mu = P.kpm_moments(m, psi[:, 0], emax, 256)
+    a = P.kpm_window(mu, 1 << 10, emax, 2.0 * 80)
+    n = P.basis_half_size(80, 4, d_ratio=2.0)
+    K = P.filter_order(emax, a)
+    r = DA.dacp(m, psi, emax, a, K, n, 80)
+    assert len(r["eigs"]) == 80
+    ex = MT.central_exact(E, 80)
+    assert np.abs(r["eigs"] - ex).max() < 1e-9 * (E[-1] - E[0])

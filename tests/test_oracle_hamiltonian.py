@@ -127,3 +127,67 @@ def test_row_apply_matches_full_apply():
         y, a = Hm.apply_h_rows(m, x, rows, with_abs=True)
         assert np.abs(y - full[rows]).max() < 1e-13 * np.abs(full).max()
         assert (a >= np.abs(y) - 1e-12).all()
+
+
+def _pair_model(N, seed):
+    m = W.random_model(N, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    m["Jxx"] = np.triu(rng.uniform(-1.0, 1.0, (N, N)), 1)
+    m["Jyy"] = np.triu(rng.uniform(-1.0, 1.0, (N, N)), 1)
+    return m
+
+
+def test_pair_flips_match_kronecker_dense():
+    """XX and YY couplings: the matrix-free pair flips with the -z_i z_j sign of
+    Y_i Y_j equal the Kronecker products of the 2 x 2 Pauli matrices (Y complex,
+    Y x Y real), on one and several columns and on sampled rows."""
+    m = _pair_model(7, seed=5)
+    H = Hm.dense_h(m)
+    assert np.abs(H - H.T).max() == 0.0
+    rng = np.random.default_rng(6)
+    for x in (rng.standard_normal(1 << 7), rng.standard_normal((1 << 7, 3))):
+        ref = H @ x
+        assert np.abs(Hm.apply_h(m, x) - ref).max() < 1e-13 * np.abs(ref).max()
+        rows = rng.integers(0, 1 << 7, size=40)
+        assert np.abs(Hm.apply_h_rows(m, x, rows) - ref[rows]).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_heisenberg_two_spins_closed_form():
+    """J (XX + YY + ZZ) on two spins: sigma_1 . sigma_2 = 2 S(S+1) - 3, so the
+    triplet sits at J (three times) and the singlet at -3J."""
+    J = 0.7
+    m = {"N": 2, "J": np.array([[0.0, J], [0.0, 0.0]]), "h": np.zeros(2), "gamma": np.zeros(2),
+         "Jxx": np.array([[0.0, J], [0.0, 0.0]]), "Jyy": np.array([[0.0, J], [0.0, 0.0]])}
+    assert np.allclose(np.linalg.eigvalsh(Hm.dense_h(m)), [-3 * J, J, J, J], atol=1e-15)
+    # matrix-free: the singlet (|01> - |10>)/sqrt2 is an eigenvector with -3J
+    singlet = np.array([0.0, 1.0, -1.0, 0.0]) / np.sqrt(2.0)
+    assert np.allclose(Hm.apply_h(m, singlet), -3 * J * singlet, atol=1e-15)
+
+
+def test_pair_terms_traces_and_bound():
+    m = _pair_model(8, seed=9)
+    H = Hm.dense_h(m)
+    D = H.shape[0]
+    assert abs(np.trace(H)) < 1e-11                       # pair flips are off-diagonal
+    assert abs(np.trace(H @ H) / D - Hm.trace_h2_per_state(m)) < 1e-11
+    assert np.abs(np.linalg.eigvalsh(H)).max() <= Hm.pauli_norm_bound(m) + 1e-12
+
+
+def test_xx_plus_yy_conserves_magnetization():
+    """With Jxx = Jyy and no x-field the coupling only swaps unequal bits, so
+    H maps each Hamming-weight sector into itself."""
+    m = W.heisenberg_chain(9, seed=2)
+    s = np.arange(1 << 9)
+    weight = np.array([bin(v).count("1") for v in s])
+    x = np.where(weight == 4, np.random.default_rng(1).standard_normal(1 << 9), 0.0)
+    y = Hm.apply_h(m, x)
+    assert np.abs(y[weight != 4]).max() == 0.0 and np.abs(y[weight == 4]).max() > 0.1
+
+
+def test_planted_yy_sign_mistake_is_caught():
+    """Y_i Y_j with +z_i z_j instead of -z_i z_j (i.e. XX - YY pairing terms)
+    changes the spectrum of the XX chain, so the free-fermion pin catches it."""
+    m = W.heisenberg_chain(6, seed=3, delta=0.0)
+    bad = dict(m)
+    bad["Jyy"] = -m["Jyy"]
+    assert np.abs(np.linalg.eigvalsh(Hm.dense_h(bad)) - np.linalg.eigvalsh(Hm.dense_h(m))).max() > 1e-3

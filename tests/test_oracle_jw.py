@@ -38,3 +38,14 @@ def test_jw_rejects_non_chain():
         JW.spectrum(W.chain(4))                  # h_z != 0
     with pytest.raises(ValueError):
         JW.spectrum(W.spin_glass_shard(4, 0))    # all-to-all couplings
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 8])
+def test_xx_chain_free_fermions_match_dense(N):
+    """Open XX chain in random z-fields (XXZ with delta = 0): the subset sums of
+    the hopping matrix's eigenvalues equal the dense spectrum; this pins the
+    pair flips and the sign of Y_i Y_j."""
+    m = W.heisenberg_chain(N, seed=N, J=0.8, delta=0.0, W=1.5)
+    t = [m["Jxx"][i, i + 1] for i in range(N - 1)]
+    ev = np.linalg.eigvalsh(Hm.dense_h(m))
+    assert np.abs(JW.hopping_chain_spectrum(t, m["h"]) - ev).max() < 1e-12 * max(1.0, np.abs(ev).max())

@@ -15,7 +15,9 @@ couplings here and its z-fields become the x-fields (``paper_tfim`` and
 ``paper_spin_glass``).
 
 A model is a dict with keys ``N`` (spins), ``J`` (N x N float64, only i<j
-used), ``h`` (N float64) and ``gamma`` (N float64).
+used), ``h`` (N float64) and ``gamma`` (N float64). Models with two-body flip
+couplings (``heisenberg_chain``) also carry ``Jxx`` and ``Jyy`` (N x N, i<j
+used) for + sum_{i<j} (Jxx_ij X_i X_j + Jyy_ij Y_i Y_j).
 """
 
 from __future__ import annotations
@@ -28,6 +30,7 @@ __all__ = [
     "paper_tfim",
     "paper_spin_glass",
     "random_model",
+    "heisenberg_chain",
     "start_vectors",
     "pack_models",
 ]
@@ -106,6 +109,25 @@ def random_model(N: int, seed: int, density: float = 1.0, scale: float = 1.0):
     h = rng.uniform(-scale, scale, size=N)
     gamma = rng.uniform(0.2 * scale, scale, size=N)
     return _model(N, Jm, h, gamma)
+
+
+def heisenberg_chain(N: int, seed: int, J: float = 1.0, delta: float = 1.0, W: float = 3.0,
+                     gamma: float = 0.0):
+    """Open random-field XXZ chain (the standard many-body-localization model):
+    J sum (X_i X_{i+1} + Y_i Y_{i+1} + delta Z_i Z_{i+1}) + sum h_i Z_i + gamma sum X_i,
+    h_i ~ U[-W, W] from numpy PCG64(seed). delta = 1 is the Heisenberg chain.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = rng.uniform(-W, W, size=N)
+    Jz = np.zeros((N, N))
+    Jp = np.zeros((N, N))
+    for i in range(N - 1):
+        Jz[i, i + 1] = J * delta
+        Jp[i, i + 1] = J
+    m = _model(N, Jz, h, np.full(N, float(gamma)))
+    m["Jxx"] = Jp.copy()
+    m["Jyy"] = Jp.copy()
+    return m
 
 
 def start_vectors(N: int, b: int, seed: int, r: int = 0) -> np.ndarray:
