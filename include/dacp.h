@@ -77,6 +77,27 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins,
                         int block_b, int precision, const double* psi0, void* stream);
 
 /*
+ * dacp_set_pair_couplings -- add two-body flip couplings
+ *   sum_{i<j} (Jxx_ij X_i X_j + Jyy_ij Y_i Y_j)
+ * to every realization's H. These give XXZ and Heisenberg chains, and the
+ * paper's own sigma^x sigma^x couplings (Sec. III) without the Hadamard
+ * rotation. Both terms flip bits i and j. Y_i Y_j carries the real sign
+ * -z_i(s) z_j(s), so the vectors stay real.
+ *   Jxx, Jyy  concatenated row-major N_r x N_r blocks laid out like J in
+ *             dacp_create (only i<j read). NULL means all zero. Copied; the
+ *             caller keeps ownership.
+ * A call replaces the couplings of any earlier call; all zero removes them.
+ * The Pauli 1-norm that clamps the E_max bound grows by sum |Jxx| + |Jyy|.
+ * Every stencil pass (filter, evolution, Lanczos, KPM, dacp_apply_h) then
+ * includes the pair flips, read element by element. The launch uses the
+ * generic kernels rather than the ones specialised on a uniform tile size.
+ * Parameters and results are reset (as after dacp_create): set or choose
+ * parameters again.
+ * Errors: DACP_ERR_ARG for a non-finite coupling; DACP_ERR_NOMEM, DACP_ERR_CUDA.
+ */
+dacp_status dacp_set_pair_couplings(dacp_handle hd, const double* Jxx, const double* Jyy);
+
+/*
  * dacp_set_params -- explicit per-realization parameters (arrays of n_real).
  *   emax  bound on |E| (E_min = -E_max, Sec. II A); must be a true bound.
  *   a     window half-width, 0 < a < emax (Sec. II A).

@@ -35,7 +35,7 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
-           "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver"]
+           "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -72,6 +72,7 @@ def _load():
         "dacp_solve": [P, I, D, D, P, P, P],
         "dacp_eigenvectors": [P, I, I, D, D, P, P, L, P],
         "dacp_apply_h": [P, I, P, P],
+        "dacp_set_pair_couplings": [P, P, P],
         "dacp_get_timings": [P, P],
         "dacp_get_launch_count": [P, ctypes.POINTER(L)],
         "dacp_mlp_create": [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64, P],
@@ -218,6 +219,12 @@ def dacp_eigenvectors(hd, r, n_eigs, phi_dev_ptr, ld, window=0.0, eps=0.0):
     _check(hd, _lib.dacp_eigenvectors(hd, int(r), int(n_eigs), float(window), float(eps), _ptr(eigs),
                                       ctypes.c_void_p(phi_dev_ptr), int(ld), ctypes.byref(nf)))
     return eigs[:max(nf.value, 0)], nf.value
+
+
+def dacp_set_pair_couplings(hd, Jxx, Jyy):
+    Jxx = np.ascontiguousarray(Jxx, dtype=np.float64)
+    Jyy = np.ascontiguousarray(Jyy, dtype=np.float64)
+    _check(hd, _lib.dacp_set_pair_couplings(hd, _ptr(Jxx), _ptr(Jyy)))
 
 
 def dacp_apply_h(hd, r, x_dev_ptr, y_dev_ptr):
@@ -394,6 +401,17 @@ class Dacp:
         self.stream = stream
         psi0 = np.concatenate([p.ravel() for p in self.psi0_list])
         self.handle = dacp_create(n_spins, J, h, g, block_b, precision, psi0, stream)
+        if any("Jxx" in m or "Jyy" in m for m in self.models):
+            z = [np.zeros((m["N"], m["N"])) for m in self.models]
+            Jxx = np.concatenate([np.asarray(m.get("Jxx", zz), dtype=np.float64).ravel()
+                                  for m, zz in zip(self.models, z)])
+            Jyy = np.concatenate([np.asarray(m.get("Jyy", zz), dtype=np.float64).ravel()
+                                  for m, zz in zip(self.models, z)])
+            try:
+                dacp_set_pair_couplings(self.handle, Jxx, Jyy)
+            except Exception:
+                dacp_destroy(self.handle)
+                raise
 
     def set_params(self, emax, a, K, n):
         R = self.R

@@ -88,7 +88,12 @@ struct dacp_ctx {
     int tile_bytes = 0;
     int tb_uniform = 0;                 // tile bits shared by every realization, else 0
     std::vector<double> J_h, h_h, g_h;   // [R][kMaxSpins(^2)]
-    std::vector<double> pnorm;
+    std::vector<double> pnorm;          // Pauli 1-norm of each H: clamp of the E_max bound
+    std::vector<double> pnorm0;         // the same without the pair couplings
+    bool has_pairs = false;             // dacp_set_pair_couplings gave nonzero XX / YY terms
+    int* n_pairs_d = nullptr;           // [R]
+    int* pair_ij_d = nullptr;           // [R][kMaxPairs]
+    double* pair_c_d = nullptr;         // [R][kMaxPairs][2]
 
     // device
     std::vector<void*> allocs;
@@ -294,7 +299,13 @@ StepArgs base_args(dacp_ctx* c) {
     a.err_flag = c->err_d;
     a.bar_count = c->bar_d;
     a.bar_gen = c->bar_d + 1;
-    a.tbits_uniform = c->tb_uniform;
+    // the kernels specialised on a uniform tile size carry no pair terms
+    a.tbits_uniform = c->has_pairs ? 0 : c->tb_uniform;
+    if (c->has_pairs) {
+        a.n_pairs = c->n_pairs_d;
+        a.pair_ij = c->pair_ij_d;
+        a.pair_c = c->pair_c_d;
+    }
     return a;
 }
 
@@ -596,6 +607,7 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         off += ((static_cast<int64_t>(1) << Nr) + 3) & ~static_cast<int64_t>(3);   // 16-byte aligned units
     }
     c->Dtot = off;
+    c->pnorm0 = c->pnorm;
     tile_geometry(c, kTileBytes);
     c->emax.assign(n_real, 0.0);
     c->a.assign(n_real, 0.0);
@@ -1784,6 +1796,52 @@ dacp_status dacp_set_launch(dacp_handle c, int mode, int tile_bytes) {
     c->launch_mode = mode;
     TRY(retile(c, tile_bytes));
     if (c->state > 1) c->state = 1;
+    return DACP_OK;
+}
+
+dacp_status dacp_set_pair_couplings(dacp_handle c, const double* Jxx, const double* Jyy) {
+    TRY(check_handle(c));
+    std::vector<int> np(c->R, 0), ij(static_cast<size_t>(c->R) * kMaxPairs, 0);
+    std::vector<double> cf(static_cast<size_t>(c->R) * kMaxPairs * 2, 0.0);
+    std::vector<double> pn = c->pnorm0;
+    int64_t jo = 0;
+    for (int r = 0; r < c->R; ++r) {
+        const int Nr = c->N[r];
+        for (int i = 0; i < Nr; ++i)
+            for (int j = i + 1; j < Nr; ++j) {
+                const double x = Jxx ? Jxx[jo + static_cast<int64_t>(i) * Nr + j] : 0.0;
+                const double y = Jyy ? Jyy[jo + static_cast<int64_t>(i) * Nr + j] : 0.0;
+                if (!isfinite(x) || !isfinite(y)) return fail(c, DACP_ERR_ARG, "non-finite pair coupling");
+                if (x == 0.0 && y == 0.0) continue;
+                const size_t t = static_cast<size_t>(r) * kMaxPairs + np[r]++;
+                ij[t] = i | (j << 8);
+                cf[2 * t] = x - y;          // bits i and j equal: z_i z_j = +1
+                cf[2 * t + 1] = x + y;      // bits differ: z_i z_j = -1
+                pn[r] += fabs(x) + fabs(y);
+            }
+        jo += static_cast<int64_t>(Nr) * Nr;
+    }
+    bool any = false;
+    for (int r = 0; r < c->R; ++r) any = any || np[r] > 0;
+    if (any && !c->n_pairs_d) {
+        TRY(dalloc_t(c, &c->n_pairs_d, static_cast<size_t>(c->R)));
+        TRY(dalloc_t(c, &c->pair_ij_d, ij.size()));
+        TRY(dalloc_t(c, &c->pair_c_d, cf.size()));
+    }
+    if (any) {
+        CK(cudaMemcpyAsync(c->n_pairs_d, np.data(), sizeof(int) * np.size(), cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(c->pair_ij_d, ij.data(), sizeof(int) * ij.size(), cudaMemcpyHostToDevice, c->st));
+        CK(cudaMemcpyAsync(c->pair_c_d, cf.data(), sizeof(double) * cf.size(), cudaMemcpyHostToDevice, c->st));
+    }
+    c->pnorm = pn;
+    CK(cudaMemcpyAsync(c->pnorm_d, c->pnorm.data(), sizeof(double) * c->R, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->has_pairs = any;
+    for (Graph* g : {&c->gf, &c->ge}) {          // captured launches hold the old arguments
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+    }
+    c->state = 0;                                 // H changed: parameters and results are stale
     return DACP_OK;
 }
 

@@ -10,6 +10,7 @@ namespace dacp {
 
 constexpr int kThreads = 256;       // threads per CTA of the stencil kernels
 constexpr int kMaxSpins = 26;       // N limit (2^26 states per realization)
+constexpr int kMaxPairs = kMaxSpins * (kMaxSpins - 1) / 2;   // two-body flip terms per realization
 constexpr int kTileBytes = 65536;   // shared-memory tile of one stencil CTA
 constexpr int kFeatureMoments = 32; // Chebyshev moments fed to the parameter network
 constexpr int kFeatures = 8 + kFeatureMoments;
@@ -91,6 +92,11 @@ struct StepArgs {
     unsigned* bar_gen;       // and generation
     int tbits_uniform;       // > 0: every realization's tile has this many bits (lets a launch pick a
                              // kernel specialised on it); 0: mixed
+    // two-body flip couplings sum_{i<j} (Jxx_ij X_i X_j + Jyy_ij Y_i Y_j); n_pairs == nullptr: none
+    const int* n_pairs;      // [R] terms of each realization
+    const int* pair_ij;      // [R][kMaxPairs] bit i | (bit j << 8), i < j
+    const double* pair_c;    // [R][kMaxPairs][2] coefficient when bits i, j are equal (Jxx - Jyy)
+                             // and when they differ (Jxx + Jyy)
 };
 
 }  // namespace dacp

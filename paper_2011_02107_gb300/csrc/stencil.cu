@@ -489,6 +489,36 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                         for (int v = 0; v < VU; ++v) AC::mad(acc[k][v], g, pv[v]);
                     }
                 }
+                // two-body flips X_i X_j, Y_i Y_j: partner s XOR (2^i + 2^j) with coefficient
+                // Jxx - Jyy z_i(s) z_j(s); element by element, from the tile when both bits lie
+                // inside it, else from global memory
+                const int npair = a.n_pairs ? a.n_pairs[it.r] : 0;
+                for (int t = 0; t < npair; ++t) {
+                    const int ij = __ldg(a.pair_ij + it.r * kMaxPairs + t);
+                    const int pi = ij & 255, pj = ij >> 8;
+                    const double* pc = a.pair_c + (static_cast<int64_t>(it.r) * kMaxPairs + t) * 2;
+                    const T ceq = kFold ? ch * static_cast<T>(__ldg(pc)) : static_cast<T>(__ldg(pc));
+                    const T cne = kFold ? ch * static_cast<T>(__ldg(pc + 1)) : static_cast<T>(__ldg(pc + 1));
+                    const int64_t msk = (static_cast<int64_t>(1) << pi) | (static_cast<int64_t>(1) << pj);
+                    const bool inside = pj < R.tbits;
+#pragma unroll
+                    for (int k = 0; k < UP; ++k) {
+                        if (!val[k]) continue;
+#pragma unroll
+                        for (int js = 0; js < SU; ++js) {
+                            const int64_t sl = static_cast<int64_t>(uu[k]) * SU + js;   // state within the tile
+                            const int64_t sx = tile0 + sl;
+                            const T cf2 = (((sx >> pi) ^ (sx >> pj)) & 1) ? cne : ceq;
+#pragma unroll
+                            for (int col = 0; col < B; ++col) {
+                                const T xp = inside ? tile[(sl ^ msk) * B + col]
+                                                    : (COHERENT ? ld_cg(xg + (sx ^ msk) * B + col)
+                                                                : ld_ro(xg + (sx ^ msk) * B + col));
+                                AC::mad(acc[k][js * B + col], cf2, xp);
+                            }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < UP; ++k) {
                     if (!val[k]) continue;
@@ -805,6 +835,22 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
                 ld2_g<COHERENT>(xg + ((sg ^ (1u << (tbits + j))) * B + col), p0, p1);
                 dot2_mad(acc0, g, p0);
                 dot2_mad(acc1, g, p1);
+            }
+            if constexpr (TB == 0) {
+                // two-body flips (the launch picks TB = 0 when the handle has them)
+                const int npair = a.n_pairs ? a.n_pairs[it.r] : 0;
+                for (int t = 0; t < npair; ++t) {
+                    const int ij = __ldg(a.pair_ij + it.r * kMaxPairs + t);
+                    const int pi = ij & 255, pj = ij >> 8;
+                    const double* pc = a.pair_c + (static_cast<int64_t>(it.r) * kMaxPairs + t) * 2;
+                    const uint32_t msk = (1u << pi) | (1u << pj);
+                    const T cf2 = ch * T(__ldg(pc + (((sg >> pi) ^ (sg >> pj)) & 1u)));
+                    T p0, p1;
+                    if (pj < tbits) ld2_s(tile + (static_cast<uint32_t>(sl) ^ msk) * B + col, p0, p1);
+                    else ld2_g<COHERENT>(xg + ((sg ^ msk) * B + col), p0, p1);
+                    dot2_mad(acc0, cf2, p0);
+                    dot2_mad(acc1, cf2, p1);
+                }
             }
             // diagonal term, then w_{k+1} = c_h H x + c_1 y + c_2 z
             const T d = ch * dr;
