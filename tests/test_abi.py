@@ -60,3 +60,12 @@ def test_argument_errors_need_no_gpu(lib):
     with pytest.raises(P.DacpError) as e:
         P.dacp_create(np.array([40], dtype=np.int32), np.zeros(1), np.zeros(1), np.zeros(1), 1, 0, np.zeros(1))
     assert e.value.status == 1          # N beyond 26
+    with pytest.raises(P.DacpError) as e:
+        P.dacp_create(np.array([], dtype=np.int32), np.zeros(1), np.zeros(1), np.zeros(1), 1, 0, np.zeros(1))
+    assert e.value.status == 1          # empty batch
+    with pytest.raises(P.DacpError) as e:
+        P.dacp_create(np.array([0], dtype=np.int32), np.zeros(1), np.zeros(1), np.zeros(1), 1, 0, np.zeros(1))
+    assert e.value.status == 1          # a realization without spins
+    with pytest.raises(P.DacpError) as e:
+        P.dacp_create(np.array([3], dtype=np.int32), np.zeros(9), np.zeros(3), np.zeros(3), 1, 7, np.zeros(8))
+    assert e.value.status == 1          # unknown precision
