@@ -132,36 +132,51 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk, launch_mode=0):
             "algorithmic": f"{fma_per_state} float64 FMA per state and order"}
 
 
-GOLDEN_DENSE = os.path.join(ROOT, "tests", "golden", "shard14_dense_central_levels.txt")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
-def exact_accuracy(wl, rank, last_eigs, n_eigs, path=GOLDEN_DENSE):
+def _exact_levels(wl):
+    """{realization: exact levels ascending} for the workloads with a stored dense
+    spectrum (tests/golden, written by the generator scripts beside them), else None:
+    the 256-shard N = 14 batch (realizations 0, 64, 128, 192) and the N = 16
+    mixed-field chain."""
+    levels = {}
+    if wl["kind"] == "sgs" and wl["N"] == 14:
+        with open(os.path.join(GOLDEN, "shard14_dense_central_levels.txt")) as f:
+            for line in f:
+                row = line.split()
+                if line.startswith("#") or len(row) != 2:    # (seed, level); three columns hold the bounds
+                    continue
+                levels.setdefault(int(row[0]), []).append(float(row[1]))
+    elif wl["kind"] == "chain" and wl["N"] == 16:
+        with open(os.path.join(GOLDEN, "chain16_dense_central_levels.txt")) as f:
+            rows = [line.split() for line in f if not line.startswith("#") and line.strip()]
+        levels[0] = [float(r[0]) for r in rows[1:]]              # the first row holds the bounds
+    else:
+        return None
+    return {k: np.asarray(v) for k, v in levels.items()}
+
+
+def exact_accuracy(wl, rank, last_eigs, n_eigs):
     """Worst error, in local mean spacings, of the timed path's levels against the
-    exact levels of realizations 0, 64, 128 and 192 of the 256-shard N = 14 batch
-    (dense float64 eigh, stored under tests/golden by its generator script).
-    None for other workloads or ranks; never raises (the line then carries the
-    error message)."""
+    exact levels of the realizations that have a stored dense spectrum (see
+    _exact_levels). None for other workloads, other ranks or more levels than
+    stored; never raises (the line then carries the error message)."""
     try:
-        if not (wl["kind"] == "sgs" and wl["N"] == 14 and rank == 0 and n_eigs <= 600 and os.path.exists(path)):
+        if rank != 0:
+            return None
+        levels = _exact_levels(wl)
+        if not levels:
             return None
         from paper_2011_02107_gb300 import train_mlp
-        levels = {}
-        with open(path) as f:
-            for line in f:
-                if line.startswith("#") or not line.strip():
-                    continue
-                row = line.split()
-                if len(row) == 2:                   # (seed, level); three columns hold the bounds
-                    levels.setdefault(int(row[0]), []).append(float(row[1]))
         errs = {}
-        for seed, lv in sorted(levels.items()):
-            if seed >= len(last_eigs):
+        for r, lv in sorted(levels.items()):
+            if r >= len(last_eigs) or n_eigs > len(lv) - 40:
                 continue
-            lv = np.asarray(lv)
             ref = np.sort(lv[np.argsort(np.abs(lv), kind="stable")[:n_eigs]])
-            got = np.asarray(last_eigs[seed], dtype=np.float64)
+            got = np.asarray(last_eigs[r], dtype=np.float64)
             got = got[np.isfinite(got)]
-            errs[seed] = train_mlp.accurate(got[:n_eigs], ref)[1] if len(got) >= n_eigs else float("inf")
+            errs[r] = train_mlp.accurate(got[:n_eigs], ref)[1] if len(got) >= n_eigs else float("inf")
         if not errs:
             return None
         return {"realizations": sorted(errs), "reference": "exact levels, dense float64 eigh",

@@ -81,5 +81,5 @@ def test_exact_accuracy_reports_errors_in_spacings(bench):
     # a short list counts as a miss; other workloads and ranks are not checked
     last[0] = central[0][:10]
     assert bench.exact_accuracy(wl, 0, last, n)["max_spacing_err"] == float("inf")
-    assert bench.exact_accuracy(bench.WORKLOADS["c2"], 0, last, n) is None
+    assert bench.exact_accuracy(bench.WORKLOADS["c1"], 0, last, n) is None
     assert bench.exact_accuracy(wl, 1, last, n) is None
