@@ -78,6 +78,7 @@ def test_exact_accuracy_reports_errors_in_spacings(bench):
     last[64][i] += 0.5 * sp
     out = bench.exact_accuracy(wl, 0, last, n)
     assert abs(out["max_spacing_err"] - 0.5) < 1e-9 and out["within_1e-2"] == 3
+    assert out["median_spacing_err"] == 0.0 and out["p99_spacing_err"] < 0.5
     # a short list counts as a miss; other workloads and ranks are not checked
     last[0] = central[0][:10]
     assert bench.exact_accuracy(wl, 0, last, n)["max_spacing_err"] == float("inf")
