@@ -84,3 +84,27 @@ def test_exact_accuracy_reports_errors_in_spacings(bench):
     assert bench.exact_accuracy(wl, 0, last, n)["max_spacing_err"] == float("inf")
     assert bench.exact_accuracy(bench.WORKLOADS["c1"], 0, last, n) is None
     assert bench.exact_accuracy(wl, 1, last, n) is None
+
+
+def test_chain16_fixture_shape_and_bounds():
+    """The N = 16 mixed-field chain's exact central levels (two mirror-sector
+    blocks, tests/golden/make_chain16_dense_levels.py): 1100 sorted levels
+    around E = 0 inside the Pauli bound, with the Gaussian-density spacing."""
+    rows = read_golden("chain16_dense_central_levels.txt")
+    emin, emax = float(rows[0][0]), float(rows[0][1])
+    v = np.array([float(r[0]) for r in rows[1:]])
+    m = W.chain(16)
+    assert len(v) == 1100 and np.all(np.diff(v) >= 0) and v[0] < 0 < v[-1]
+    assert -Hm.pauli_norm_bound(m) <= emin < v[0] and v[-1] < emax <= Hm.pauli_norm_bound(m)
+    assert max(-emin, emax) ** 2 <= (1 << 16) * Hm.trace_h2_per_state(m)
+    spacing = np.sqrt(2 * np.pi) * np.sqrt(Hm.trace_h2_per_state(m)) / (1 << 16)
+    assert 0.3 * spacing < np.mean(np.diff(v)) < 3.0 * spacing
+
+
+def test_exact_accuracy_on_the_chain(bench):
+    rows = read_golden("chain16_dense_central_levels.txt")
+    v = np.array([float(r[0]) for r in rows[1:]])
+    n = 1000
+    central = np.sort(v[np.argsort(np.abs(v), kind="stable")[:n]])
+    out = bench.exact_accuracy(bench.WORKLOADS["c2"], 0, [central], n)
+    assert out["realizations"] == [0] and out["max_spacing_err"] == 0.0 and out["within_1e-2"] == 1
