@@ -21,7 +21,8 @@ Modules
   metrics        matching against an exact spectrum, local mean spacing
   mlp            plain forward/backward of the parameter MLP
 
-Parity status: every function is pinned by a test in tests/test_oracle_*.py
-except ``params.kpm_window`` (a heuristic; parity unpinned beyond its DOS
-count identity) -- see the module docstrings.
+Parity status: every function is pinned by a test in tests/test_oracle_*.py.
+``params.kpm_window`` is a heuristic. It is pinned by its count identity and by
+exact level counts of four N = 14 shards (dense eigh), to within 10 %; see the
+module docstrings.
 """

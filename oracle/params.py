@@ -19,8 +19,11 @@ Readings (the paper only cites these estimators):
     rank removal, and the accuracy falls off toward the window edge (the
     "inverted filter shape" of Fig. 2), so the window holds twice the levels
     that are returned.
-``kpm_window`` is a heuristic: parity unpinned beyond the count identity and
-the large-M convergence tested in tests/test_oracle_params.py.
+``kpm_window`` is a heuristic (one stochastic start vector, 256 damped
+moments). Its pins, in tests/test_oracle_params.py, are the count identity, the
+large-M convergence, and exact level counts at N = 14: on four benchmark shards
+its windows hold within 10 % of the requested number of exact levels (observed
+within 3 %).
 """
 
 from __future__ import annotations

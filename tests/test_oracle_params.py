@@ -69,3 +69,27 @@ def test_kpm_count_converges_to_weighted_count():
 def test_filter_order_and_basis():
     assert P.filter_order(10.0, 1.0) == 180
     assert P.basis_half_size(100, 4, d_ratio=2.0) == 37     # 4(2n+1) = 300
+
+
+def test_kpm_window_counts_against_exact_levels_at_benchmark_size():
+    """At N = 14 (four shards of the benchmark batch), the window that the KPM
+    estimate from one start vector and 256 Jackson-damped moments puts around
+    d levels holds d levels of the exact spectrum (dense eigh,
+    tests/golden/shard14_dense_central_levels.txt) to within 10 %."""
+    from tests.conftest import read_golden
+    lv = {}
+    for row in read_golden("shard14_dense_central_levels.txt"):
+        if len(row) == 2:
+            lv.setdefault(int(row[0]), []).append(float(row[1]))
+    for seed, v in lv.items():
+        m = W.spin_glass_shard(14, seed=seed)
+        psi = W.start_vectors(14, 1, seed=0, r=seed)[:, 0]
+        diag = Hm.diagonal(m)
+        emax = P.emax_bound(m, psi, diag=diag)
+        mu = P.kpm_moments(m, psi, emax, 256, diag=diag)
+        v = np.asarray(v)
+        for target in (200, 400, 600):
+            a = P.kpm_window(mu, 1 << 14, emax, target)
+            assert a < v[-1] and -a > v[0]                  # inside the stored levels
+            count = int(np.sum(np.abs(v) <= a))
+            assert abs(count - target) <= 0.1 * target, (seed, target, count)
