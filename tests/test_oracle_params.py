@@ -93,3 +93,24 @@ def test_kpm_window_counts_against_exact_levels_at_benchmark_size():
             assert a < v[-1] and -a > v[0]                  # inside the stored levels
             count = int(np.sum(np.abs(v) <= a))
             assert abs(count - target) <= 0.1 * target, (seed, target, count)
+
+
+def test_emax_bound_holds_against_exact_extremes_at_benchmark_sizes():
+    """The Lanczos E_max bound must exceed every |E| (Sec. II A: a level beyond it
+    grows exponentially in both recurrences). Checked against the exact extreme
+    levels (dense eigh, tests/golden) of four N = 14 shards and of the N = 16
+    mixed-field chain. The bound is loose: 1.36 to 1.50 times the spectral
+    radius on these five, which the filter order and the evolution length pay
+    for in proportion (both scale with E_max / a)."""
+    from tests.conftest import read_golden
+    cases = []
+    for row in read_golden("shard14_dense_central_levels.txt"):
+        if len(row) == 3:
+            cases.append((W.spin_glass_shard(14, seed=int(row[0])), float(row[1]), float(row[2]), int(row[0])))
+    row = read_golden("chain16_dense_central_levels.txt")[0]
+    cases.append((W.chain(16), float(row[0]), float(row[1]), 0))
+    for m, emin, emax_exact, r in cases:
+        psi = W.start_vectors(m["N"], 1, seed=0, r=r)[:, 0]
+        radius = max(-emin, emax_exact)
+        bound = P.emax_bound(m, psi)
+        assert radius <= bound <= min(1.6 * radius, Hm.pauli_norm_bound(m)), (m["N"], r, radius, bound)
