@@ -57,11 +57,26 @@ def lanczos_tridiagonal(model, v0, steps: int = 20, diag=None):
     return np.array(alphas), np.array(betas)
 
 
-def emax_bound(model, v0, steps: int = 20, safety: float = 1e-3, diag=None) -> float:
-    """Upper bound on max |E|: Lanczos extreme Ritz values plus the residual norm."""
+def emax_bound(model, v0, steps: int = 20, safety: float = 1e-3, diag=None, rule: str = "residual") -> float:
+    """Upper bound on max |E| from k Lanczos steps (the estimator Sec. III cites).
+
+    rule "residual": the extreme Ritz value plus the whole residual norm
+    beta_{k+1} (the form the CUDA path uses). rule "ritz": the extreme Ritz value
+    plus beta_{k+1} max_i |e_k^T z_i|, the largest residual of any Ritz pair
+    (z_i the eigenvectors of the tridiagonal matrix). "ritz" is tighter (about
+    1.14 times the spectral radius on N = 11..16 shards and chains, against
+    1.36..1.54), but it is a bound only in practice. The residual of the extreme
+    Ritz pair alone fell below the radius on 12 of 150 N = 11 shards.
+    """
     al, be = lanczos_tridiagonal(model, v0, min(steps, 1 << model["N"]), diag)
     k = len(al)
     T = np.diag(al) + np.diag(be[:k - 1], 1) + np.diag(be[:k - 1], -1)
+    if rule == "ritz":
+        th, Z = np.linalg.eigh(T)
+        bound = max(abs(th[0]), abs(th[-1])) + be[k - 1] * float(np.abs(Z[-1, :]).max())
+        return float(min(bound * (1.0 + safety), pauli_norm_bound(model)))
+    if rule != "residual":
+        raise ValueError(rule)
     th = np.linalg.eigvalsh(T)
     bound = max(abs(th[0]), abs(th[-1])) + be[k - 1]
     return float(min(bound * (1.0 + safety), pauli_norm_bound(model)))

@@ -114,3 +114,27 @@ def test_emax_bound_holds_against_exact_extremes_at_benchmark_sizes():
         radius = max(-emin, emax_exact)
         bound = P.emax_bound(m, psi)
         assert radius <= bound <= min(1.6 * radius, Hm.pauli_norm_bound(m)), (m["N"], r, radius, bound)
+
+
+def test_ritz_rule_is_tighter_and_still_above_the_radius():
+    """The Ritz-residual rule against exact spectral radii: 40 N = 10 shards
+    (dense eigh) and the five benchmark-size cases (tests/golden). It stays
+    above the radius on every one and below 1.25 times it, where the residual
+    rule sits near 1.46."""
+    from tests.conftest import read_golden
+    cases = []
+    for seed in range(40):
+        m = W.spin_glass_shard(10, seed=500 + seed)
+        E = np.linalg.eigvalsh(Hm.dense_h(m))
+        cases.append((m, max(-E[0], E[-1]), seed))
+    for row in read_golden("shard14_dense_central_levels.txt"):
+        if len(row) == 3:
+            cases.append((W.spin_glass_shard(14, seed=int(row[0])), max(-float(row[1]), float(row[2])), int(row[0])))
+    row = read_golden("chain16_dense_central_levels.txt")[0]
+    cases.append((W.chain(16), max(-float(row[0]), float(row[1])), 0))
+    for m, radius, r in cases:
+        psi = W.start_vectors(m["N"], 1, seed=0, r=r)[:, 0]
+        diag = Hm.diagonal(m)
+        tight = P.emax_bound(m, psi, diag=diag, rule="ritz")
+        loose = P.emax_bound(m, psi, diag=diag)
+        assert radius <= tight <= 1.25 * radius < loose, (m["N"], r, radius, tight, loose)
