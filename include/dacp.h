@@ -313,7 +313,10 @@ dacp_status dacp_get_launch_count(dacp_handle hd, int64_t* count);
  * Layers: affine + ReLU for the hidden layers, affine output; loss
  * sum (y - t)^2 / (2B) on standardised inputs and targets; Adam.
  * Weights are one flat float32 vector: for each layer W (out x in, row-major)
- * then b. */
+ * then b. Host arrays passed in are copied; the caller keeps ownership. Every
+ * call returns a status (DACP_ERR_ARG for NULL or mis-sized arguments,
+ * DACP_ERR_NOMEM, DACP_ERR_CUDA), and a failed call leaves its message in
+ * dacp_mlp_last_error. */
 typedef struct dacp_mlp_ctx* dacp_mlp;
 
 /* dacp_mlp_create -- layers n_in -> hidden_layers x n_hidden -> n_out.
@@ -330,8 +333,11 @@ dacp_status dacp_mlp_set_output_range(dacp_mlp m, const float* lo, const float* 
  * z = (x - in_mean) / in_std into the network, y = z_out * out_std + out_mean. */
 dacp_status dacp_mlp_set_normalization(dacp_mlp m, const float* in_mean, const float* in_std,
                                        const float* out_mean, const float* out_std);
-/* dacp_mlp_get_weights / dacp_mlp_set_weights -- the flat float32 weights
- * (set also resets the Adam state). *count receives the number of weights. */
+/* dacp_mlp_get_weights / dacp_mlp_set_weights -- copy the flat float32
+ * weights to / from caller-owned host memory (set also resets the Adam state).
+ * get writes *count (the number of weights, when count is not NULL) and
+ * returns DACP_ERR_ARG if cap is smaller. set returns DACP_ERR_ARG unless
+ * count equals that number. */
 dacp_status dacp_mlp_get_weights(dacp_mlp m, float* w, int64_t cap, int64_t* count);
 dacp_status dacp_mlp_set_weights(dacp_mlp m, const float* w, int64_t count);
 /* dacp_mlp_forward -- y[batch][n_out] (denormalised) from host x[batch][n_in]. */
@@ -345,8 +351,16 @@ dacp_status dacp_mlp_gradients(dacp_mlp m, const float* x, const float* t, int b
  * copied to the device once. *final_loss = loss of the last minibatch. */
 dacp_status dacp_mlp_train(dacp_mlp m, const float* x, const float* t, int n_samples, int batch,
                            int epochs, float lr, uint64_t seed, double* final_loss);
+/* dacp_mlp_get_launch_count -- kernels this network has launched since
+ * dacp_mlp_create (forward, backward, loss and Adam kernels). DACP_ERR_ARG for
+ * a NULL handle or count. */
 dacp_status dacp_mlp_get_launch_count(dacp_mlp m, int64_t* count);
+/* dacp_mlp_last_error -- message of the last failed call on m. The string is
+ * owned by m and valid until m's next call or its destruction. Returns
+ * "NULL handle" for NULL. */
 const char* dacp_mlp_last_error(dacp_mlp m);
+/* dacp_mlp_destroy -- waits for m's stream, then frees its device buffers and,
+ * if m created it, its stream. NULL is ignored. */
 void dacp_mlp_destroy(dacp_mlp m);
 
 /*
