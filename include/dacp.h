@@ -8,6 +8,8 @@
  * on 2^N-dimensional real state vectors, matrix-free (Sec. II intro; the
  * paper's sigma^x sigma^x + sigma^z models of Sec. III are this form after a
  * global Hadamard rotation). Z_i acts on bit i of the basis-state index.
+ * dacp_set_pair_couplings adds sum_{i<j} (Jxx_ij X_i X_j + Jyy_ij Y_i Y_j)
+ * (XXZ and Heisenberg chains; the vectors stay real).
  *
  * Conventions for every entry point
  *   - Return a dacp_status; nothing throws across the ABI. On failure the
