@@ -29,3 +29,24 @@ def test_reference_arm_prints_one_contract_line():
     assert out["cpu_baseline"]["value"] == out["value"]
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in out["config"]
+
+
+def test_roofline_arithmetic():
+    """The roofline entry of the benchmark line: algorithmic work over the
+    evolution time against the stated peak, per vector precision."""
+    sys.path.insert(0, ROOT)
+    import bench as B
+    import workloads as W
+    models = [W.spin_glass_shard(14, seed=s) for s in range(2)]
+    phase = [0.0, 1000.0, 0.0]                          # T_E = 1 s
+    clk = {"sm_mhz": 2000.0}
+    states = 1e9
+    wl = dict(B.WORKLOADS["c3"])
+    r = B.roofline(wl, models, phase, 3e12, states, clk)
+    # double-float: (N b + 2 b + b (b + 1)) multiply-adds x 12 instructions per state
+    fma = 14 * 4 + 2 * 4 + 4 * 5
+    assert r["bound"] == "alu" and abs(r["achieved"] - states * fma * B.DF_FMA_INSTR / 1e12) < 1e-9
+    assert abs(r["peak"] - 152 * 128 * 2000e6 / 1e12) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    wl["prec"] = "fp32"
+    r = B.roofline(wl, models, phase, 3e12, states, clk)
+    assert r["bound"] == "hbm" and abs(r["achieved"] - 3000.0) < 1e-9 and r["unit"] == "GB/s"
