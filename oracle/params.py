@@ -57,6 +57,35 @@ def lanczos_tridiagonal(model, v0, steps: int = 20, diag=None):
     return np.array(alphas), np.array(betas)
 
 
+def ritz_last_components(alpha, beta) -> np.ndarray:
+    """|e_k^T z_i| for every eigenvector z_i of the k x k tridiagonal T (diagonal
+    alpha, off-diagonal beta[:k-1]) without forming the vectors:
+    z_{k,i}^2 = prod_j (theta_i - mu_j) / prod_{j != i} (theta_i - theta_j), with
+    theta the eigenvalues of T and mu those of its leading (k-1) x (k-1) block
+    (the characteristic-polynomial identity p_{k-1}(theta_i) / p_k'(theta_i)).
+    Cauchy interlacing (theta_1 < mu_1 < theta_2 < ...) pairs every factor into
+    a ratio of magnitude at most one, which keeps the products stable. This is
+    the form a per-realization GPU thread can evaluate from Sturm-bisection
+    eigenvalues."""
+    al = np.asarray(alpha, dtype=np.float64)
+    k = len(al)
+    if k == 1:
+        return np.ones(1)
+    b = np.asarray(beta, dtype=np.float64)[:k - 1]
+    T = np.diag(al) + np.diag(b, 1) + np.diag(b, -1)
+    th = np.linalg.eigvalsh(T)
+    mu = np.linalg.eigvalsh(T[:k - 1, :k - 1])
+    out = np.empty(k)
+    for i in range(k):
+        v = 1.0
+        for j in range(i):                 # theta_j < mu_j < theta_{j+1} <= theta_i
+            v *= (th[i] - mu[j]) / (th[i] - th[j])
+        for j in range(i + 1, k):          # theta_i <= mu_{j-1} < theta_j
+            v *= (th[i] - mu[j - 1]) / (th[i] - th[j])
+        out[i] = np.sqrt(max(v, 0.0))
+    return out
+
+
 def emax_bound(model, v0, steps: int = 20, safety: float = 1e-3, diag=None, rule: str = "residual") -> float:
     """Upper bound on max |E| from k Lanczos steps (the estimator Sec. III cites).
 

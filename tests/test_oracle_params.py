@@ -138,3 +138,20 @@ def test_ritz_rule_is_tighter_and_still_above_the_radius():
         tight = P.emax_bound(m, psi, diag=diag, rule="ritz")
         loose = P.emax_bound(m, psi, diag=diag)
         assert radius <= tight <= 1.25 * radius < loose, (m["N"], r, radius, tight, loose)
+
+
+def test_ritz_last_components_from_the_interlacing_identity():
+    """The eigenvector-free last components equal those of eigh's eigenvectors
+    on random tridiagonals and on a Lanczos tridiagonal of a shard."""
+    rng = np.random.default_rng(7)
+    cases = [(rng.standard_normal(k), np.abs(rng.standard_normal(k)) + 0.1) for k in (1, 2, 5, 20)]
+    m = W.spin_glass_shard(10, seed=3)
+    cases.append(P.lanczos_tridiagonal(m, W.start_vectors(10, 1, seed=1)[:, 0], 20)[:2])
+    for al, be in cases:
+        k = len(al)
+        T = np.diag(al) + np.diag(be[:k - 1], 1) + np.diag(be[:k - 1], -1)
+        _, Z = np.linalg.eigh(T)
+        got, ref = P.ritz_last_components(al, be), np.abs(Z[-1, :])
+        # components far below one (nearly converged Ritz pairs) are where both forms lose digits
+        assert np.abs(got - ref).max() < 1e-7
+        assert abs(got.max() - ref.max()) < 1e-10          # the one the Ritz-residual rule uses
