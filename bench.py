@@ -261,25 +261,44 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 
-def oracle_sample(wl, budget_s=15.0):
-    """Time the float64 oracle on one realization of the workload in a child
-    process pinned to one thread (the paper's sequential mode) and extrapolate
-    to the whole batch. Returns (eigs/s, description, cores)."""
+def oracle_sample(wl, budget_s=15.0, procs=None):
+    """Time the float64 oracle on the host cores: `procs` single-threaded child
+    processes at once (default: one per core, at most one per realization), each
+    on its own realization of the workload. Their per-realization times are
+    extrapolated to the whole batch spread over those cores. Returns (eigs/s,
+    description, cores)."""
+    procs = max(1, min(procs or os.cpu_count() or 1, wl["R"]))
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
     name = [k for k, v in WORKLOADS.items() if v is wl][0]
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", name,
-                        "--budget", str(budget_s), "--realizations", str(wl["R"]), "--n-eigs", str(wl["n_eigs"]),
-                        "--precision", wl["prec"]], env=env, capture_output=True, text=True, check=True)
-    res = json.loads(r.stdout.strip().splitlines()[-1])
-    return res["rate"], res["desc"], 1
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", name,
+           "--budget", str(budget_s), "--realizations", str(wl["R"]), "--n-eigs", str(wl["n_eigs"]),
+           "--precision", wl["prec"]]
+    ps = [subprocess.Popen(cmd + ["--oracle-rank", str(r)], env=env, stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE, text=True) for r in range(procs)]
+    res = []
+    for p in ps:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(f"oracle sample failed: {err[-2000:]}")
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    t_real = float(np.mean([x["t_real"] for x in res]))
+    t_batch = math.ceil(wl["R"] / procs) * t_real
+    rate = wl["R"] * wl["n_eigs"] / t_batch
+    x = res[0]
+    desc = (f"float64 oracle, {procs} single-threaded process(es) at once, one realization each "
+            f"(r = 0..{procs - 1}); realization 0: parameters {x['t_params']:.2f}s, {x['n_hv']} H.v timed "
+            f"({x['t_hv'] * 1e3:.2f} ms each), one {x['M']}x{x['M']} generalized eigensolve {x['t_gep']:.2f}s; "
+            f"mean {t_real:.0f}s per realization extrapolated from {x['hv_total']} H.v; "
+            f"{wl['R']} realizations over {procs} core(s) = {t_batch:.0f}s per batch")
+    return rate, desc, procs
 
 
-def _oracle_sample_child(wl, budget_s):
+def _oracle_sample_child(wl, budget_s, r=0):
     from oracle import dacp as DA
     from oracle import hamiltonian as Hm
     from oracle import params as OP
-    models, psis = make_inputs(dict(wl, R=1))
-    m, psi = models[0], psis[0]
+    models, psis = make_inputs(dict(wl, R=r + 1))
+    m, psi = models[r], psis[r]
     N = wl["N"]
     D = 1 << N
     t0 = time.perf_counter()
@@ -313,12 +332,8 @@ def _oracle_sample_child(wl, budget_s):
     t_gep = time.perf_counter() - t2
     hv_total = 2 * K + 2 * kn + 1               # filter (2 per order) + direct moments to 2 k_n
     t_real = t_params + hv_total * t_hv + t_gep
-    t_batch = wl["R"] * t_real
-    rate = wl["R"] * wl["n_eigs"] / t_batch
-    desc = (f"float64 oracle, 1 thread, 1 realization: parameters {t_params:.2f}s, {n_hv} H.v timed "
-            f"({t_hv * 1e3:.2f} ms each), one {M}x{M} generalized eigensolve {t_gep:.2f}s; extrapolated to "
-            f"{hv_total} H.v per realization x {wl['R']} realizations = {t_batch:.0f}s per batch")
-    print(json.dumps({"rate": rate, "desc": desc}))
+    print(json.dumps({"t_real": t_real, "t_params": t_params, "n_hv": n_hv, "t_hv": t_hv, "M": M,
+                      "t_gep": t_gep, "hv_total": hv_total}))
 
 
 # ---------------------------------------------------------------------------
@@ -529,6 +544,7 @@ def main():
     ap.add_argument("--n-eigs", type=int, default=None, help="override the central eigenvalues per realization")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-rank", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.precision or args.realizations or args.n_eigs:
@@ -542,7 +558,7 @@ def main():
         wl["desc"] += f" [variant: R={wl['R']}, n_eigs={wl['n_eigs']}, {wl['prec']}]"
         WORKLOADS[args.workload] = wl
     if args.oracle_sample:
-        _oracle_sample_child(wl, args.budget)
+        _oracle_sample_child(wl, args.budget, args.oracle_rank)
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
