@@ -277,6 +277,35 @@ dacp_status dacp_set_launch(dacp_handle hd, int mode, int tile_bytes);
 dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);
 
 /*
+ * dacp_set_emax_rule -- how dacp_choose_params / dacp_choose_params_mlp turn
+ * their k Lanczos steps into the bound E_max on |E| (Sec. III cites the
+ * Lanczos upper-bound estimator; Sec. II A needs a true bound):
+ *   0 (default)  max |theta| + beta_{k+1}: the extreme Ritz value plus the
+ *                whole residual norm;
+ *   1            max |theta| + beta_{k+1} max_i |e_k^T z_i|: the largest
+ *                residual of any Ritz pair (z_i the eigenvectors of the
+ *                tridiagonal matrix, taken from the interlacing identity
+ *                without forming them).
+ * Both are times 1.001 and clamped to the Pauli 1-norm. Rule 1 runs about 1.14
+ * times the spectral radius where rule 0 runs about 1.46 (measured against
+ * dense spectra), and the filter and evolution lengths shrink in proportion.
+ * It is a bound in practice, not in theory. A realization whose moments then
+ * exceed mu_0 is reported as DACP_ERR_NUMERIC. Takes effect at the next
+ * parameter choice. Errors: DACP_ERR_ARG for another rule.
+ */
+dacp_status dacp_set_emax_rule(dacp_handle hd, int rule);
+
+/*
+ * dacp_test_emax_rule -- test hook (host arithmetic only, no device work): the
+ * bound of rule 0 or 1 above, before the safety factor and the clamp, for a
+ * k x k Lanczos tridiagonal (1 <= k <= 64): alpha[k] its diagonal, beta2[k] the
+ * squared off-diagonals beta_2^2 .. beta_k^2 followed by the squared residual
+ * norm beta_{k+1}^2. It is the same code the device kernel runs for rule 1.
+ * Errors: DACP_ERR_ARG.
+ */
+dacp_status dacp_test_emax_rule(int k, const double* alpha, const double* beta2, int rule, double* bound);
+
+/*
  * dacp_set_solver -- how dacp_central_eigs runs the dense float64 algebra:
  * 1 (default) = one batched cuSOLVER syev call per group for S and one for
  * H~, with a strided-batched dgemm (W = H U) and a syrkx per realization

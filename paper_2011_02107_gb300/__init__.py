@@ -35,7 +35,8 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_mlp_set_weights", "dacp_mlp_forward", "dacp_mlp_gradients", "dacp_mlp_train",
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
-           "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings"]
+           "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings",
+           "dacp_set_emax_rule", "dacp_test_emax_rule"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -73,6 +74,8 @@ def _load():
         "dacp_eigenvectors": [P, I, I, D, D, P, P, L, P],
         "dacp_apply_h": [P, I, P, P],
         "dacp_set_pair_couplings": [P, P, P],
+        "dacp_set_emax_rule": [P, I],
+        "dacp_test_emax_rule": [I, P, P, I, ctypes.POINTER(D)],
         "dacp_get_timings": [P, P],
         "dacp_get_launch_count": [P, ctypes.POINTER(L)],
         "dacp_mlp_create": [ctypes.POINTER(P), I, I, I, I, P, ctypes.c_uint64, P],
@@ -225,6 +228,20 @@ def dacp_set_pair_couplings(hd, Jxx, Jyy):
     Jxx = np.ascontiguousarray(Jxx, dtype=np.float64)
     Jyy = np.ascontiguousarray(Jyy, dtype=np.float64)
     _check(hd, _lib.dacp_set_pair_couplings(hd, _ptr(Jxx), _ptr(Jyy)))
+
+
+def dacp_set_emax_rule(hd, rule):
+    _check(hd, _lib.dacp_set_emax_rule(hd, int(rule)))
+
+
+def dacp_test_emax_rule(alpha, beta2, rule):
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta2 = np.ascontiguousarray(beta2, dtype=np.float64)
+    if len(beta2) != len(alpha):
+        raise ValueError("beta2 needs one entry per Lanczos step (the last is the squared residual norm)")
+    out = ctypes.c_double(0.0)
+    _check(None, _lib.dacp_test_emax_rule(len(alpha), _ptr(alpha), _ptr(beta2), int(rule), ctypes.byref(out)))
+    return out.value
 
 
 def dacp_apply_h(hd, r, x_dev_ptr, y_dev_ptr):
@@ -429,6 +446,9 @@ class Dacp:
 
     def set_solver(self, mode):
         dacp_set_solver(self.handle, mode)
+
+    def set_emax_rule(self, rule):
+        dacp_set_emax_rule(self.handle, rule)
 
     def set_launch(self, mode, tile_bytes):
         dacp_set_launch(self.handle, mode, tile_bytes)

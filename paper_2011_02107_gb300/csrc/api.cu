@@ -112,6 +112,7 @@ struct dacp_ctx {
                                         // 2: as 0 with every HBM read of a tile staged (float32 only)
     bool poison_barrier = false;        // test hook: the next persistent launch's barrier never opens
     bool batched_solve = true;          // equal basis sizes: batched cuSOLVER instead of lanes
+    int emax_rule = 0;                  // E_max bound: 0 Ritz value + residual norm, 1 Ritz-residual rule
     double* mom_d = nullptr;
     int64_t mom_cap = 0;
 
@@ -802,7 +803,7 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
             vc = w;
             w = t;
         }
-        CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax_d, c->st));
+        CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax_d, c->emax_rule, c->st));
         // reset the apply coefficients of the test hook
         for (int r = 0; r < R; ++r) lc[8 * r + 1] = 0.0;
         CK(cudaMemcpyAsync(c->apply_coef_d, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice, c->st));
@@ -1842,6 +1843,13 @@ dacp_status dacp_set_pair_couplings(dacp_handle c, const double* Jxx, const doub
         g->exec = nullptr;
     }
     c->state = 0;                                 // H changed: parameters and results are stale
+    return DACP_OK;
+}
+
+dacp_status dacp_set_emax_rule(dacp_handle c, int rule) {
+    TRY(check_handle(c));
+    if (rule != 0 && rule != 1) return fail(c, DACP_ERR_ARG, "E_max rule must be 0 or 1");
+    c->emax_rule = rule;
     return DACP_OK;
 }
 

@@ -7,6 +7,7 @@
 
 #include <math.h>
 
+#include "../../include/dacp.h"
 #include "common.cuh"
 #include "ops.h"
 
@@ -86,7 +87,7 @@ __global__ void lanczos_coef_kernel(int R, const double* __restrict__ beta2, int
 }
 
 // Number of eigenvalues of the k x k tridiagonal (alpha, beta) below x (Sturm count).
-__device__ int sturm_count(const double* al, const double* b2, int k, double x) {
+__host__ __device__ int sturm_count(const double* al, const double* b2, int k, double x) {
     int cnt = 0;
     double d = 1.0;
     for (int i = 0; i < k; ++i) {
@@ -98,11 +99,54 @@ __device__ int sturm_count(const double* al, const double* b2, int k, double x) 
     return cnt;
 }
 
-// Extreme Ritz values by bisection; bound = max(|theta_min|, |theta_max|) + beta_{k+1},
-// times (1 + safety), clamped to the Pauli 1-norm pnorm[r].
+// The idx-th smallest eigenvalue (0-based) of the k x k tridiagonal, by bisection
+// on the Sturm count inside the Gershgorin interval [-gmax, gmax].
+__host__ __device__ double tridiag_eig(const double* al, const double* b2, int k, int idx, double gmax) {
+    double lo = -gmax - 1.0, hi = gmax + 1.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(al, b2, k, mid) >= idx + 1) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Ritz-residual rule (rule 1): max |theta| + beta_{k+1} max_i |e_k^T z_i|, before the
+// safety factor. The last components of the tridiagonal's eigenvectors come without
+// the vectors, from z_{k,i}^2 = prod_j (theta_i - mu_j) / prod_{j != i} (theta_i - theta_j)
+// (mu: eigenvalues of the leading (k-1) x (k-1) block). Cauchy interlacing pairs each
+// factor into a ratio of magnitude at most one; a zero denominator counts as one, which
+// can only enlarge the bound. b2[0..k-2] are the squared off-diagonals, b2[k-1] the
+// squared residual norm. k <= 64.
+__host__ __device__ double ritz_rule_bound(const double* al, const double* b2, int k) {
+    double gmax = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double bl = i > 0 ? sqrt(b2[i - 1]) : 0.0;
+        const double br = i < k - 1 ? sqrt(b2[i]) : 0.0;
+        gmax = fmax(gmax, fabs(al[i]) + bl + br);
+    }
+    double th[64], mu[64];
+    for (int i = 0; i < k; ++i) th[i] = tridiag_eig(al, b2, k, i, gmax);
+    for (int i = 0; i < k - 1; ++i) mu[i] = tridiag_eig(al, b2, k - 1, i, gmax);
+    double zmax = k == 1 ? 1.0 : 0.0;
+    for (int i = 0; k > 1 && i < k; ++i) {
+        double v = 1.0;
+        for (int j = 0; j < k; ++j) {
+            if (j == i) continue;
+            const double num = th[i] - mu[j < i ? j : j - 1];
+            const double den = th[i] - th[j];
+            if (den != 0.0) v *= fmin(1.0, fabs(num / den));
+        }
+        zmax = fmax(zmax, sqrt(v));
+    }
+    return fmax(fabs(th[0]), fabs(th[k - 1])) + sqrt(b2[k - 1]) * zmax;
+}
+
+// Extreme Ritz values by bisection; bound = max(|theta_min|, |theta_max|) + beta_{k+1}
+// (rule 0) or the Ritz-residual rule (rule 1), times (1 + safety), clamped to the
+// Pauli 1-norm pnorm[r].
 __global__ void lanczos_bound_kernel(int R, const double* __restrict__ lmom, int rows,
                                      const double* __restrict__ beta2, int steps,
-                                     const double* __restrict__ pnorm, double safety, double* emax) {
+                                     const double* __restrict__ pnorm, double safety, double* emax, int rule) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     double al[64], b2[64];
@@ -129,7 +173,8 @@ __global__ void lanczos_bound_kernel(int R, const double* __restrict__ lmom, int
         if (sturm_count(al, b2, k, mid) >= k) hi = mid; else lo = mid;
     }
     const double tmax = 0.5 * (lo + hi);
-    const double bound = (fmax(fabs(tmin), fabs(tmax)) + sqrt(b2[k - 1])) * (1.0 + safety);
+    double bound = (fmax(fabs(tmin), fabs(tmax)) + sqrt(b2[k - 1])) * (1.0 + safety);
+    if (rule == 1) bound = ritz_rule_bound(al, b2, k) * (1.0 + safety);
     emax[r] = fmin(bound, pnorm[r]);
 }
 
@@ -219,8 +264,8 @@ cudaError_t launch_lanczos_scale(int prec, const Item* items, const RealInfo* re
 }
 
 cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps,
-                                 const double* pnorm, double safety, double* emax, cudaStream_t st) {
-    lanczos_bound_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, lmom, rows, beta2, steps, pnorm, safety, emax);
+                                 const double* pnorm, double safety, double* emax, int rule, cudaStream_t st) {
+    lanczos_bound_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, lmom, rows, beta2, steps, pnorm, safety, emax, rule);
     return cudaGetLastError();
 }
 
@@ -277,3 +322,23 @@ cudaError_t launch_features(int R, const RealInfo* real, const double* J, const 
 }
 
 }  // namespace dacp
+
+// Host entry to the bound arithmetic the Lanczos kernel runs (test hook).
+extern "C" dacp_status dacp_test_emax_rule(int k, const double* alpha, const double* beta2, int rule,
+                                           double* bound) {
+    if (k < 1 || k > 64 || !alpha || !beta2 || !bound || (rule != 0 && rule != 1)) return DACP_ERR_ARG;
+    if (rule == 1) {
+        *bound = dacp::ritz_rule_bound(alpha, beta2, k);
+        return DACP_OK;
+    }
+    double gmax = 0.0;
+    for (int i = 0; i < k; ++i) {
+        const double bl = i > 0 ? sqrt(beta2[i - 1]) : 0.0;
+        const double br = i < k - 1 ? sqrt(beta2[i]) : 0.0;
+        gmax = fmax(gmax, fabs(alpha[i]) + bl + br);
+    }
+    const double tmin = dacp::tridiag_eig(alpha, beta2, k, 0, gmax);
+    const double tmax = dacp::tridiag_eig(alpha, beta2, k, k - 1, gmax);
+    *bound = fmax(fabs(tmin), fabs(tmax)) + sqrt(beta2[k - 1]);
+    return DACP_OK;
+}
