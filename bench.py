@@ -372,6 +372,8 @@ def run_gpu(args, wl, rank, world):
 
     # ---- value: inputs resident on the device, K whole-path steps
     d = P.Dacp(models, psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
+    if args.emax_rule:
+        d.set_emax_rule(args.emax_rule)
     d.choose_params(n_eigs)
     tile_bytes = d.autotune(64)            # cached per (sizes, b, precision) for this process
     launch_mode = d.launch()[0]            # 0 graph replay, 1 persistent, 2 staged tiles (float32)
@@ -502,7 +504,7 @@ def run_gpu(args, wl, rank, world):
                    "parallelism": f"independent realizations, {world} GPU(s)",
                    "emax_mean": float(np.mean(params["emax"])), "a_mean": float(np.mean(params["a"])),
                    "K_max": int(params["K"].max()), "kn_max": int(params["kn"].max()),
-                   "n": int(params["n"].max())},
+                   "n": int(params["n"].max()), "emax_rule": args.emax_rule},
         "eigenvalues_found_per_step": found_all / args.steps,
         "phase_ms_per_step": {"T_F": phase[0] / args.steps, "T_E": phase[1] / args.steps,
                               "T_D": phase[2] / args.steps,
@@ -542,6 +544,9 @@ def main():
                     help="override the workload's precision (df32: double-float vectors on the float32 pipes)")
     ap.add_argument("--realizations", type=int, default=None, help="override the number of realizations per GPU")
     ap.add_argument("--n-eigs", type=int, default=None, help="override the central eigenvalues per realization")
+    ap.add_argument("--emax-rule", type=int, default=0, choices=[0, 1],
+                    help="E_max bound of the parameter choice: 0 Ritz value + residual norm (default), "
+                         "1 Ritz-residual rule (tighter, a bound in practice)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-rank", type=int, default=0, help=argparse.SUPPRESS)
