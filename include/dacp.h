@@ -290,7 +290,9 @@ dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);
  * times the spectral radius where rule 0 runs about 1.46 (measured against
  * dense spectra), and the filter and evolution lengths shrink in proportion.
  * It is a bound in practice, not in theory. A realization whose moments then
- * exceed mu_0 is reported as DACP_ERR_NUMERIC. Takes effect at the next
+ * exceed mu_0 is reported as DACP_ERR_NUMERIC. The parameter network's
+ * moment features are taken in units of E_max, so a network trained under
+ * one rule sees shifted features under the other. Takes effect at the next
  * parameter choice. Errors: DACP_ERR_ARG for another rule.
  */
 dacp_status dacp_set_emax_rule(dacp_handle hd, int rule);
