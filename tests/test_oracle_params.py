@@ -117,13 +117,13 @@ def test_emax_bound_holds_against_exact_extremes_at_benchmark_sizes():
 
 
 def test_ritz_rule_is_tighter_and_still_above_the_radius():
-    """The Ritz-residual rule against exact spectral radii: 40 N = 10 shards
+    """The Ritz-residual rule against exact spectral radii: 16 N = 10 shards
     (dense eigh) and the five benchmark-size cases (tests/golden). It stays
     above the radius on every one and below 1.25 times it, where the residual
     rule sits near 1.46."""
     from tests.conftest import read_golden
     cases = []
-    for seed in range(40):
+    for seed in range(16):
         m = W.spin_glass_shard(10, seed=500 + seed)
         E = np.linalg.eigvalsh(Hm.dense_h(m))
         cases.append((m, max(-E[0], E[-1]), seed))
