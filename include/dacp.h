@@ -415,10 +415,11 @@ dacp_status dacp_get_features(dacp_handle hd, float* feats, int64_t cap);
 /*
  * dacp_moments_noalloc -- Chebyshev moments of one realization without any
  * device allocation. The paper has no counterpart: this entry point exists for
- * callers that cannot call cudaMalloc -- code running while its stream is
- * being captured into a CUDA graph (allocation is illegal there), engines
- * whose device memory all comes from their own pool or arena, and loops that
- * must not enter an allocator.
+ * callers that cannot call cudaMalloc -- engines whose device memory all comes
+ * from their own pool or arena (a cudaMalloc behind their back would break
+ * their accounting or fail under their memory cap), and loops that must not
+ * enter an allocator (an allocation can synchronize the device and stall
+ * them).
  *
  *   n_spins      N, 1 <= N <= 16; larger N returns DACP_ERR_ARG (the scratch
  *                array below holds 3 x 2^16 float64 states).
@@ -431,15 +432,18 @@ dacp_status dacp_get_features(dacp_handle hd, float* feats, int64_t cap);
  *   mu_dev       device pointer, 2 * n_orders float64: on return
  *                mu_j = <psi| T_j(G) |psi>, j = 0 .. 2 n_orders - 1, from the
  *                same fused stencil kernel as dacp_basis_moments.
- *   stream       cudaStream_t or NULL; the call returns when the work is done.
+ *   stream       cudaStream_t or NULL. The call copies J, h, gamma and its
+ *                run lengths from host memory into the scratch array on this
+ *                stream, and waits for the stream before it returns.
  *
  * Scratch: one file-scope device array of about 1.6 MB (vectors, diagonal,
  * couplings, partial sums, counters), held by every GPU that loads the
- * library until the process exits. The first call on a device looks up the
- * array's address and sets the kernel's shared-memory limit; make that first
- * call before any stream capture. Every call overwrites the array, and two
- * calls that overlap on the GPU (different streams or threads) race on it and
- * corrupt each other's results: serialise them.
+ * library until the process exits. The first call on a device does the
+ * set-up: it looks up the array's address (cudaGetSymbolAddress) and raises
+ * the stencil kernel's shared-memory limit; make that first call before any
+ * stream capture. Every call overwrites the array and clears its counters,
+ * and two calls that overlap on the GPU (different streams or threads) race
+ * on it and corrupt each other's results: serialise them.
  * Returns DACP_OK, DACP_ERR_ARG, DACP_ERR_CUDA or DACP_ERR_TIMEOUT.
  */
 dacp_status dacp_moments_noalloc(int n_spins, const double* J, const double* h, const double* gamma,

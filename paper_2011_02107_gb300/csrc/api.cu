@@ -550,6 +550,20 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
     if (precision != DACP_FP64 && precision != DACP_FP32 && precision != DACP_DF32) return DACP_ERR_ARG;
     for (int r = 0; r < n_real; ++r)
         if (n_spins[r] < 1 || n_spins[r] > kMaxSpins) return DACP_ERR_ARG;
+    // every coupling and field finite, checked before any device use
+    {
+        int64_t jo = 0, ho = 0;
+        for (int r = 0; r < n_real; ++r) {
+            const int Nr = n_spins[r];
+            for (int i = 0; i < Nr; ++i) {
+                if (!isfinite(h[ho + i]) || !isfinite(gamma[ho + i])) return DACP_ERR_ARG;
+                for (int j = i + 1; j < Nr; ++j)
+                    if (!isfinite(J[jo + static_cast<int64_t>(i) * Nr + j])) return DACP_ERR_ARG;
+            }
+            jo += static_cast<int64_t>(Nr) * Nr;
+            ho += Nr;
+        }
+    }
 
     dacp_ctx* c = new dacp_ctx();
     auto bail = [&](dacp_status s) {

@@ -1,14 +1,14 @@
 // Allocation-free Chebyshev moments: dacp_moments_noalloc.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (allocation calls are illegal there), engines
-// whose device memory all belongs to their own pool or arena, and latency-
-// critical loops that forbid allocator calls. For them this entry point runs
-// the float64 evolution stencil (H.v fused with the Chebyshev recurrence and
-// the moment sums) for one realization without allocating anything: its
-// working vectors, diagonal, couplings, partial sums and counters live in one
-// file-scope device array, and the caller passes only the input vector and
-// the output moments.
+// Some callers cannot call cudaMalloc: engines whose device memory all
+// belongs to their own pool or arena, and latency-critical loops that forbid
+// allocator calls. For them this entry point runs the float64 evolution
+// stencil (H.v fused with the Chebyshev recurrence and the moment sums) for
+// one realization without allocating anything: its working vectors,
+// diagonal, couplings, partial sums and counters live in one file-scope
+// device array, and the caller passes only the input vector and the output
+// moments. The call copies its small host inputs into the array on the
+// caller's stream and waits for that stream before it returns.
 //
 // The array holds at most kMaxSpins states' worth of scratch, so N <= 16. It
 // is loaded with the library and every GPU that loads it keeps it until the

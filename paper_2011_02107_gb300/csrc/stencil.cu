@@ -26,7 +26,10 @@
 
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "common.cuh"
 #include "ops.h"
@@ -1075,27 +1078,53 @@ static cudaError_t launch_one(const StepArgs& a, int item_base, int n_items, int
     return cudaGetLastError();
 }
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize is process-wide per kernel and
+// device, while handles with different tile sizes share the kernels: a later
+// handle with a smaller tile must not lower the limit an earlier handle (or
+// an already instantiated graph) launches with. So the attribute only grows:
+// the largest value set so far is kept per (kernel, device) under a mutex,
+// and the runtime is called only when a launch needs more.
+static std::mutex g_smem_mu;
+static std::map<std::pair<const void*, int>, int> g_smem_max;
+
+static cudaError_t grow_smem_attr(const void* func, int smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    int& have = g_smem_max[std::make_pair(func, dev)];
+    if (smem <= have) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) have = smem;
+    return e;
+}
+
+template <typename K>
+static cudaError_t grow_smem(K* kernel, int smem) {
+    return grow_smem_attr(reinterpret_cast<const void*>(kernel), smem);
+}
+
 template <int MODE>
 static cudaError_t prepare_df4tb(int smem) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(step_kernel_df4tb<MODE, 10>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(step_kernel_df4tb<MODE, 11>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_kernel_df4tb<MODE, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if ((e = grow_smem(step_kernel_df4tb<MODE, 10>, smem)) != cudaSuccess) return e;
+    if ((e = grow_smem(step_kernel_df4tb<MODE, 11>, smem)) != cudaSuccess) return e;
+    return grow_smem(step_kernel_df4tb<MODE, 12>, smem);
 }
 
 template <typename T, int B>
 static cudaError_t prepare_tb(int smem) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(step_kernel<T, B, kApply>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(step_kernel<T, B, kFilter1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(step_kernel<T, B, kFilter2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = grow_smem(step_kernel<T, B, kApply>, smem)) != cudaSuccess) return e;
+    if ((e = grow_smem(step_kernel<T, B, kFilter1>, smem)) != cudaSuccess) return e;
+    if ((e = grow_smem(step_kernel<T, B, kFilter2>, smem)) != cudaSuccess) return e;
     if constexpr (std::is_same<T, df32>::value && B == 4) {
         if ((e = prepare_df4tb<kApply>(smem)) != cudaSuccess) return e;
         if ((e = prepare_df4tb<kFilter1>(smem)) != cudaSuccess) return e;
         if ((e = prepare_df4tb<kFilter2>(smem)) != cudaSuccess) return e;
         if ((e = prepare_df4tb<kEvolve>(smem)) != cudaSuccess) return e;
     }
-    return cudaFuncSetAttribute(step_kernel<T, B, kEvolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return grow_smem(step_kernel<T, B, kEvolve>, smem);
 }
 
 // Allow the dynamic shared-memory tile for every mode of (precision, b);
@@ -1167,12 +1196,11 @@ bool staged_fits(int b, int tile_smem) {
 template <int B>
 static cudaError_t prepare_staged_b(int tile_smem) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(step_kernel_staged<B, kFilter1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  staged_smem_bytes(kFilter1, B, tile_smem))) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(step_kernel_staged<B, kFilter2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  staged_smem_bytes(kFilter2, B, tile_smem))) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_kernel_staged<B, kEvolve>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                staged_smem_bytes(kEvolve, B, tile_smem));
+    if ((e = grow_smem(step_kernel_staged<B, kFilter1>, staged_smem_bytes(kFilter1, B, tile_smem))) != cudaSuccess)
+        return e;
+    if ((e = grow_smem(step_kernel_staged<B, kFilter2>, staged_smem_bytes(kFilter2, B, tile_smem))) != cudaSuccess)
+        return e;
+    return grow_smem(step_kernel_staged<B, kEvolve>, staged_smem_bytes(kEvolve, B, tile_smem));
 }
 
 // Allow the staged kernels' dynamic shared memory (call staged_fits first);
@@ -1223,7 +1251,7 @@ template <typename T, int B, int SEQ>
 static cudaError_t launch_persistent_tb(const StepArgs& a, int n_items, int orders, int smem, cudaStream_t st,
                                        int* grid_out) {
     auto k = persistent_kernel<T, B, SEQ>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = grow_smem(k, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);

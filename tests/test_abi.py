@@ -69,3 +69,44 @@ def test_argument_errors_need_no_gpu(lib):
     with pytest.raises(P.DacpError) as e:
         P.dacp_create(np.array([3], dtype=np.int32), np.zeros(9), np.zeros(3), np.zeros(3), 1, 7, np.zeros(8))
     assert e.value.status == 1          # unknown precision
+
+
+@pytest.mark.parametrize("where", ["J", "h", "gamma"])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")])
+def test_non_finite_couplings_rejected_without_gpu(lib, where, bad):
+    """A NaN or infinite zz coupling, z-field or x-field is refused by dacp_create (DACP_ERR_ARG)
+    before any device use: H would not be a finite matrix, and E_max would be no bound."""
+    import numpy as np
+    import paper_2011_02107_gb300 as P
+    n = np.array([2, 3], dtype=np.int32)
+    J = np.zeros(4 + 9)
+    h = np.zeros(5)
+    g = np.ones(5)
+    if where == "J":
+        J[4 + 1 * 3 + 2] = bad             # realization 1, J_12 (i < j: read)
+    elif where == "h":
+        h[3] = bad
+    else:
+        g[4] = bad
+    with pytest.raises(P.DacpError) as e:
+        P.dacp_create(n, J, h, g, 1, 0, np.zeros(4 + 8))
+    assert e.value.status == 1
+
+
+def test_lower_triangle_of_j_is_not_read(lib):
+    """Only J_ij with i < j is read: a NaN below the diagonal passes validation (then the call needs
+    the device, so on a host without one it fails later, with DACP_ERR_CUDA, not DACP_ERR_ARG)."""
+    import numpy as np
+    import paper_2011_02107_gb300 as P
+    J = np.zeros(9)
+    J[1 * 3 + 0] = float("nan")            # J_10, below the diagonal
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if has_gpu:
+        pytest.skip("on a GPU host the call succeeds; covered by the GPU tests")
+    with pytest.raises(P.DacpError) as e:
+        P.dacp_create(np.array([3], dtype=np.int32), J, np.zeros(3), np.ones(3), 1, 0, np.zeros(8))
+    assert e.value.status != 1

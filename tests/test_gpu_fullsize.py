@@ -11,7 +11,11 @@ sampled outputs and properties that hold at any size:
   * |mu_j| <= mu_0 and the requested count, for sampled realizations;
   * sampled realizations' levels against float64 DACP with the paper's parameters, within 1e-2 of the
     local mean spacing. That float64 run is itself pinned to the oracle and to dense spectra by the other
-    parity tests.
+    parity tests;
+  * every one of the 500 levels of realizations 0, 64, 128 and 192 against their exact levels (dense
+    float64 eigh of the 16384 x 16384 matrices, tests/golden/shard14_dense_central_levels.txt, written
+    by an oracle-only script), within 1e-2 of the local mean spacing: the accuracy measure of Sec. III
+    (Fig. 2 judges DACP's levels against exact ones) at the batched target.
 """
 
 import os
@@ -21,6 +25,8 @@ import pytest
 
 import workloads as W
 from oracle import dacp as DA
+from oracle import metrics as MT
+from tests.conftest import read_golden
 
 pytestmark = pytest.mark.gpu
 P = pytest.importorskip("paper_2011_02107_gb300")
@@ -92,3 +98,22 @@ def test_fullsize_sampled_levels_vs_float64_dacp(batch):
         assert nf[j] == NE
         ok, err = TM.accurate(np.asarray(batch["eigs"][r])[:NE], np.asarray(ref[j])[:NE])
         assert ok, (r, err)
+
+
+def test_fullsize_levels_vs_exact_levels(batch):
+    """All 500 central levels of the four shards with a stored dense spectrum, level by level."""
+    exact = {}
+    for row in read_golden("shard14_dense_central_levels.txt"):
+        if len(row) == 2:
+            exact.setdefault(int(row[0]), []).append(float(row[1]))
+    assert sorted(exact) == [0, 64, 128, 192]
+    for r, lv in sorted(exact.items()):
+        lv = np.sort(np.asarray(lv))                         # the 640 levels nearest E = 0
+        ref = MT.central_exact(lv, NE)
+        got = np.sort(np.asarray(batch["eigs"][r]))
+        assert len(got) == NE, r
+        first = int(np.searchsorted(lv, ref[0]))            # ref is a contiguous run of lv
+        assert np.array_equal(lv[first:first + NE], ref)
+        spacing = np.array([MT.local_spacing(lv, first + i) for i in range(NE)])
+        err = np.abs(got - ref) / spacing
+        assert err.max() <= 1e-2, (r, float(err.max()), int(np.argmax(err)))
