@@ -236,8 +236,12 @@ dacp_status dacp_get_filtered(dacp_handle hd, int r, double* psi, int64_t cap);
 /*
  * dacp_apply_h -- one matrix-free H.v of realization r (Sec. II intro):
  * y = H x for the b columns of x. x_dev, y_dev: device pointers to 2^N_r * b
- * values of the handle's precision (float64 or float32), layout
- * [state][column], 16-byte aligned, not overlapping. Test hook.
+ * values of the handle's precision, layout [state][column], 16-byte aligned,
+ * not overlapping. Test hook. Values are float64 or float32 as they are; a
+ * double-float value is the pair (hi, lo) of float32 with value hi + lo, and
+ * with b = 4 each state's 32 bytes hold (hi_0, hi_1, lo_0, lo_1, hi_2, hi_3,
+ * lo_2, lo_3) (the paired-float32 layout of the stencil), with b = 1 or 2
+ * (hi, lo) per column.
  */
 dacp_status dacp_apply_h(dacp_handle hd, int r, const void* x_dev, void* y_dev);
 

@@ -1486,7 +1486,7 @@ dacp_status dacp_get_filtered(dacp_handle c, int r, double* psi, int64_t cap) {
     auto run = [&]() -> dacp_status {
         TRY(dalloc_t(c, &tmp, static_cast<size_t>(n)));
         const char* src = static_cast<const char*>(c->psiE_d) + static_cast<size_t>(c->info[r].off) * c->b * c->esz;
-        CK(launch_to_double(c->prec, src, tmp, n, c->st));
+        CK(launch_to_double(c->prec, src, tmp, n, c->b, c->st));
         c->launches += 1;
         CK(cudaMemcpyAsync(psi, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));

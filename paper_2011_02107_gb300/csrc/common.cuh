@@ -15,6 +15,38 @@ constexpr int kTileBytes = 65536;   // shared-memory tile of one stencil CTA
 constexpr int kFeatureMoments = 32; // Chebyshev moments fed to the parameter network
 constexpr int kFeatures = 8 + kFeatureMoments;
 
+// Element (s, p) of a [state][b] vector in precision T. Double-float vectors
+// with b = 4 keep each state's two column pairs as (hi_0, hi_1, lo_0, lo_1 |
+// hi_2, hi_3, lo_2, lo_3): one 16-byte load then gives the hi parts and the lo
+// parts of two columns in two 64-bit registers, the operands of the paired
+// float32 instructions of the stencil. Every other precision and block size
+// stores element (s, p) at s * b + p.
+template <typename T>
+struct VecAt {
+    __device__ static T get(const T* v, int64_t s, int p, int b) { return v[s * b + p]; }
+    __device__ static void set(T* v, int64_t s, int p, int b, T x) { v[s * b + p] = x; }
+};
+template <>
+struct VecAt<df32> {
+    __device__ static int64_t hi_index(int64_t s, int p) { return s * 8 + (p >> 1) * 4 + (p & 1); }
+    __device__ static df32 get(const df32* v, int64_t s, int p, int b) {
+        if (b != 4) return v[s * b + p];
+        const float* f = reinterpret_cast<const float*>(v);
+        const int64_t i = hi_index(s, p);
+        return df32(f[i], f[i + 2]);
+    }
+    __device__ static void set(df32* v, int64_t s, int p, int b, df32 x) {
+        if (b != 4) {
+            v[s * b + p] = x;
+            return;
+        }
+        float* f = reinterpret_cast<float*>(v);
+        const int64_t i = hi_index(s, p);
+        f[i] = x.hi;
+        f[i + 2] = x.lo;
+    }
+};
+
 // Per-realization geometry and run lengths, read by every stencil CTA.
 struct RealInfo {
     int N;            // spins

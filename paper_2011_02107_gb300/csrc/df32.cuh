@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace dacp {
 
@@ -97,6 +98,121 @@ __device__ __forceinline__ void dot2_mad(Dot2& acc, df32 a, df32 b) {
 }
 
 __device__ __forceinline__ df32 dot2_final(Dot2 acc) { return df_fast_two_sum(acc.hi, acc.err); }
+
+// ---- two double-floats per instruction (paired float32 arithmetic) ----------
+//
+// sm_100-family GPUs execute add / sub / mul / fma on pairs of float32
+// (.f32x2) as one instruction. On GB300 a paired instruction takes the
+// float32 pipe for two cycles, so it does not raise the float32 rate, but it
+// halves the issue slots of float32 work: in an issue-bound kernel the loads,
+// shuffles and address arithmetic then issue in the slots freed. A register
+// pair lane 0 | lane 1 holds one component (hi or lo) of two double-floats.
+// Every step below is the same error-free operation as its scalar form above,
+// in the same order, so results are bit-identical to the scalar path.
+
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// -x on both lanes: flips the two sign bits (integer pipe, exact)
+__device__ __forceinline__ uint64_t neg2(uint64_t a) { return a ^ 0x8000000080000000ull; }
+
+// Two double-floats: hi = (x0.hi | x1.hi), lo = (x0.lo | x1.lo).
+struct DF2 {
+    uint64_t hi, lo;
+};
+// A multiplier with its negated hi part, for the TwoProduct below.
+struct DF2m {
+    uint64_t hi, nhi, lo;
+};
+__device__ __forceinline__ DF2m df2m(DF2 a) { return DF2m{a.hi, neg2(a.hi), a.lo}; }
+__device__ __forceinline__ DF2m df2m_bcast(df32 a) {
+    const uint64_t h = pk2(a.hi, a.hi);
+    return DF2m{h, neg2(h), pk2(a.lo, a.lo)};
+}
+
+// Two Dot2 accumulators (running float32 sum and error term per lane).
+struct Dot2x2 {
+    uint64_t hi, err;
+};
+
+// acc = a * b: TwoProduct (q = -p with p = fl(a.hi b.hi), a.hi b.hi - p exact)
+// and the cross terms in the error term.
+__device__ __forceinline__ Dot2x2 dot2x2_prod(const DF2m& a, DF2 b) {
+    const uint64_t q = mul2(a.nhi, b.hi);
+    const uint64_t pe = fma2(a.hi, b.hi, q);
+    return Dot2x2{neg2(q), add2(pe, fma2(a.hi, b.lo, mul2(a.lo, b.hi)))};
+}
+
+// acc += a * b (the Dot2 step): TwoProduct, Knuth's TwoSum of acc.hi + p written
+// with q = -p, and four updates of the error term. 12 paired instructions.
+__device__ __forceinline__ void dot2x2_mad(Dot2x2& acc, const DF2m& a, DF2 b) {
+    const uint64_t q = mul2(a.nhi, b.hi);                  // -p
+    const uint64_t pe = fma2(a.hi, b.hi, q);               // a.hi b.hi - p, exact
+    const uint64_t s = sub2(acc.hi, q);                    // fl(acc.hi + p)
+    const uint64_t bb = sub2(s, acc.hi);
+    const uint64_t e = sub2(sub2(acc.hi, sub2(s, bb)), add2(q, bb));   // acc.hi + p - s, exact
+    acc.hi = s;
+    acc.err = add2(add2(fma2(a.lo, b.hi, fma2(a.hi, b.lo, acc.err)), pe), e);
+}
+
+// acc -= y: the Dot2 step with the factor -1, whose TwoProduct is exact (8 paired
+// instructions).
+__device__ __forceinline__ void dot2x2_sub(Dot2x2& acc, DF2 y) {
+    const uint64_t s = sub2(acc.hi, y.hi);
+    const uint64_t bb = sub2(s, acc.hi);
+    const uint64_t e = sub2(sub2(acc.hi, sub2(s, bb)), add2(y.hi, bb));
+    acc.hi = s;
+    acc.err = add2(sub2(acc.err, y.lo), e);
+}
+
+// Dekker's Fast2Sum of the two parts: the double-float results.
+__device__ __forceinline__ DF2 dot2x2_final(Dot2x2 acc) {
+    const uint64_t s = add2(acc.hi, acc.err);
+    return DF2{s, sub2(acc.err, sub2(s, acc.hi))};
+}
+
+// Lane k of a pair of double-floats, and the scalar Dot2 of lane k.
+__device__ __forceinline__ df32 df2_lane0(DF2 v) {
+    float h0, h1, l0, l1;
+    upk2(v.hi, h0, h1);
+    upk2(v.lo, l0, l1);
+    return df32(h0, l0);
+}
+__device__ __forceinline__ df32 df2_lane1(DF2 v) {
+    float h0, h1, l0, l1;
+    upk2(v.hi, h0, h1);
+    upk2(v.lo, l0, l1);
+    return df32(h1, l1);
+}
+__device__ __forceinline__ void dot2x2_split(Dot2x2 a, Dot2& l0, Dot2& l1) {
+    upk2(a.hi, l0.hi, l1.hi);
+    upk2(a.err, l0.err, l1.err);
+}
 
 // Generic accumulation used by the stencil: plain FMA for float / double,
 // Dot2 for double-float.

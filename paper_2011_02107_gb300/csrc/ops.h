@@ -27,7 +27,7 @@ cudaError_t launch_diag_all(int prec, const RealInfo* real, int R, int max_N, co
 cudaError_t launch_scatter_convert(int prec, const double* src, const int64_t* src_off, const RealInfo* real, int R,
                                    int max_N, int b, void* dst, cudaStream_t st);
 cudaError_t launch_convert(int prec, const double* src, void* dst, int64_t n, cudaStream_t st);
-cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, int b, cudaStream_t st);
 cudaError_t launch_gather_basis(int prec, int b, const void* src, int64_t D, double* V, int64_t ldv, int col0,
                                 cudaStream_t st);
 cudaError_t launch_normalize(int prec, int b, const Item* items, const RealInfo* real, int n_items,

@@ -220,6 +220,12 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// Bulk prefetch of [src, src + bytes) into L2 (no shared memory, no barrier):
+// src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -667,28 +673,29 @@ reduce:
 // h = 0: <o_p, x_q> and h = 1: <x_p, x_q> for p in {0,1}, q in {2,3}. Only the
 // evolution emits moments on this path (its <o, x> block is symmetric).
 
+// A column pair of one state: 16 bytes (hi_p, hi_{p+1}, lo_p, lo_{p+1}) (VecAt<df32>).
 __device__ __forceinline__ void ld2_s(const df32* p, df32& v0, df32& v1) {
     const float4 f = *reinterpret_cast<const float4*>(p);
-    v0 = df32(f.x, f.y);
-    v1 = df32(f.z, f.w);
+    v0 = df32(f.x, f.z);
+    v1 = df32(f.y, f.w);
 }
 
 template <bool COHERENT>
 __device__ __forceinline__ void ld2_g(const df32* p, df32& v0, df32& v1) {
     const float4 f = COHERENT ? __ldcg(reinterpret_cast<const float4*>(p)) : __ldg(reinterpret_cast<const float4*>(p));
-    v0 = df32(f.x, f.y);
-    v1 = df32(f.z, f.w);
+    v0 = df32(f.x, f.z);
+    v1 = df32(f.y, f.w);
 }
 
 template <bool COHERENT>
 __device__ __forceinline__ void ld2_rw(const df32* p, df32& v0, df32& v1) {
     const float4 f = COHERENT ? __ldcg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
-    v0 = df32(f.x, f.y);
-    v1 = df32(f.z, f.w);
+    v0 = df32(f.x, f.z);
+    v1 = df32(f.y, f.w);
 }
 
 __device__ __forceinline__ void st2(df32* p, df32 v0, df32 v1) {
-    *reinterpret_cast<float4*>(p) = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+    *reinterpret_cast<float4*>(p) = make_float4(v0.hi, v1.hi, v0.lo, v1.lo);
 }
 
 static_assert((static_cast<int64_t>(1) << kMaxSpins) * 4 < (static_cast<int64_t>(1) << 31),
@@ -948,6 +955,295 @@ reduce_df4:
     __syncthreads();   // the tile buffer is reused by the next tile of a persistent CTA
 }
 
+// ---- the same pass on paired float32 instructions ---------------------------
+//
+// Each thread's two columns are the two lanes of every .f32x2 instruction
+// (DF2: one register pair holds both columns' hi parts, one their lo parts).
+// Every arithmetic step is the scalar Dot2 step of tile_step_df4, in the same
+// order, so the vectors and moments are bit-identical; the paired form halves
+// the issue slots of the float32 work, which bounds this kernel. The factor
+// -1 of w_{k-1} (evolution) and of w_{k-1} in the filter's second pass is a
+// subtraction without a product. Tiles of TB bits in every realization, no
+// two-body flips (those handles launch tile_step_df4 with TB = 0).
+
+// The 16 bytes of a column pair are (hi_p, hi_{p+1} | lo_p, lo_{p+1}): the two
+// register pairs of a DF2 as they are.
+__device__ __forceinline__ DF2 ld_df2_s(const df32* p) {
+    const ulonglong2 f = *reinterpret_cast<const ulonglong2*>(p);
+    return DF2{f.x, f.y};
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ DF2 ld_df2_g(const df32* p) {
+    const ulonglong2 f = COHERENT ? __ldcg(reinterpret_cast<const ulonglong2*>(p))
+                                  : __ldg(reinterpret_cast<const ulonglong2*>(p));
+    return DF2{f.x, f.y};
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ DF2 ld_df2_rw(const df32* p) {
+    const ulonglong2 f = COHERENT ? __ldcg(reinterpret_cast<const ulonglong2*>(p))
+                                  : *reinterpret_cast<const ulonglong2*>(p);
+    return DF2{f.x, f.y};
+}
+
+__device__ __forceinline__ void st_df2(df32* p, DF2 v) {
+    *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(v.hi, v.lo);
+}
+
+// lanes swapped: (x1 | x0)
+__device__ __forceinline__ DF2 df2_swap(DF2 v) {
+    float h0, h1, l0, l1;
+    upk2(v.hi, h0, h1);
+    upk2(v.lo, l0, l1);
+    return DF2{pk2(h1, h0), pk2(l1, l0)};
+}
+
+__device__ __forceinline__ DF2 df2_shfl_xor(DF2 v, int o) {
+    float h0, h1, l0, l1;
+    upk2(v.hi, h0, h1);
+    upk2(v.lo, l0, l1);
+    return DF2{pk2(__shfl_xor_sync(0xffffffffu, h0, o), __shfl_xor_sync(0xffffffffu, h1, o)),
+               pk2(__shfl_xor_sync(0xffffffffu, l0, o), __shfl_xor_sync(0xffffffffu, l1, o))};
+}
+
+template <int MODE, bool COHERENT, int TB>
+__device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int item, const int step) {
+    static_assert(TB > 0, "the paired pass is specialised on the tile's bit count");
+    using T = df32;
+    constexpr int B = 4, EG = EarlyGlobal<T>::value;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);
+    // per spin: (g.hi, g.hi, g.lo, g.lo) and (-g.hi, -g.hi), the register pairs of a DF2m
+    __shared__ __align__(16) float4 gam_s[kMaxSpins];
+    __shared__ __align__(8) float2 ngam_s[kMaxSpins];
+    __shared__ double red_s[kThreads / 32][2 * B * B];
+    __shared__ int last_s;
+    __shared__ __align__(8) uint64_t bar_s;
+
+    const int tid = threadIdx.x;
+    const int h = tid & 1;
+    const Item it = a.items[item];
+    const RealInfo R = a.real[it.r];
+    int nsteps = (MODE == kEvolve) ? R.ne : (MODE == kApply ? 1 : R.nf);
+    if (MODE != kApply && a.nsteps_override > 0) nsteps = a.nsteps_override;
+    const bool active = step < nsteps;
+    constexpr bool want_mom = MODE == kEvolve;
+    Dot2x2 mp[5];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) mp[e] = Dot2x2{0ull, 0ull};
+
+    if (active) {
+        T* wA = static_cast<T*>(a.bufA);
+        T* wB = static_cast<T*>(a.bufB);
+        T* wk = (step & 1) ? wB : wA;
+        T* wo = (step & 1) ? wA : wB;
+        const T* x;
+        const T* y1 = nullptr;
+        const T* y2 = nullptr;
+        T* out;
+        double c_h, c_1 = 0.0, c_2 = 0.0;
+        const double* cf = a.coef + 8 * it.r + (step == 0 ? 0 : 3);
+        if (MODE == kApply) {
+            x = static_cast<const T*>(a.x); y1 = static_cast<const T*>(a.y1); out = static_cast<T*>(a.out);
+            c_h = cf[0]; c_1 = cf[1];
+        } else if (MODE == kFilter1) {
+            x = wk; out = static_cast<T*>(a.bufU); c_h = 1.0;
+        } else if (MODE == kFilter2) {
+            x = static_cast<const T*>(a.bufU); y1 = wk; y2 = wo; out = wo;
+            c_h = cf[0]; c_1 = cf[1]; c_2 = cf[2];
+        } else {
+            x = wk; y1 = wo; out = wo;
+            c_h = cf[0]; c_1 = cf[1];
+        }
+        const bool use1 = (c_1 != 0.0) && (y1 != nullptr);
+        const bool use2 = (c_2 != 0.0) && (y2 != nullptr);
+        const bool sub1 = c_1 == -1.0, sub2v = c_2 == -1.0;    // uniform over the CTA
+        const T ch = static_cast<T>(c_h);
+        const DF2m C1 = df2m_bcast(static_cast<T>(c_1)), C2 = df2m_bcast(static_cast<T>(c_2));
+
+        constexpr int tstates = 1 << TB;
+        const int64_t tile0 = static_cast<int64_t>(it.tile) << TB;
+        const int64_t gbase = R.off * B;
+        const T* xg = x + gbase;
+        const T* y1g = (MODE != kFilter1 && y1) ? y1 + gbase : nullptr;
+        const T* y2g = (MODE == kFilter2 && y2) ? y2 + gbase : nullptr;
+        T* outg = out + gbase;
+        const T* dg = static_cast<const T*>(a.diag) + R.off;
+        if (tid < R.N) {
+            const T g = ch * static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
+            gam_s[tid] = make_float4(g.hi, g.hi, g.lo, g.lo);
+            ngam_s[tid] = make_float2(-g.hi, -g.hi);
+        }
+
+        constexpr uint32_t nbytes = static_cast<uint32_t>(tstates) * B * sizeof(T);
+        if (tid == 0) {
+            mbar_init(&bar_s, 1);
+            bulk_load(tile, xg + tile0 * B, nbytes, &bar_s);
+            // evolution: the tile's rows of w_{k-1} and of the diagonal, which the threads
+            // read once each, into L2 while the tile lands (offsets are multiples of 4
+            // states, so every start is 16-byte aligned). 176 against 184 us per order on
+            // the 256-shard batch; in the filter's second pass, prefetching w_k and w_{k-1}
+            // pushed u out of L2 (292 against 275 us), so the filter does without.
+            if (MODE == kEvolve && use1) bulk_prefetch_l2(y1g + tile0 * B, nbytes);
+            if (MODE == kEvolve) bulk_prefetch_l2(dg + tile0, static_cast<uint32_t>(tstates) * sizeof(T));
+        }
+        __syncthreads();
+        const bool landed = mbar_wait(&bar_s, 0, kWaitLimit);
+        if (!landed) {
+            atomicExch(a.err_flag, 1);
+            mbar_wait(&bar_s, 0, kWaitLimit);        // let the copy land before the CTA exits
+        }
+        __syncthreads();
+        if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar_s)) : "memory");
+        if (!landed) goto reduce_df4x2;
+
+        {
+        const int ngb = R.N - TB;
+        constexpr int nhalf = 2 * tstates;               // (state, column pair) slots of the tile
+        const ulonglong2* g2 = reinterpret_cast<const ulonglong2*>(gam_s);
+        const uint64_t* ng2 = reinterpret_cast<const uint64_t*>(ngam_s);
+        for (int hb = 0; hb < nhalf; hb += kThreads) {
+            const int hs = hb + tid;
+            const bool val = (TB >= 7) || hs < nhalf;
+            const int sl = val ? (hs >> 1) : 0;
+            const uint32_t sg = static_cast<uint32_t>(tile0) + static_cast<uint32_t>(sl);
+            const int col = 2 * h;
+            const DF2 A = ld_df2_s(tile + sl * B + col);
+            DF2 pe[EG > 0 ? EG : 1];
+#pragma unroll
+            for (int j = 0; j < EG; ++j)
+                if (j < ngb) pe[j] = ld_df2_g<COHERENT>(xg + ((sg ^ (1u << (TB + j))) * B + col));
+            const T dr = ld_ro(dg + sg);
+            DF2 Y = DF2{0ull, 0ull}, Z = DF2{0ull, 0ull};
+            if (MODE != kFilter1 && use1) Y = ld_df2_rw<COHERENT>(y1g + (sg * B + col));
+            if (MODE == kFilter2 && use2) Z = ld_df2_rw<COHERENT>(y2g + (sg * B + col));
+            // flips inside the tile; bit 0 starts the sums
+            Dot2x2 acc;
+            {
+                const ulonglong2 gv = g2[0];
+                acc = dot2x2_prod(DF2m{gv.x, ng2[0], gv.y}, ld_df2_s(tile + (sl ^ 1) * B + col));
+            }
+#pragma unroll
+            for (int i = 1; i < TB; ++i) {
+                const ulonglong2 gv = g2[i];
+                dot2x2_mad(acc, DF2m{gv.x, ng2[i], gv.y}, ld_df2_s(tile + (sl ^ (1 << i)) * B + col));
+            }
+            // flips beyond the tile
+#pragma unroll
+            for (int j = 0; j < EG; ++j) {
+                if (j < ngb) {
+                    const ulonglong2 gv = g2[TB + j];
+                    dot2x2_mad(acc, DF2m{gv.x, ng2[TB + j], gv.y}, pe[j]);
+                }
+            }
+            for (int j = EG; j < ngb; ++j) {
+                const ulonglong2 gv = g2[TB + j];
+                dot2x2_mad(acc, DF2m{gv.x, ng2[TB + j], gv.y},
+                           ld_df2_g<COHERENT>(xg + ((sg ^ (1u << (TB + j))) * B + col)));
+            }
+            // diagonal term, then w_{k+1} = c_h H x + c_1 y + c_2 z
+            dot2x2_mad(acc, df2m_bcast(ch * dr), A);
+            if (MODE != kFilter1 && use1) {
+                if (sub1) dot2x2_sub(acc, Y);
+                else dot2x2_mad(acc, C1, Y);
+            }
+            if (MODE == kFilter2 && use2) {
+                if (sub2v) dot2x2_sub(acc, Z);
+                else dot2x2_mad(acc, C2, Z);
+            }
+            const DF2 O = dot2x2_final(acc);
+            if (val) st_df2(outg + (sg * B + col), O);
+            if (want_mom) {
+                const DF2 Cx = df2_shfl_xor(A, 1);        // the other pair's x
+                if (val) {
+                    // h = 0: (x0 x0 | x1 x1), (o0 x0 | o1 x1), (x0 x1 | o0 x1), (o0 x2 | o1 x3), (o0 x3 | o1 x2)
+                    // h = 1: the same with columns 2, 3 for 0, 1, and <x_p, x_q> across the pairs
+                    const DF2m Am = df2m(A);
+                    dot2x2_mad(mp[0], Am, A);
+                    dot2x2_mad(mp[1], Am, O);
+                    {
+                        float ah0, ah1, al0, al1, oh0, oh1, ol0, ol1;
+                        upk2(A.hi, ah0, ah1);
+                        upk2(A.lo, al0, al1);
+                        upk2(O.hi, oh0, oh1);
+                        upk2(O.lo, ol0, ol1);
+                        const DF2 X01 = DF2{pk2(ah0, oh0), pk2(al0, ol0)};
+                        dot2x2_mad(mp[2], df2m(X01), DF2{pk2(ah1, ah1), pk2(al1, al1)});
+                    }
+                    const DF2 U = h ? Cx : O, V = h ? A : Cx;
+                    const DF2m Um = df2m(U);
+                    dot2x2_mad(mp[3], Um, V);
+                    dot2x2_mad(mp[4], Um, df2_swap(V));
+                }
+            }
+        }
+        }
+    }
+
+reduce_df4x2:
+    if (want_mom && active) {
+        const int lane = tid & 31, warp = tid >> 5;
+        // the ten sums in the order of tile_step_df4: (x0x0, x0x1, x1x1, o0x0, o0x1, o1x1,
+        // u0v0, u0v1, u1v0, u1v1) for h = 0; columns shifted by two for h = 1
+        Dot2 ms[10];
+        dot2x2_split(mp[0], ms[0], ms[2]);
+        dot2x2_split(mp[1], ms[3], ms[5]);
+        dot2x2_split(mp[2], ms[1], ms[4]);
+        dot2x2_split(mp[3], ms[6], ms[9]);
+        dot2x2_split(mp[4], ms[7], ms[8]);
+        df32 xs[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) xs[e] = e < 10 ? dot2_final(ms[e]) : df32(0.f, 0.f);
+        const df32 t = warp_reduce_scatter<16, 2>(xs, lane);
+        const int e = (lane >> 1) & 15;
+        if (e < 10) {
+            int blk, p, q;
+            if (e < 6) {
+                blk = e / 3;
+                const int k = e % 3;
+                p = 2 * h + (k == 2 ? 1 : 0);
+                q = 2 * h + (k >= 1 ? 1 : 0);
+            } else {
+                blk = h == 0 ? 1 : 0;
+                p = (e - 6) >> 1;
+                q = 2 + ((e - 6) & 1);
+            }
+            const double v = static_cast<double>(t);
+            double* rw = red_s[warp];
+            rw[blk * B * B + p * B + q] = v;
+            rw[blk * B * B + q * B + p] = v;
+        }
+        __syncthreads();
+        if (tid < 2 * B * B) {
+            double sm = 0.0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) sm += red_s[w][tid];
+            a.part[static_cast<int64_t>(item) * 2 * B * B + tid] = sm;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(&a.real_done[it.r], 1u);
+            last_s = (prev == static_cast<unsigned>(R.item_count - 1));
+        }
+        __syncthreads();
+        if (last_s) {
+            __threadfence();
+            if (tid < 2 * B * B) {
+                double sm = 0.0;
+                for (int j = 0; j < R.item_count; ++j)
+                    sm += __ldcg(a.part + static_cast<int64_t>(R.item_begin + j) * 2 * B * B + tid);
+                const int row = 2 * step;
+                const int64_t row0 = a.mom_rows_fixed > 0 ? static_cast<int64_t>(it.r) * a.mom_rows_fixed : R.mom_off;
+                a.mom[(row0 + row) * B * B + tid] = sm;
+            }
+            if (tid == 0) a.real_done[it.r] = 0u;
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T, int B, int MODE, bool COHERENT>
 __device__ __forceinline__ void tile_step_any(const StepArgs& a, const int item, const int step) {
     if constexpr (std::is_same<T, df32>::value && B == 4) tile_step_df4<MODE, COHERENT>(a, item, step);
@@ -960,7 +1256,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<df32, 4>::value) step_kern
                                                                                          int item_base) {
     int step = 0;
     if (MODE != kApply) step = *a.step_ctr;
-    tile_step_df4<MODE, false, TB>(a, item_base + blockIdx.x, step);
+    tile_step_df4x2<MODE, false, TB>(a, item_base + blockIdx.x, step);
     if (MODE == kFilter2 || MODE == kEvolve) {
         if (threadIdx.x == 0) {
             __threadfence();
@@ -1342,10 +1638,9 @@ __global__ void scatter_convert_kernel(const double* __restrict__ src, const int
     const RealInfo R = real[r];
     const int64_t n = (static_cast<int64_t>(1) << R.N) * b;
     const double* s = src + src_off[r];
-    T* d = dst + R.off * b;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        d[i] = static_cast<T>(s[i]);
+        VecAt<T>::set(dst, R.off + i / b, static_cast<int>(i % b), b, static_cast<T>(s[i]));
 }
 
 template <typename T>
@@ -1359,14 +1654,15 @@ template <typename T>
 __global__ void extract_col_kernel(const T* __restrict__ src, T* __restrict__ dst, int b, int64_t states) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < states;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        dst[i] = src[i * b];
+        dst[i] = VecAt<T>::get(src, i, 0, b);
 }
 
+// n / b states of a [state][b] vector to float64, element (s, p) at s * b + p.
 template <typename T>
-__global__ void to_double_kernel(const T* __restrict__ src, double* __restrict__ dst, int64_t n) {
+__global__ void to_double_kernel(const T* __restrict__ src, double* __restrict__ dst, int64_t n, int b) {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        dst[i] = static_cast<double>(src[i]);
+        dst[i] = static_cast<double>(VecAt<T>::get(src, i / b, static_cast<int>(i % b), b));
 }
 
 // Squared column norms of each realization's vector; src is chosen per
@@ -1389,10 +1685,10 @@ __global__ void __launch_bounds__(kThreads) colnorm_kernel(const Item* __restric
 #pragma unroll
     for (int p = 0; p < B; ++p) acc[p] = 0.0;
     for (int sl = tid; sl < tstates; sl += kThreads) {
-        const T* q = src + (R.off + tile0 + sl) * B;
+        const int64_t sg = R.off + tile0 + sl;
 #pragma unroll
         for (int p = 0; p < B; ++p) {
-            const double v = static_cast<double>(q[p]);
+            const double v = static_cast<double>(VecAt<T>::get(src, sg, p, B));
             acc[p] = fma(v, v, acc[p]);
         }
     }
@@ -1440,12 +1736,12 @@ __global__ void __launch_bounds__(kThreads) normalize_kernel(const Item* __restr
 #pragma unroll
     for (int p = 0; p < B; ++p) sc[p] = static_cast<T>(1.0 / sqrt(norms[it.r * B + p]));
     for (int sl = tid; sl < tstates; sl += kThreads) {
-        const int64_t e = (R.off + tile0 + sl) * B;
+        const int64_t sg = R.off + tile0 + sl;
 #pragma unroll
         for (int p = 0; p < B; ++p) {
-            const T v = src[e + p] * sc[p];
-            dst[e + p] = v;
-            if (dst2) dst2[e + p] = v;
+            const T v = VecAt<T>::get(src, sg, p, B) * sc[p];
+            VecAt<T>::set(dst, sg, p, B, v);
+            if (dst2) VecAt<T>::set(dst2, sg, p, B, v);
         }
     }
 }
@@ -1503,7 +1799,7 @@ __global__ void gather_basis_kernel(const T* __restrict__ src, int b, int64_t D,
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int p = static_cast<int>(i / D);
         const int64_t s = i % D;
-        V[(col0 + p) * ldv + s] = static_cast<double>(src[s * b + p]);
+        V[(col0 + p) * ldv + s] = static_cast<double>(VecAt<T>::get(src, s, p, b));
     }
 }
 
@@ -1516,10 +1812,10 @@ cudaError_t launch_gather_basis(int prec, int b, const void* src, int64_t D, dou
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, cudaStream_t st) {
+cudaError_t launch_to_double(int prec, const void* src, double* dst, int64_t n, int b, cudaStream_t st) {
     const int grid = static_cast<int>((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
     if (n == 0) return cudaSuccess;
-    DACP_FOR_PREC(prec, to_double_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(src), dst, n);
+    DACP_FOR_PREC(prec, to_double_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(src), dst, n, b);
                         return cudaGetLastError());
     return cudaErrorInvalidValue;
 }

@@ -21,6 +21,7 @@ import pytest
 
 import workloads as W
 from oracle import hamiltonian as Hm
+from tests.conftest import df32_pack, df32_unpack
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -58,17 +59,17 @@ def test_apply_h_at_maximum_size(N, b, prec, tile):
             xd = torch.from_numpy(x.astype(np.float32)).cuda()
             xin = x.astype(np.float32).astype(np.float64)
         else:
-            hi = x.astype(np.float32)
-            lo = (x - hi.astype(np.float64)).astype(np.float32)
-            xd = torch.from_numpy(np.stack([hi, lo], axis=-1)).cuda()
-            xin = hi.astype(np.float64) + lo.astype(np.float64)
+            packed = df32_pack(x)
+            xd = torch.from_numpy(packed).cuda()
+            xin = df32_unpack(packed, b)
+            del packed
         yd = torch.zeros_like(xd)
         d.apply_h(0, xd.data_ptr(), yd.data_ptr())
         torch.cuda.synchronize()
         idx = torch.from_numpy(rows).cuda()
         got = yd[idx].double().cpu().numpy()
         if prec == "df32":
-            got = got[..., 0] + got[..., 1]
+            got = df32_unpack(got, b)
         del xd, yd
         ref, scale = Hm.apply_h_rows(m, xin, rows, with_abs=True)
         unit = {"fp64": 2.0 ** -53, "fp32": 2.0 ** -24, "df32": 2.0 ** -44}[prec]

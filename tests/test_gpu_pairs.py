@@ -18,6 +18,7 @@ import pytest
 import workloads as W
 from oracle import hamiltonian as Hm
 from oracle import metrics as MT
+from tests.conftest import df32_pack, df32_unpack
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -44,9 +45,8 @@ def _to_dev(x, prec):
         return torch.from_numpy(x).cuda(), x
     if prec == "fp32":
         return torch.from_numpy(x.astype(np.float32)).cuda(), x.astype(np.float32).astype(np.float64)
-    hi = x.astype(np.float32)
-    lo = (x - hi.astype(np.float64)).astype(np.float32)
-    return torch.from_numpy(np.stack([hi, lo], axis=-1)).cuda(), hi.astype(np.float64) + lo.astype(np.float64)
+    packed = df32_pack(x)
+    return torch.from_numpy(packed).cuda(), df32_unpack(packed, x.shape[1])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "df32"])
@@ -66,7 +66,7 @@ def test_apply_h_with_pair_couplings(prec, b):
             torch.cuda.synchronize()
             got = yd.double().cpu().numpy()
             if prec == "df32":
-                got = got[..., 0] + got[..., 1]
+                got = df32_unpack(got, b)
             rows = np.arange(1 << m["N"])
             ref, scale = Hm.apply_h_rows(m, xin, rows, with_abs=True)
             assert np.abs(Hm.apply_h(m, xin) - ref).max() <= 1e-12 * np.abs(ref).max()
