@@ -67,25 +67,36 @@ def make_inputs(wl, rank=0):
     return models, psis
 
 
-DF32_EVOLVE_TRAFFIC = 302504192 + 104424448   # bytes, step_kernel_df4tb<kEvolve, 11>, one launch (ncu)
+# DRAM bytes (read + write) of one evolution launch of step_kernel_df4tb<kEvolve, 11> with all 256
+# realizations of the default workload active, from one ncu capture of the current kernel (the
+# profile summaries keep the command); other workloads report none.
+DF32_EVOLVE_TRAFFIC = 319758592 + 101683968
+DF32_TRAFFIC_SOURCE = "stored ncu capture of the current kernel, one launch, not re-measured in this run"
 # One error-free double-float multiply-add (the Dot2 step): TwoProduct 2,
-# TwoSum 6, and 4 float32 instructions that fold the cross terms and the two
-# rounding errors into the error term.
-DF_FMA_INSTR = 12
-SMS, FP32_LANES_PER_SM = 152, 128
+# TwoSum 6, and 4 float32 operations that fold the cross terms and the two
+# rounding errors into the error term. A subtraction of w_{k-1} (factor -1)
+# needs no product: 8. The kernel issues them as paired (.f32x2) instructions,
+# two float32 lane operations each.
+DF_FMA_OPS, DF_SUB_OPS = 12, 8
+FP32_LANES_PER_SM = 128
 
 
-def roofline(wl, models, phase, bytes_evo, states_evo, clk, launch_mode=0):
+def sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def roofline(wl, models, phase, bytes_evo, states_evo, clk, sms, launch_mode=0):
     """Roofline of the evolution stencil over the timed steps.
 
     float32: HBM-bound; algorithmic bytes = 3 * 2^N * b * 4 per order (read
     w_k, read w_{k-1}, write w_{k+1}) against the measured copy bandwidth.
-    double-float: float32-issue bound; algorithmic work per state and order =
-    (N b flips + b diagonal + b recurrence + b(b+1)/2 <w_k, w_k> + b(b+1)/2
-    <w_{k+1}, w_k> products; c_h is folded into the fields and both moment
-    blocks are symmetric) double-float multiply-adds x DF_FMA_INSTR float32
-    instructions, against 152 SMs x 128 lanes x the SM clock sampled during
-    the run.
+    double-float: float32-pipe bound; algorithmic work per state and order =
+    (N b flips + b diagonal + b(b+1)/2 <w_k, w_k> + b(b+1)/2 <w_{k+1}, w_k>
+    products; c_h is folded into the fields and both moment blocks are
+    symmetric) double-float multiply-adds x DF_FMA_OPS float32 lane operations,
+    plus b subtractions of w_{k-1} x DF_SUB_OPS, against the device's SMs x 128
+    lanes x the SM clock sampled during the run.
     float64: FP64-pipe bound; same multiply-add count against the measured
     float64 dgemm rate (1.10 TFLOP/s = 0.55 T FMA/s on this GB300).
     """
@@ -99,7 +110,9 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk, launch_mode=0):
     b = wl["b"]
     N = wl["N"]
     fma_per_state = N * b + 2 * b + b * (b + 1)
-    kern = {"fp32": "step_kernel<float,4,kEvolve>", "df32": "step_kernel_df4tb<kEvolve,11> (double-float, b = 4)",
+    df_ops_per_state = DF_FMA_OPS * (N * b + b + b * (b + 1)) + DF_SUB_OPS * b
+    kern = {"fp32": "step_kernel<float,4,kEvolve>",
+            "df32": "step_kernel_df4tb<kEvolve,11> (double-float, b = 4, paired float32 instructions)",
             "fp64": "step_kernel<double,4,kEvolve>"}[wl["prec"]]
     if wl["prec"] == "fp32":
         if launch_mode == 2:
@@ -111,19 +124,19 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk, launch_mode=0):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic": "3 * 2^N * b * 4 B per realization and order"}
     if wl["prec"] == "df32":
-        # DRAM bytes of one evolution launch with all 256 realizations of the default workload
-        # active, from one ncu capture of the current kernel (profiles/); other workloads: none
         traffic = DF32_EVOLVE_TRAFFIC if (N, b, len(models)) == (14, 4, 256) else None
         mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
-        peak = SMS * FP32_LANES_PER_SM * mhz * 1e6 / 1e12            # T instr/s
-        achieved = states_evo * fma_per_state * DF_FMA_INSTR / t_e / 1e12 if t_e > 0 else None
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T float32 instr/s",
+        peak = sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12            # T lane-ops/s
+        achieved = states_evo * df_ops_per_state / t_e / 1e12 if t_e > 0 else None
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T float32 lane-ops/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one full evolution launch "
-                                "(all 256 realizations active); algorithmic 402.7 MB + 33.6 MB diagonal"
-                                if traffic else None, "kernel": kern,
-                "peak_source": f"152 SMs x 128 float32 lanes x {mhz:.0f} MHz (sampled)",
-                "algorithmic": f"{fma_per_state} double-float FMA x {DF_FMA_INSTR} instr per state and order"}
+                "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full evolution launch "
+                                 "(all 256 realizations active), " + DF32_TRAFFIC_SOURCE +
+                                 "; algorithmic 402.7 MB + 33.6 MB diagonal") if traffic else None,
+                "kernel": kern,
+                "peak_source": f"{sms} SMs x 128 float32 lanes x {mhz:.0f} MHz (sampled)",
+                "algorithmic": f"{DF_FMA_OPS} x {N * b + b + b * (b + 1)} double-float FMA + {DF_SUB_OPS} x {b} "
+                               f"subtractions = {df_ops_per_state} float32 lane operations per state and order"}
     peak = 0.55                                                         # T FMA/s, measured dgemm
     achieved = states_evo * fma_per_state / t_e / 1e12 if t_e > 0 else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T float64 FMA/s",
@@ -290,7 +303,7 @@ def oracle_sample(wl, budget_s=15.0, procs=None):
             f"({x['t_hv'] * 1e3:.2f} ms each), one {x['M']}x{x['M']} generalized eigensolve {x['t_gep']:.2f}s; "
             f"mean {t_real:.0f}s per realization extrapolated from {x['hv_total']} H.v; "
             f"{wl['R']} realizations over {procs} core(s) = {t_batch:.0f}s per batch")
-    return rate, desc, procs
+    return rate, desc, procs, wl["n_eigs"] / t_real
 
 
 def _oracle_sample_child(wl, budget_s, r=0):
@@ -448,6 +461,33 @@ def run_gpu(args, wl, rank, world):
 
     exact = exact_accuracy(wl, rank, last_eigs, n_eigs)
 
+    # ---- plain float64 DACP on the same GPU and workload (the comparison the metric names):
+    # float64 vectors, the paper's parameters (Sec. III heuristic: c = 18, window ratio 2, basis
+    # ratio 1.5), one step over the whole batch, outside the timed region, same end-of-step sync
+    fp64_arm = None
+    if args.fp64_arm and wl["prec"] != "fp64" and R > 0:
+        d64 = P.Dacp(models, psis, block_b=wl["b"], precision=P.DACP_FP64, stream=stream.cuda_stream)
+        try:
+            d64.choose_params(n_eigs, c_order=18.0)
+            d64.autotune(16)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d64.choose_params(n_eigs, c_order=18.0)
+            _, nf64, _ = d64.run(n_eigs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            ph64 = d64.timings()
+        finally:
+            d64.close()
+        v64 = float(np.clip(nf64, 0, None).sum()) / (ms64 / 1e3)
+        fp64_arm = {"value": v64, "unit": UNIT, "ms_per_step": ms64, "ratio": value / v64 if v64 > 0 else None,
+                    "realizations": R, "phase_ms": {"T_F": ph64[0], "T_E": ph64[1], "T_D": ph64[2]},
+                    "note": "plain float64 vectors and moments, heuristic (paper) parameters, the whole batch, "
+                            "one step on the same GPU after the timed steps; ratio = value / this value"}
+
     # ---- e2e: public API from pinned host buffers, H2D and D2H inside the timed region
     n_spins, J, h, g = W.pack_models(models)
     psi_flat = np.concatenate([p.ravel() for p in psis])
@@ -466,9 +506,14 @@ def run_gpu(args, wl, rank, world):
         try:
             P.dacp_choose_params(hd, n_eigs)
             P.dacp_autotune(hd)            # cached: only switches the tile size
-            if mlp is not None:
-                P.dacp_choose_params_mlp(hd, mlp, n_eigs)
-            eigs, nf, rk = P.dacp_solve(hd, R, n_eigs)
+            if args.emax_rule:
+                P.dacp_set_emax_rule(hd, args.emax_rule)
+            if mlp is not None:           # learned parameters, heuristic re-run in the library
+                eigs, nf, rk, _ = P.dacp_solve_learned(hd, mlp, R, n_eigs)
+            else:
+                if args.emax_rule:
+                    P.dacp_choose_params(hd, n_eigs)
+                eigs, nf, rk = P.dacp_solve(hd, R, n_eigs)
             found_e2e += int(np.clip(nf, 0, None).sum())
         finally:
             P.dacp_destroy(hd)
@@ -480,7 +525,7 @@ def run_gpu(args, wl, rank, world):
         P.dacp_mlp_destroy(mlp)
 
     # ---- roofline of the dominant kernel (evolution stencil), per vector precision
-    roof = roofline(wl, models, phase, bytes_evo, states_evo, clk, launch_mode)
+    roof = roofline(wl, models, phase, bytes_evo, states_evo, clk, sm_count(), launch_mode)
     # H.v HBM bandwidth of the evolution (algorithmic bytes: read w_k, read w_{k-1},
     # write w_{k+1}) against the measured copy bandwidth, for every precision
     try:
@@ -493,6 +538,11 @@ def run_gpu(args, wl, rank, world):
     hbm = {"achieved_gbs": hbm_gbs, "peak_gbs": hbm_peak, "frac": hbm_gbs / hbm_peak if hbm_gbs else None,
            "bytes": "3 * 2^N * b * value size per realization and order, over T_E",
            "bound_here": roof["bound"]}
+    esz = 4 if wl["prec"] == "fp32" else 8
+    ws = 3 * sum((1 << m["N"]) * wl["b"] * esz for m in models)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    l2_note = (f"inputs larger than L2: the evolution's working set (w_k, w_(k-1), w_(k+1)) is "
+               f"{ws / 2**20:.0f} MiB against the {l2 / 2**20:.0f} MiB L2 ({ws / l2:.1f}x)")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -500,7 +550,7 @@ def run_gpu(args, wl, rank, world):
         "data": "synthetic (seeded random couplings and Gaussian start vectors)",
         "config": {"workload": wl["desc"], "realizations_per_gpu": R, "N": wl["N"], "n_eigs": n_eigs,
                    "block_b": wl["b"], "precision": wl["prec"],
-                   "L2": "working set of the recurrences (3 x 64 MB) exceeds the 129 MB L2",
+                   "L2": l2_note,
                    "parallelism": f"independent realizations, {world} GPU(s)",
                    "emax_mean": float(np.mean(params["emax"])), "a_mean": float(np.mean(params["a"])),
                    "K_max": int(params["K"].max()), "kn_max": int(params["kn"].max()),
@@ -517,6 +567,7 @@ def run_gpu(args, wl, rank, world):
         "parameter_choice": "learned network (heuristic fallback)" if mlp is not None else "heuristic",
         "accuracy": accuracy,
         "accuracy_exact": exact,
+        "fp64_same_gpu": fp64_arm,
         "fallback_realizations": fallbacks[0],
         "tile_bytes": tile_bytes,
         "launch_mode": launch_mode,
@@ -544,6 +595,8 @@ def main():
                     help="override the workload's precision (df32: double-float vectors on the float32 pipes)")
     ap.add_argument("--realizations", type=int, default=None, help="override the number of realizations per GPU")
     ap.add_argument("--n-eigs", type=int, default=None, help="override the central eigenvalues per realization")
+    ap.add_argument("--no-fp64-arm", dest="fp64_arm", action="store_false",
+                    help="skip the plain float64 run of the same batch on the same GPU after the timed steps")
     ap.add_argument("--emax-rule", type=int, default=0, choices=[0, 1],
                     help="E_max bound of the parameter choice: 0 Ritz value + residual norm (default), "
                          "1 Ritz-residual rule (tighter, a bound in practice)")
@@ -574,7 +627,7 @@ def main():
         vals = []
         desc = ""
         for _ in range(args.warmup + args.steps):
-            v, desc, cores = oracle_sample(wl, budget_s=8.0)
+            v, desc, cores, _ = oracle_sample(wl, budget_s=8.0)
             vals.append(v)
         v = float(np.mean(vals[args.warmup:]))
         print(json.dumps({
@@ -598,8 +651,11 @@ def main():
     out = run_gpu(args, wl, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
-            v, desc, cores = oracle_sample(wl)
-            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+            v, desc, cores, v1 = oracle_sample(wl)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                                   "value_one_core": v1,
+                                   "one_core_note": "one single-threaded process's own rate (the paper's "
+                                                    "sequential mode), taken while the other cores ran theirs"}
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -406,11 +406,31 @@ void dacp_mlp_destroy(dacp_mlp m);
  * pass over all realizations on the device, and the window / order / basis
  * from the predicted knobs (clamped to window ratio [1, 4], c [3, 24],
  * basis ratio [0.6, 3]). The network must have 40 inputs and 3 outputs.
- * Callers fall back to dacp_choose_params for realizations whose
- * dacp_central_eigs count comes back short.
+ * dacp_solve_learned runs the path with these parameters and falls back to
+ * dacp_choose_params for realizations whose count comes back short.
  */
 dacp_status dacp_choose_params_mlp(dacp_handle hd, dacp_mlp m, int n_eigs, int lanczos_steps,
                                    int kpm_moments);
+
+/*
+ * dacp_solve_learned -- the whole path with the network's parameters and the
+ * heuristic as fallback: dacp_choose_params_mlp (20 Lanczos steps, 256 KPM
+ * moments), then dacp_solve; every realization that returns fewer than n_eigs
+ * levels (n_found[r] < n_eigs, failures included) is run again with the
+ * heuristic of dacp_choose_params (d_ratio 2, basis ratio 1.5, the precision's
+ * filter constant, the handle's E_max rule) on a handle of its own, built from
+ * this handle's copies of its couplings, fields, pair couplings and start
+ * vectors, on the same stream; its results replace the learned ones.
+ *   net         a 40-input, 3-output network (dacp_mlp_create); not modified.
+ *   n_eigs, window, eps, eigs, n_found, rank  as in dacp_solve.
+ *   n_fallback  may be NULL; the number of realizations re-run.
+ * The handle keeps the learned run's state (moments, timings); the re-run's
+ * device work is counted in dacp_get_launch_count but not in
+ * dacp_get_timings. Errors: as dacp_choose_params_mlp and dacp_solve;
+ * a failed re-run returns its status with its message.
+ */
+dacp_status dacp_solve_learned(dacp_handle hd, dacp_mlp net, int n_eigs, double window, double eps, double* eigs,
+                               int* n_found, int* rank, int* n_fallback);
 
 /* dacp_get_features -- the 40 network features of every realization
  * (float32, [n_real][40]) from the last parameter choice. */

@@ -36,7 +36,7 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
            "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings",
-           "dacp_set_emax_rule", "dacp_test_emax_rule"]
+           "dacp_set_emax_rule", "dacp_test_emax_rule", "dacp_solve_learned"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -71,6 +71,7 @@ def _load():
         "dacp_get_filtered": [P, I, P, L],
         "dacp_residuals": [P, I, I, D, D, P, P, P],
         "dacp_solve": [P, I, D, D, P, P, P],
+        "dacp_solve_learned": [P, P, I, D, D, P, P, P, P],
         "dacp_eigenvectors": [P, I, I, D, D, P, P, L, P],
         "dacp_apply_h": [P, I, P, P],
         "dacp_set_pair_couplings": [P, P, P],
@@ -189,6 +190,18 @@ def dacp_solve(hd, R, n_eigs, window=0.0, eps=0.0):
     rank = np.zeros(R, dtype=np.int32)
     _check(hd, _lib.dacp_solve(hd, int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(nf), _ptr(rank)))
     return eigs.reshape(R, n_eigs), nf, rank
+
+
+def dacp_solve_learned(hd, m, R, n_eigs, window=0.0, eps=0.0):
+    """Network parameters, overlapped solve, heuristic re-run of short realizations (all in the
+    library). Returns (eigs [R, n_eigs], n_found, rank, n_fallback)."""
+    eigs = np.zeros(R * n_eigs)
+    nf = np.zeros(R, dtype=np.int32)
+    rank = np.zeros(R, dtype=np.int32)
+    nfb = ctypes.c_int(0)
+    _check(hd, _lib.dacp_solve_learned(hd, m, int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(nf),
+                                       _ptr(rank), ctypes.byref(nfb)))
+    return eigs.reshape(R, n_eigs), nf, rank, nfb.value
 
 
 def dacp_get_moments(hd, r, cap):
@@ -474,25 +487,16 @@ class Dacp:
 
     def solve(self, n_eigs, mlp=None, window=0.0, eps=0.0):
         """Whole path for the batch: parameters (network when given, else the
-        heuristic), filter, evolution, subspace solve. Realizations for which
-        the network's parameters return fewer than n_eigs levels are re-run
-        with the heuristic. Returns (eigs list, n_found, rank, n_fallback)."""
-        if mlp is not None:
-            self.choose_params_mlp(mlp, n_eigs)
-        else:
+        heuristic), filter, evolution, subspace solve. With a network the
+        library re-runs, with the heuristic, every realization whose learned
+        parameters return fewer than n_eigs levels (dacp_solve_learned).
+        Returns (eigs list, n_found, rank, n_fallback)."""
+        if mlp is None:
             self.choose_params(n_eigs)
-        eigs, nf, rank = self.run(n_eigs, window, eps)
-        redo = [r for r in range(self.R) if nf[r] < n_eigs] if mlp is not None else []
-        if redo:
-            sub = Dacp([self.models[r] for r in redo], [self.psi0_list[r] for r in redo], self.b, self.precision,
-                       self.stream)
-            try:
-                e2, nf2, rk2, _ = sub.solve(n_eigs, None, window, eps)
-            finally:
-                sub.close()
-            for j, r in enumerate(redo):
-                eigs[r], nf[r], rank[r] = e2[j], nf2[j], rk2[j]
-        return eigs, nf, rank, len(redo)
+            eigs, nf, rank = self.run(n_eigs, window, eps)
+            return eigs, nf, rank, 0
+        e, nf, rank, nfb = dacp_solve_learned(self.handle, mlp, self.R, n_eigs, window, eps)
+        return [e[r, :max(nf[r], 0)].copy() for r in range(self.R)], nf, rank, nfb
 
     def run(self, n_eigs, window=0.0, eps=0.0):
         """Filter, evolution and subspace solves with the solves overlapped (dacp_solve)."""

@@ -91,6 +91,8 @@ struct dacp_ctx {
     std::vector<double> pnorm;          // Pauli 1-norm of each H: clamp of the E_max bound
     std::vector<double> pnorm0;         // the same without the pair couplings
     bool has_pairs = false;             // dacp_set_pair_couplings gave nonzero XX / YY terms
+    std::vector<double> jxx_h, jyy_h;   // the caller's pair couplings (packed as given), for re-runs
+    std::vector<double> psi0_h;         // the caller's start vectors (packed float64), for re-runs
     int* n_pairs_d = nullptr;           // [R]
     int* pair_ij_d = nullptr;           // [R][kMaxPairs]
     double* pair_c_d = nullptr;         // [R][kMaxPairs][2]
@@ -682,6 +684,7 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const 
         // the caller's layout is packed; the device layout pads each realization to 4 states
         int64_t packed_total = 0;
         for (int r = 0; r < n_real; ++r) packed_total += (static_cast<int64_t>(1) << c->N[r]) * block_b;
+        c->psi0_h.assign(psi0, psi0 + packed_total);
         ok = ok && ck(cudaMemsetAsync(c->psi0_d, 0, static_cast<size_t>(nv) * c->esz, c->st)) &&
              ck(cudaMemcpyAsync(tmp2, psi0, static_cast<size_t>(packed_total) * 8, cudaMemcpyHostToDevice, c->st));
         std::vector<int64_t> src_off(n_real);
@@ -1447,6 +1450,71 @@ dacp_status dacp_solve(dacp_handle c, int n_eigs, double window, double eps, dou
     return DACP_OK;
 }
 
+// Realizations whose learned parameters returned fewer than n_eigs levels go
+// through the heuristic on a handle of their own, built from this handle's host
+// copies of their couplings, fields and start vectors.
+dacp_status dacp_solve_learned(dacp_handle c, dacp_mlp net, int n_eigs, double window, double eps, double* eigs,
+                               int* n_found, int* rank, int* n_fallback) {
+    TRY(check_handle(c));
+    if (!net) return fail(c, DACP_ERR_ARG, "NULL network");
+    if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
+    if (n_fallback) *n_fallback = 0;
+    TRY(choose_impl(c, n_eigs, 2.0, 1.5, 0.0, 20, 256, net));
+    TRY(dacp_solve(c, n_eigs, window, eps, eigs, n_found, rank));
+    std::vector<int> redo;
+    for (int r = 0; r < c->R; ++r)
+        if (n_found[r] < n_eigs) redo.push_back(r);
+    if (n_fallback) *n_fallback = static_cast<int>(redo.size());
+    if (redo.empty()) return DACP_OK;
+    const int nr = static_cast<int>(redo.size()), b = c->b;
+    std::vector<int64_t> psi_off(c->R + 1, 0), j_off(c->R + 1, 0);
+    for (int r = 0; r < c->R; ++r) {
+        psi_off[r + 1] = psi_off[r] + (static_cast<int64_t>(1) << c->N[r]) * b;
+        j_off[r + 1] = j_off[r] + static_cast<int64_t>(c->N[r]) * c->N[r];
+    }
+    std::vector<int> ns;
+    std::vector<double> J, h, g, psi, jxx, jyy;
+    for (int r : redo) {
+        const int Nr = c->N[r];
+        ns.push_back(Nr);
+        for (int i = 0; i < Nr; ++i) {
+            h.push_back(c->h_h[static_cast<size_t>(r) * kMaxSpins + i]);
+            g.push_back(c->g_h[static_cast<size_t>(r) * kMaxSpins + i]);
+            for (int j = 0; j < Nr; ++j)
+                J.push_back(c->J_h[static_cast<size_t>(r) * kMaxSpins * kMaxSpins + i * kMaxSpins + j]);
+        }
+        psi.insert(psi.end(), c->psi0_h.begin() + psi_off[r], c->psi0_h.begin() + psi_off[r + 1]);
+        if (c->has_pairs) {
+            jxx.insert(jxx.end(), c->jxx_h.begin() + j_off[r], c->jxx_h.begin() + j_off[r + 1]);
+            jyy.insert(jyy.end(), c->jyy_h.begin() + j_off[r], c->jyy_h.begin() + j_off[r + 1]);
+        }
+    }
+    dacp_handle sub = nullptr;
+    dacp_status st = dacp_create(&sub, nr, ns.data(), J.data(), h.data(), g.data(), b, c->prec, psi.data(), c->st);
+    if (st != DACP_OK) return fail(c, st, "heuristic re-run: set-up failed");
+    std::vector<double> e2(static_cast<size_t>(nr) * n_eigs, 0.0);
+    std::vector<int> nf2(nr, 0), rk2(nr, 0);
+    if (c->has_pairs) st = dacp_set_pair_couplings(sub, jxx.data(), jyy.data());
+    if (st == DACP_OK) st = dacp_set_emax_rule(sub, c->emax_rule);
+    if (st == DACP_OK) st = dacp_choose_params(sub, n_eigs, 2.0, 1.5, 0.0, 20, 256);
+    if (st == DACP_OK) st = dacp_solve(sub, n_eigs, window, eps, e2.data(), nf2.data(), rk2.data());
+    if (st != DACP_OK) {
+        const std::string msg = dacp_last_error(sub);
+        dacp_destroy(sub);
+        return fail(c, st, "heuristic re-run: %s", msg.c_str());
+    }
+    c->launches += sub->launches.load();
+    dacp_destroy(sub);
+    for (int j = 0; j < nr; ++j) {
+        const int r = redo[j];
+        memcpy(eigs + static_cast<size_t>(r) * n_eigs, e2.data() + static_cast<size_t>(j) * n_eigs,
+               sizeof(double) * n_eigs);
+        n_found[r] = nf2[j];
+        if (rank) rank[r] = rk2[j];
+    }
+    return DACP_OK;
+}
+
 dacp_status dacp_get_moments(dacp_handle c, int r, double* mu, int64_t cap, int64_t* count) {
     TRY(check_handle(c));
     if (c->state < 3) return fail(c, DACP_ERR_STATE, "no moments yet");
@@ -1852,6 +1920,14 @@ dacp_status dacp_set_pair_couplings(dacp_handle c, const double* Jxx, const doub
     CK(cudaMemcpyAsync(c->pnorm_d, c->pnorm.data(), sizeof(double) * c->R, cudaMemcpyHostToDevice, c->st));
     CK(cudaStreamSynchronize(c->st));
     c->has_pairs = any;
+    c->jxx_h.clear();
+    c->jyy_h.clear();
+    if (any) {
+        c->jxx_h.assign(static_cast<size_t>(jo), 0.0);
+        c->jyy_h.assign(static_cast<size_t>(jo), 0.0);
+        if (Jxx) c->jxx_h.assign(Jxx, Jxx + jo);
+        if (Jyy) c->jyy_h.assign(Jyy, Jyy + jo);
+    }
     for (Graph* g : {&c->gf, &c->ge}) {          // captured launches hold the old arguments
         if (g->exec) cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;

@@ -153,3 +153,40 @@ def test_network_knobs_drive_the_parameters():
         d1.close()
         d2.close()
         P.dacp_mlp_destroy(m)
+
+
+def test_fallback_reruns_short_realizations_in_the_library():
+    """dacp_solve_learned: knobs that cannot return the requested count fall back to the heuristic.
+
+    The network's outputs are clamped to window ratio 1 and basis ratio 0.6 (dacp_mlp_set_output_range),
+    so b(2n+1) < n_eigs and every realization comes back short. The library must then re-run all of
+    them with the heuristic and return exactly what a heuristic run of the same batch returns."""
+    import math
+    models = [W.spin_glass_shard(10, seed=s) for s in (1, 2, 3)]
+    psis = [W.start_vectors(10, 4, seed=5, r=i) for i in range(3)]
+    n_eigs = 40
+    m = P.dacp_mlp_create(40, 64, 3, 3, seed=7)
+    try:
+        lo = np.array([math.log(1.0), 9.0, 0.6], np.float32)
+        P.dacp_mlp_set_output_range(m, lo, lo)
+        d = P.Dacp(models, psis, block_b=4, precision=P.DACP_DF32)
+        try:
+            d.choose_params_mlp(m, n_eigs)
+            assert all(4 * (2 * n + 1) < n_eigs for n in d.params()["n"])   # the learned basis is too small
+            eigs, nf, rank, nfb = d.solve(n_eigs, mlp=m)
+            p_fb = d.params()
+        finally:
+            d.close()
+    finally:
+        P.dacp_mlp_destroy(m)
+    assert nfb == 3
+    ref = P.Dacp(models, psis, block_b=4, precision=P.DACP_DF32)
+    try:
+        eref, nref, rref, nfb0 = ref.solve(n_eigs)
+    finally:
+        ref.close()
+    assert nfb0 == 0
+    for r in range(3):
+        assert nf[r] == nref[r] == n_eigs and rank[r] == rref[r]
+        assert np.array_equal(eigs[r], eref[r])
+    assert all(4 * (2 * n + 1) < n_eigs for n in p_fb["n"])     # the handle keeps the learned run's state
