@@ -229,6 +229,34 @@ dacp_status dacp_residuals(dacp_handle hd, int r, int n_eigs, double window, dou
 dacp_status dacp_eigenvectors(dacp_handle hd, int r, int n_eigs, double window, double eps, double* eigs,
                               double* phi_dev, int64_t ld, int* n_found);
 
+/*
+ * dacp_lanczos_filtered -- the comparison method of Appendix D on this
+ * library's kernels: the exp-semicircle filter combined with the Lanczos
+ * method. For realization r, with this handle's E_max, a and K: v_0 = column 0
+ * of its start vectors, normalised; v_{j+1} = the part of T_K(F) v_j
+ * (F = (H^2 - E_c)/E_0, one filter run of 2K H.v, Sec. II A) orthogonal to
+ * v_0 .. v_j (classical Gram-Schmidt twice, float64), normalised, until
+ * `steps` directions or a direction below 1e-8 of the filtered vector (1e-4
+ * for DACP_FP32: the filter's own rounding); then Rayleigh-Ritz of H in the
+ * space (V^T H V), the residual norms |H y - theta y| of its Ritz vectors,
+ * and of the Ritz values with residual <= res_tol * E_max (res_tol <= 0 ->
+ * 1e-8) the n_eigs of smallest |E| inside [-a, a], ascending.
+ * T_K(F) is even in E, so the space does not separate levels E and -E: the
+ * appendix's point that DACP is the more reliable route.
+ *   steps     Krylov dimension, 1 .. min(4096, 2^N_r).
+ *   eigs      host, n_eigs doubles; n_found the count written.
+ *   dim       may be NULL: the dimension reached.
+ *   ms        may be NULL, else 3 doubles: milliseconds of the filter runs,
+ *             of the reorthogonalisation, of the Rayleigh-Ritz step.
+ *   hv        may be NULL: H.v applied ((dim - 1) 2K + dim).
+ * Memory: four float64 D x steps matrices plus O(steps^2), allocated and freed
+ * here; the filter runs on a single-column handle of its own, on the same
+ * stream. Needs parameters (else DACP_ERR_STATE); DACP_ERR_ARG for a bad r,
+ * steps or n_eigs.
+ */
+dacp_status dacp_lanczos_filtered(dacp_handle hd, int r, int steps, int n_eigs, double res_tol, double* eigs,
+                                  int* n_found, int* dim, double* ms, int64_t* hv);
+
 /* dacp_get_filtered -- copy realization r's psi_E (2^N_r x b, float64) into
  * psi (capacity cap doubles). Test hook. */
 dacp_status dacp_get_filtered(dacp_handle hd, int r, double* psi, int64_t cap);

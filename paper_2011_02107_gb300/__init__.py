@@ -36,7 +36,8 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_mlp_get_launch_count", "dacp_mlp_last_error", "dacp_mlp_destroy", "dacp_choose_params_mlp",
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
            "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings",
-           "dacp_set_emax_rule", "dacp_test_emax_rule", "dacp_solve_learned"]
+           "dacp_set_emax_rule", "dacp_test_emax_rule", "dacp_solve_learned",
+           "dacp_lanczos_filtered"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -72,6 +73,7 @@ def _load():
         "dacp_residuals": [P, I, I, D, D, P, P, P],
         "dacp_solve": [P, I, D, D, P, P, P],
         "dacp_solve_learned": [P, P, I, D, D, P, P, P, P],
+        "dacp_lanczos_filtered": [P, I, I, I, D, P, P, P, P, ctypes.POINTER(L)],
         "dacp_eigenvectors": [P, I, I, D, D, P, P, L, P],
         "dacp_apply_h": [P, I, P, P],
         "dacp_set_pair_couplings": [P, P, P],
@@ -202,6 +204,18 @@ def dacp_solve_learned(hd, m, R, n_eigs, window=0.0, eps=0.0):
     _check(hd, _lib.dacp_solve_learned(hd, m, int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(nf),
                                        _ptr(rank), ctypes.byref(nfb)))
     return eigs.reshape(R, n_eigs), nf, rank, nfb.value
+
+
+def dacp_lanczos_filtered(hd, r, steps, n_eigs, res_tol=0.0):
+    """The Appendix D comparison method (see include/dacp.h). Returns (eigs, dim, ms[3], hv)."""
+    eigs = np.zeros(n_eigs)
+    nf = ctypes.c_int(0)
+    dim = ctypes.c_int(0)
+    ms = np.zeros(3)
+    hv = ctypes.c_int64(0)
+    _check(hd, _lib.dacp_lanczos_filtered(hd, int(r), int(steps), int(n_eigs), float(res_tol), _ptr(eigs),
+                                          ctypes.byref(nf), ctypes.byref(dim), _ptr(ms), ctypes.byref(hv)))
+    return eigs[:nf.value].copy(), dim.value, ms, hv.value
 
 
 def dacp_get_moments(hd, r, cap):

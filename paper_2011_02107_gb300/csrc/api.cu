@@ -1782,6 +1782,186 @@ dacp_status dacp_eigenvectors(dacp_handle c, int r, int n_eigs, double window, d
 }
 
 
+// The comparison method of Appendix D on this library's kernels: a Krylov
+// space of the filtered operator T_K(F) (each new direction one dacp_filter of
+// a single-column handle of realization r, then classical Gram-Schmidt twice
+// against all earlier directions with cuBLAS), Rayleigh-Ritz of H in it, and
+// the converged Ritz values.
+dacp_status dacp_lanczos_filtered(dacp_handle c, int r, int steps, int n_eigs, double res_tol, double* eigs,
+                                  int* n_found, int* dim_out, double* ms_out, int64_t* hv_out) {
+    TRY(check_handle(c));
+    if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_lanczos_filtered before parameters");
+    if (r < 0 || r >= c->R || n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad arguments");
+    const int N = c->N[r];
+    const int64_t D = static_cast<int64_t>(1) << N;
+    if (steps < 1 || steps > 4096 || steps > D) return fail(c, DACP_ERR_ARG, "steps must be in [1, min(4096, 2^N)]");
+    if (!(res_tol > 0.0)) res_tol = 1e-8;
+    // directions below this part of |A v_j| are the filter's own rounding, not Krylov directions
+    const double thr = c->fp32 ? 1e-4 : 1e-8;
+    const int b = c->b;
+    // the single-column handle: realization r's couplings, fields, pair terms and start column 0
+    std::vector<double> J(static_cast<size_t>(N) * N), hz(N), gx(N), v0(static_cast<size_t>(D));
+    for (int i = 0; i < N; ++i) {
+        hz[i] = c->h_h[static_cast<size_t>(r) * kMaxSpins + i];
+        gx[i] = c->g_h[static_cast<size_t>(r) * kMaxSpins + i];
+        for (int j = 0; j < N; ++j)
+            J[static_cast<size_t>(i) * N + j] = c->J_h[static_cast<size_t>(r) * kMaxSpins * kMaxSpins + i * kMaxSpins + j];
+    }
+    int64_t off = 0, joff = 0;
+    for (int q = 0; q < r; ++q) {
+        off += (static_cast<int64_t>(1) << c->N[q]) * b;
+        joff += static_cast<int64_t>(c->N[q]) * c->N[q];
+    }
+    double nrm0 = 0.0;
+    for (int64_t s2 = 0; s2 < D; ++s2) {
+        v0[s2] = c->psi0_h[off + s2 * b];
+        nrm0 += v0[s2] * v0[s2];
+    }
+    if (!(nrm0 > 0.0)) return fail(c, DACP_ERR_ARG, "start column 0 of realization %d is zero", r);
+    for (auto& x : v0) x /= sqrt(nrm0);
+    dacp_handle S = nullptr;
+    dacp_status st = dacp_create(&S, 1, &N, J.data(), hz.data(), gx.data(), 1, c->prec, v0.data(), c->st);
+    if (st != DACP_OK) return fail(c, st, "single-column handle: set-up failed");
+    double* V = nullptr;
+    double* HV = nullptr;
+    double* Y = nullptr;
+    double* HY = nullptr;
+    double* w = nullptr;
+    double* hbuf = nullptr;
+    double* Hm = nullptr;
+    double* Hs = nullptr;
+    double* lam = nullptr;
+    double* res = nullptr;
+    double* conv = nullptr;
+    double* sel = nullptr;
+    int* ints = nullptr;
+    void* xbuf = nullptr;
+    void* ybuf = nullptr;
+    void* work = nullptr;
+    auto run = [&]() -> dacp_status {
+        if (c->has_pairs) {
+            std::vector<double> jx(c->jxx_h.begin() + joff, c->jxx_h.begin() + joff + static_cast<int64_t>(N) * N);
+            std::vector<double> jy(c->jyy_h.begin() + joff, c->jyy_h.begin() + joff + static_cast<int64_t>(N) * N);
+            TRY(dacp_set_pair_couplings(S, jx.data(), jy.data()));
+        }
+        const int one = 1, K = c->K[r];
+        TRY(dacp_set_params(S, &c->emax[r], &c->a[r], &K, &one));
+        const int m = steps;
+        TRY(dalloc_t(c, &V, static_cast<size_t>(D) * m));
+        TRY(dalloc_t(c, &HV, static_cast<size_t>(D) * m));
+        TRY(dalloc_t(c, &w, static_cast<size_t>(D)));
+        TRY(dalloc_t(c, &hbuf, static_cast<size_t>(m)));
+        TRY(dalloc_t(c, &lam, static_cast<size_t>(m)));
+        TRY(dalloc_t(c, &res, static_cast<size_t>(m)));
+        TRY(dalloc_t(c, &conv, static_cast<size_t>(m)));
+        TRY(dalloc_t(c, &sel, static_cast<size_t>(n_eigs)));
+        TRY(dalloc_t(c, &ints, 2));
+        TRY(dalloc(c, &xbuf, static_cast<size_t>(D) * c->esz + 64));
+        TRY(dalloc(c, &ybuf, static_cast<size_t>(D) * c->esz + 64));
+        CK(cudaMemcpyAsync(V, v0.data(), sizeof(double) * D, cudaMemcpyHostToDevice, c->st));
+        const double one_d = 1.0, zero_d = 0.0, mone_d = -1.0;
+        double t_filter = 0.0, t_orth = 0.0;
+        int dim = 1;
+        for (int j = 0; j + 1 < m; ++j) {
+            // w = T_K(F) v_j / |T_K(F) v_j|
+            CK(launch_convert(c->prec, V + static_cast<int64_t>(j) * D, S->psi0_d, D, c->st));
+            TRY(dacp_filter(S));
+            t_filter += S->t_ms[0];
+            CK(cudaEventRecord(c->ev[2], c->st));
+            CK(launch_to_double(c->prec, S->psiE_d, w, D, 1, c->st));
+            c->launches += 2;
+            // classical Gram-Schmidt against v_0 .. v_j, twice
+            for (int pass = 0; pass < 2; ++pass) {
+                CKB(cublasDgemv(c->blas, CUBLAS_OP_T, static_cast<int>(D), j + 1, &one_d, V, static_cast<int>(D), w, 1,
+                                &zero_d, hbuf, 1));
+                CKB(cublasDgemv(c->blas, CUBLAS_OP_N, static_cast<int>(D), j + 1, &mone_d, V, static_cast<int>(D), hbuf, 1,
+                                &one_d, w, 1));
+            }
+            double nrm = 0.0;
+            CKB(cublasDnrm2(c->blas, static_cast<int>(D), w, 1, &nrm));
+            CK(cudaEventRecord(c->ev[3], c->st));
+            CK(cudaStreamSynchronize(c->st));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+            t_orth += ms;
+            if (!(nrm >= thr)) break;                 // the space is exhausted (or the filter broke)
+            const double inv = 1.0 / nrm;
+            CKB(cublasDscal(c->blas, static_cast<int>(D), &inv, w, 1));
+            CK(cudaMemcpyAsync(V + static_cast<int64_t>(j + 1) * D, w, sizeof(double) * D, cudaMemcpyDeviceToDevice,
+                               c->st));
+            ++dim;
+        }
+        // Rayleigh-Ritz of H in the space
+        CK(cudaEventRecord(c->ev[4], c->st));
+        for (int j = 0; j < dim; ++j) {
+            CK(launch_convert(c->prec, V + static_cast<int64_t>(j) * D, xbuf, D, c->st));
+            TRY(dacp_apply_h(S, 0, xbuf, ybuf));
+            CK(launch_to_double(c->prec, ybuf, HV + static_cast<int64_t>(j) * D, D, 1, c->st));
+            c->launches += 2;
+        }
+        TRY(dalloc_t(c, &Hm, static_cast<size_t>(dim) * dim));
+        TRY(dalloc_t(c, &Hs, static_cast<size_t>(dim) * dim));
+        TRY(dalloc_t(c, &Y, static_cast<size_t>(D) * dim));
+        TRY(dalloc_t(c, &HY, static_cast<size_t>(D) * dim));
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_T, CUBLAS_OP_N, dim, dim, static_cast<int>(D), &one_d, V, static_cast<int>(D),
+                        HV, static_cast<int>(D), &zero_d, Hm, dim));
+        const double half = 0.5;
+        CKB(cublasDgeam(c->blas, CUBLAS_OP_N, CUBLAS_OP_T, dim, dim, &half, Hm, dim, &half, Hm, dim, Hs, dim));
+        size_t dbytes = 0, hbytes = 0;
+        CKS(cusolverDnXsyevd_bufferSize(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, dim, CUDA_R_64F,
+                                        Hs, dim, CUDA_R_64F, lam, CUDA_R_64F, &dbytes, &hbytes));
+        TRY(dalloc(c, &work, dbytes + 64));
+        std::vector<char> work_h(hbytes + 64);
+        CKS(cusolverDnXsyevd(c->sol, c->sp, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, dim, CUDA_R_64F, Hs, dim,
+                             CUDA_R_64F, lam, CUDA_R_64F, work, dbytes, work_h.data(), hbytes, ints + 1));
+        // residuals of the Ritz pairs: |H V z - theta V z|
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, static_cast<int>(D), dim, dim, &one_d, V, static_cast<int>(D),
+                        Hs, dim, &zero_d, Y, static_cast<int>(D)));
+        CKB(cublasDgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, static_cast<int>(D), dim, dim, &one_d, HV,
+                        static_cast<int>(D), Hs, dim, &zero_d, HY, static_cast<int>(D)));
+        CK(launch_ritz_residual(HY, Y, lam, D, dim, res, c->st));
+        CK(launch_compact_converged(lam, res, dim, res_tol * c->emax[r], conv, ints, c->st));
+        int host_ints[2] = {0, 0};
+        CK(cudaMemcpyAsync(host_ints, ints, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (host_ints[1] != 0) return fail(c, DACP_ERR_NOT_CONVERGED, "Rayleigh-Ritz eigensolve: info %d", host_ints[1]);
+        CK(launch_select(conv, host_ints[0], n_eigs, c->a[r], sel, ints + 1, c->st));
+        c->launches += 3;
+        int nf = 0;
+        CK(cudaMemcpyAsync(&nf, ints + 1, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (nf > 0) {
+            CK(cudaMemcpyAsync(eigs, sel, sizeof(double) * nf, cudaMemcpyDeviceToHost, c->st));
+        }
+        CK(cudaEventRecord(c->ev[5], c->st));
+        CK(cudaStreamSynchronize(c->st));
+        float ms_rr = 0.f;
+        CK(cudaEventElapsedTime(&ms_rr, c->ev[4], c->ev[5]));
+        *n_found = nf;
+        if (dim_out) *dim_out = dim;
+        if (ms_out) {
+            ms_out[0] = t_filter;
+            ms_out[1] = t_orth;
+            ms_out[2] = ms_rr;
+        }
+        if (hv_out) *hv_out = static_cast<int64_t>(dim - 1) * 2 * K + dim;
+        c->launches += S->launches.load();
+        return DACP_OK;
+    };
+    dacp_status s2 = run();
+    for (void* p : {static_cast<void*>(V), static_cast<void*>(HV), static_cast<void*>(Y), static_cast<void*>(HY),
+                    static_cast<void*>(w), static_cast<void*>(hbuf), static_cast<void*>(Hm), static_cast<void*>(Hs),
+                    static_cast<void*>(lam), static_cast<void*>(res), static_cast<void*>(conv), static_cast<void*>(sel),
+                    static_cast<void*>(ints), xbuf, ybuf, work})
+        if (p) dfree(c, p);
+    if (s2 != DACP_OK && S) {
+        const std::string msg = dacp_last_error(S);
+        if (!msg.empty() && c->err.empty()) fail(c, s2, "single-column handle: %s", msg.c_str());
+    }
+    dacp_destroy(S);
+    return s2;
+}
+
 dacp_status dacp_apply_h(dacp_handle c, int r, const void* x_dev, void* y_dev) {
     TRY(check_handle(c));
     if (r < 0 || r >= c->R || !x_dev || !y_dev || x_dev == y_dev) return fail(c, DACP_ERR_ARG, "bad arguments");

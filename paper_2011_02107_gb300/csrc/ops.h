@@ -52,6 +52,10 @@ cudaError_t launch_residual(const double* Bsel, const double* W2, int M, int cou
 cudaError_t launch_pad_columns(double* V, int M, int64_t strideV, const int* m, int m_max, int count, cudaStream_t st);
 cudaError_t launch_pad_diagonal(double* Ht, int m_max, int64_t strideH, const int* m, const double* big, int count,
                                 cudaStream_t st);
+cudaError_t launch_ritz_residual(const double* HY, const double* Y, const double* th, int64_t D, int m, double* res,
+                                 cudaStream_t st);
+cudaError_t launch_compact_converged(const double* th, const double* res, int m, double tol, double* out, int* count,
+                                     cudaStream_t st);
 
 // params.cu
 cudaError_t launch_lanczos_orth(int prec, const Item* items, const RealInfo* real, int n_items, const void* v,

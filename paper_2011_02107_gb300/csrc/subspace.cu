@@ -264,4 +264,50 @@ cudaError_t launch_select(const double* lam, int m, int n_eigs, double w, double
     return cudaGetLastError();
 }
 
+// Residual norms |H y_j - theta_j y_j| of Ritz pairs, from HY = H V Z and Y = V Z (column-major,
+// columns of length D): one block per column, float64 sums reduced over the block.
+__global__ void ritz_residual_kernel(const double* __restrict__ HY, const double* __restrict__ Y,
+                                     const double* __restrict__ th, int64_t D, double* __restrict__ res) {
+    __shared__ double red[256 / 32];
+    const int j = blockIdx.x;
+    const double t = th[j];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < D; i += blockDim.x) {
+        const double d = HY[j * D + i] - t * Y[j * D + i];
+        s = fma(d, d, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 256 / 32; ++w) tot += red[w];
+        res[j] = sqrt(tot);
+    }
+}
+
+// The Ritz values whose residual is at most tol, in their (ascending) order.
+__global__ void compact_converged_kernel(const double* __restrict__ th, const double* __restrict__ res, int m,
+                                         double tol, double* __restrict__ out, int* __restrict__ count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int c = 0;
+    for (int j = 0; j < m; ++j)
+        if (res[j] <= tol) out[c++] = th[j];
+    *count = c;
+}
+
+cudaError_t launch_ritz_residual(const double* HY, const double* Y, const double* th, int64_t D, int m, double* res,
+                                 cudaStream_t st) {
+    if (m < 1) return cudaSuccess;
+    ritz_residual_kernel<<<m, 256, 0, st>>>(HY, Y, th, D, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_converged(const double* th, const double* res, int m, double tol, double* out, int* count,
+                                     cudaStream_t st) {
+    compact_converged_kernel<<<1, 32, 0, st>>>(th, res, m, tol, out, count);
+    return cudaGetLastError();
+}
+
 }  // namespace dacp
