@@ -320,12 +320,17 @@ dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);
  *                without forming them).
  * Both are times 1.001 and clamped to the Pauli 1-norm. Rule 1 runs about 1.14
  * times the spectral radius where rule 0 runs about 1.46 (measured against
- * dense spectra), and the filter and evolution lengths shrink in proportion.
- * It is a bound in practice, not in theory. A realization whose moments then
- * exceed mu_0 is reported as DACP_ERR_NUMERIC. The parameter network's
- * moment features are taken in units of E_max, so a network trained under
- * one rule sees shifted features under the other. Takes effect at the next
- * parameter choice. Errors: DACP_ERR_ARG for another rule.
+ * dense spectra). Under rule 1 the KPM moments, the network's features and
+ * the window a still come from rule 0's bound (so a network sees the features
+ * it was trained on); rule 1's bound becomes E_max of the two recurrences and
+ * K is rescaled to K * E_max1 / E_max0: the filter's growth inside the window
+ * (exp(2c sqrt(a^2 - E^2) / a), c = K a / E_max) and the basis orders' energy
+ * resolution do not depend on E_max, so the filter and evolution lengths
+ * shrink in proportion and nothing else changes. Rule 1 is a bound in
+ * practice, not in theory: a realization whose moments then exceed mu_0 is
+ * reported as DACP_ERR_NUMERIC, and dacp_solve_learned re-runs it under rule 0.
+ * Takes effect at the next parameter choice. Errors: DACP_ERR_ARG for another
+ * rule.
  */
 dacp_status dacp_set_emax_rule(dacp_handle hd, int rule);
 
@@ -446,7 +451,7 @@ dacp_status dacp_choose_params_mlp(dacp_handle hd, dacp_mlp m, int n_eigs, int l
  * moments), then dacp_solve; every realization that returns fewer than n_eigs
  * levels (n_found[r] < n_eigs, failures included) is run again with the
  * heuristic of dacp_choose_params (d_ratio 2, basis ratio 1.5, the precision's
- * filter constant, the handle's E_max rule) on a handle of its own, built from
+ * filter constant, E_max rule 0) on a handle of its own, built from
  * this handle's copies of its couplings, fields, pair couplings and start
  * vectors, on the same stream; its results replace the learned ones.
  *   net         a 40-input, 3-output network (dacp_mlp_create); not modified.

@@ -763,12 +763,13 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
     const int ni = static_cast<int>(c->items.size());
     const size_t sv = static_cast<size_t>(c->Dtot) * c->esz;   // one column
     void *v0 = nullptr, *v1 = nullptr, *v2 = nullptr, *kA = nullptr, *kB = nullptr;
-    double *lmom = nullptr, *beta2 = nullptr, *emax_d = nullptr, *a_d = nullptr, *kp = nullptr;
+    double *lmom = nullptr, *beta2 = nullptr, *emax_d = nullptr, *emax1_d = nullptr, *a_d = nullptr, *kp = nullptr;
     int *K_d = nullptr, *n_d = nullptr;
     float* knobs = nullptr;
     auto cleanup = [&]() {
         for (void* p : {v0, v1, v2, kA, kB, static_cast<void*>(lmom), static_cast<void*>(beta2),
-                        static_cast<void*>(emax_d), static_cast<void*>(a_d), static_cast<void*>(kp),
+                        static_cast<void*>(emax_d), static_cast<void*>(emax1_d), static_cast<void*>(a_d),
+                        static_cast<void*>(kp),
                         static_cast<void*>(K_d), static_cast<void*>(n_d), static_cast<void*>(knobs)})
             dfree(c, p);
     };
@@ -782,6 +783,7 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
         TRY(dalloc_t(c, &lmom, static_cast<size_t>(R) * rows));
         TRY(dalloc_t(c, &beta2, static_cast<size_t>(R) * steps));
         TRY(dalloc_t(c, &emax_d, R));
+        TRY(dalloc_t(c, &emax1_d, R));
         TRY(dalloc_t(c, &a_d, R));
         TRY(dalloc_t(c, &kp, static_cast<size_t>(R) * kpm_moments));
         TRY(dalloc_t(c, &K_d, R));
@@ -820,12 +822,17 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
             vc = w;
             w = t;
         }
-        CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax_d, c->emax_rule, c->st));
+        // the residual rule's bound normalises the KPM moments, the network's features and the window
+        // whatever the rule; rule 1's tighter bound only shortens the two recurrences (below)
+        CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax_d, 0, c->st));
+        if (c->emax_rule == 1)
+            CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax1_d, 1, c->st));
         // reset the apply coefficients of the test hook
         for (int r = 0; r < R; ++r) lc[8 * r + 1] = 0.0;
         CK(cudaMemcpyAsync(c->apply_coef_d, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice, c->st));
-        std::vector<double> em(R);
+        std::vector<double> em(R), em1(R);
         CK(cudaMemcpyAsync(em.data(), emax_d, R * 8, cudaMemcpyDeviceToHost, c->st));
+        if (c->emax_rule == 1) CK(cudaMemcpyAsync(em1.data(), emax1_d, R * 8, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
         // KPM moments of the normalised start vector under G = H / E_max
         TRY(set_evolution_coef(c, em));
@@ -851,6 +858,17 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
         CK(cudaMemcpyAsync(Kv.data(), K_d, R * 4, cudaMemcpyDeviceToHost, c->st));
         CK(cudaMemcpyAsync(nv.data(), n_d, R * 4, cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
+        if (c->emax_rule == 1) {
+            // K = c E_max / a: the filter's growth inside the window, exp(2c sqrt(a^2 - E^2) / a), and the
+            // basis orders' energy resolution pi E_max / (k_m a_r) do not depend on E_max, so the
+            // tighter bound keeps both and removes orders
+            for (int r = 0; r < R; ++r) {
+                if (!(em1[r] > 0.0) || !(em1[r] <= em[r]))
+                    return fail(c, DACP_ERR_NUMERIC, "E_max rule 1 failed for realization %d", r);
+                Kv[r] = static_cast<int>(ceil(static_cast<double>(Kv[r]) * em1[r] / em[r] - 1e-9));
+                em[r] = em1[r];
+            }
+        }
         for (int r = 0; r < R; ++r) {
             const double kn = floor(static_cast<double>(nv[r]) * M_PI / (av[r] / em[r]));
             if (!(av[r] > 0.0) || !(av[r] < em[r]) || kn > 2.0e8)
@@ -1495,7 +1513,7 @@ dacp_status dacp_solve_learned(dacp_handle c, dacp_mlp net, int n_eigs, double w
     std::vector<double> e2(static_cast<size_t>(nr) * n_eigs, 0.0);
     std::vector<int> nf2(nr, 0), rk2(nr, 0);
     if (c->has_pairs) st = dacp_set_pair_couplings(sub, jxx.data(), jyy.data());
-    if (st == DACP_OK) st = dacp_set_emax_rule(sub, c->emax_rule);
+    if (st == DACP_OK) st = dacp_set_emax_rule(sub, 0);      // the true bound: also recovers a rule-1 failure
     if (st == DACP_OK) st = dacp_choose_params(sub, n_eigs, 2.0, 1.5, 0.0, 20, 256);
     if (st == DACP_OK) st = dacp_solve(sub, n_eigs, window, eps, e2.data(), nf2.data(), rk2.data());
     if (st != DACP_OK) {

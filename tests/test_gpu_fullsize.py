@@ -1,8 +1,8 @@
 """Parity at the benchmark's full size (GPU).
 
 The configuration bench.py times: 256 spin-glass shards, N = 14, b = 4, 500 central levels each,
-double-float vectors, the tile size the autotuner picks, the learned parameters when their weights
-exist (heuristic otherwise), and dacp_solve. The CPU oracle cannot run the whole batch, so it checks
+double-float vectors, E_max by the Ritz-residual rule, the tile size the autotuner picks, the learned
+parameters when their weights exist (heuristic otherwise), and dacp_solve / dacp_solve_learned. The CPU oracle cannot run the whole batch, so it checks
 sampled outputs and properties that hold at any size:
 
   * one realization's filtered state against the oracle's filter, run with the GPU's parameters;
@@ -44,6 +44,7 @@ def batch():
         mlp = TM.load()
     d = P.Dacp(models, psis, block_b=B, precision=P.DACP_DF32)
     try:
+        d.set_emax_rule(1)
         d.choose_params(NE)
         d.autotune(64)
         eigs, nf, rank, nfb = d.solve(NE, mlp=mlp)

@@ -13,7 +13,11 @@ The learned run must keep every requested level within 1e-2 of the local
 mean spacing of the reference, and cost less than the heuristic run: at
 least 10 % less in the GB300 cost model (stencil value-orders + M^3 subspace
 term), and less in the measured T_F + T_E + T_D of the library's own CUDA
-events.
+events. At N = 16 (beyond the training range, 1000 levels) the evolution's
+k_n = n pi E_max / a hardly moves (the network narrows window and basis
+together; on 16 N = 18 shards with 2000 levels it ran 840838 orders against
+840152), so the gain there is in the filter and the solve: the learned run
+must still cost less in the model and in the measured path.
 """
 
 import os
@@ -54,7 +58,8 @@ def test_learned_parameters_keep_accuracy_and_cut_cost():
         pytest.skip("weights trained for another precision")
     mlp = TM.load(WEIGHTS)
     try:
-        for N, ne, seeds in ((12, 100, range(900_000, 900_006)), (13, 200, range(910_000, 910_004))):
+        for N, ne, seeds in ((12, 100, range(900_000, 900_006)), (13, 200, range(910_000, 910_004)),
+                             (16, 1000, range(920_000, 920_002))):
             models = [W.spin_glass_shard(N, seed=s) for s in seeds]
             psis = [W.start_vectors(N, 4, seed=77, r=i) for i in range(len(models))]
             ref, nf_ref, _, _, _ = _run(models, psis, P.DACP_FP64, ne, c_order=18.0)
@@ -68,7 +73,7 @@ def test_learned_parameters_keep_accuracy_and_cut_cost():
             cost_l = sum(TM.cost(N, 4, p_l, r) for r in range(len(models)))
             # the eligible knob settings all keep the basis ratio 1.5: the gain comes from the
             # window and the filter order (at most ~25 %)
-            assert cost_l < 0.9 * cost_h, (N, cost_l, cost_h)
+            assert cost_l < (0.9 if N < 16 else 1.0) * cost_h, (N, cost_l, cost_h)
             # whole measured path: the learned knobs keep the basis ratio (so T_E is alike) and
             # save in the filter and the subspace solve
             assert sum(ms_l) < sum(ms_h), (N, ms_l, ms_h)
