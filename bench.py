@@ -44,7 +44,8 @@ import workloads as W  # noqa: E402
 WORKLOADS = {
     "c3": dict(desc="256 spin-glass shards N=14 (dim 16384), Gamma~U[0.6,1.4], J~U[-1,1] all-to-all, "
                     "500 central eigenvalues each; batched double-float vectors (float32 pairs on the "
-                    "float32 pipes; plain float32 misses the 1e-2-spacing target) + fp64 moments/solve",
+                    "float32 pipes; plain float32 misses the 1e-2-spacing target) + fp64 moments/solve; "
+                    "solved as the two parity sectors (dim 8192) of each shard, levels merged",
                kind="sgs", N=14, R=256, n_eigs=500, b=4, prec="df32"),
     "c2": dict(desc="mixed-field Ising chain N=16 (dim 65536), 1000 central eigenvalues, plain fp64",
                kind="chain", N=16, R=1, n_eigs=1000, b=4, prec="fp64"),
@@ -56,7 +57,8 @@ WORKLOADS = {
                kind="chain", N=10, R=1, n_eigs=100, b=4, prec="fp64"),
     "c5": dict(desc="64 spin-glass shards N=18 (dim 262144), Gamma~U[0.6,1.4], J~U[-1,1] all-to-all, "
                     "2000 central eigenvalues each; parameters from the learned network with the heuristic "
-                    "as fallback; double-float vectors + fp64 moments/solve",
+                    "as fallback; double-float vectors + fp64 moments/solve; solved as the two parity "
+                    "sectors (dim 131072) of each shard, levels merged",
                kind="sgs", N=18, R=64, n_eigs=2000, b=4, prec="df32"),
 }
 METRIC = "central eigenvalues/s (batched FP32+FP64 moments vs plain FP64); H·v HBM GB/s"
@@ -73,10 +75,29 @@ def make_inputs(wl, rank=0):
     return models, psis
 
 
+# Levels asked of each parity sector when a model is solved as its two sectors: the two sectors
+# share the central levels about evenly, so 0.6 n_eigs each leaves a margin of 0.1 n_eigs per
+# sector (the merge returns fewer levels, never wrong ones, when a sector falls short).
+SECTOR_SHARE = 0.6
+
+
+def use_sectors(args, wl):
+    """The spin-glass shards have no z-fields: every term commutes with the global flip."""
+    if args.sectors == "auto":
+        return wl["kind"] == "sgs"
+    return args.sectors == "on"
+
+
+def sector_inputs(wl, rank=0):
+    return [p for r in range(wl["R"]) for p in W.sector_start_vectors(wl["N"], wl["b"], seed=rank, r=r)]
+
+
 # DRAM bytes (read + write) of one evolution launch of step_kernel_df4tb<kEvolve, 11> with all 256
 # realizations of the default workload active, from one ncu capture of the current kernel (the
 # profile summaries keep the command); other workloads report none.
-DF32_EVOLVE_TRAFFIC = 319758592 + 101683968
+DF32_EVOLVE_TRAFFIC = 319496192 + 102434304
+# the same for the launch over the 512 parity sectors (N - 1 = 13 spins) of that batch
+DF32_SECTOR_EVOLVE_TRAFFIC = 317191936 + 104094208
 DF32_TRAFFIC_SOURCE = "stored ncu capture of the current kernel, one launch, not re-measured in this run"
 # One error-free double-float multiply-add (the Dot2 step): TwoProduct 2,
 # TwoSum 6, and 4 float32 operations that fold the cross terms and the two
@@ -92,7 +113,7 @@ def sm_count():
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
-def roofline(wl, models, phase, bytes_evo, states_evo, clk, sms, launch_mode=0):
+def roofline(wl, n_real, phase, bytes_evo, states_evo, clk, sms, launch_mode=0, sectors=False):
     """Roofline of the evolution stencil over the timed steps.
 
     float32: HBM-bound; algorithmic bytes = 3 * 2^N * b * 4 per order (read
@@ -105,6 +126,8 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk, sms, launch_mode=0):
     lanes x the SM clock sampled during the run.
     float64: FP64-pipe bound; same multiply-add count against the measured
     float64 dgemm rate (1.10 TFLOP/s = 0.55 T FMA/s on this GB300).
+    sectors: the recurrences run on the parity sectors, N - 1 spins whose
+    N - 1 x-fields and one global flip make N flip terms per state.
     """
     peaks = {}
     try:
@@ -114,7 +137,7 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk, sms, launch_mode=0):
         pass
     t_e = phase[1] / 1e3
     b = wl["b"]
-    N = wl["N"]
+    N = wl["N"]                   # flip terms per state: N x-fields, or N - 1 and the global flip
     fma_per_state = N * b + 2 * b + b * (b + 1)
     df_ops_per_state = DF_FMA_OPS * (N * b + b + b * (b + 1)) + DF_SUB_OPS * b
     kern = {"fp32": "step_kernel<float,4,kEvolve>",
@@ -130,14 +153,15 @@ def roofline(wl, models, phase, bytes_evo, states_evo, clk, sms, launch_mode=0):
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "algorithmic": "3 * 2^N * b * 4 B per realization and order"}
     if wl["prec"] == "df32":
-        traffic = DF32_EVOLVE_TRAFFIC if (N, b, len(models)) == (14, 4, 256) else None
+        key = (N, b, n_real, bool(sectors))
+        traffic = {(14, 4, 256, False): DF32_EVOLVE_TRAFFIC, (14, 4, 512, True): DF32_SECTOR_EVOLVE_TRAFFIC}.get(key)
         mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
         peak = sms * FP32_LANES_PER_SM * mhz * 1e6 / 1e12            # T lane-ops/s
         achieved = states_evo * df_ops_per_state / t_e / 1e12 if t_e > 0 else None
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T float32 lane-ops/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one full evolution launch "
-                                 "(all 256 realizations active), " + DF32_TRAFFIC_SOURCE +
+                                 f"(all {n_real} realizations active), " + DF32_TRAFFIC_SOURCE +
                                  "; algorithmic 402.7 MB + 33.6 MB diagonal") if traffic else None,
                 "kernel": kern,
                 "peak_source": f"{sms} SMs x 128 float32 lanes x {mhz:.0f} MHz (sampled)",
@@ -390,17 +414,30 @@ def run_gpu(args, wl, rank, world):
                 mlp = train_mlp.load(stream=stream.cuda_stream)
 
     # ---- value: inputs resident on the device, K whole-path steps
-    d = P.Dacp(models, psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
+    sectors = use_sectors(args, wl)
+    if sectors:
+        # each shard as its two parity sectors (Z2: the global flip commutes with H when h = 0),
+        # built in the library; levels merged per shard (dacp_merge_sectors) inside the step
+        sec_psis = sector_inputs(wl, rank)
+        d = P.Dacp.parity_sectors(models, sec_psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
+        n_run = int(np.ceil(SECTOR_SHARE * n_eigs))
+    else:
+        d = P.Dacp(models, psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
+        n_run = n_eigs
     if args.emax_rule:
         d.set_emax_rule(args.emax_rule)
-    d.choose_params(n_eigs)
+    d.choose_params(n_run)
     tile_bytes = d.autotune(64)            # cached per (sizes, b, precision) for this process
     launch_mode = d.launch()[0]            # 0 graph replay, 1 persistent, 2 staged tiles (float32)
     fallbacks = [0]
+    short = [0]
 
     def step():
-        eigs, nf, rank, nfb = d.solve(n_eigs, mlp=mlp)
+        eigs, nf, rank, nfb = d.solve(n_run, mlp=mlp)
         fallbacks[0] += nfb
+        if sectors:
+            eigs, nf = P.merge_sector_levels(eigs, nf, n_eigs)
+            short[0] += int(np.sum(np.asarray(nf) < n_eigs))
         return eigs, nf, rank
 
     for _ in range(args.warmup):
@@ -423,9 +460,9 @@ def run_gpu(args, wl, rank, world):
         phase += d.timings()
         p = d.params()
         esz = 4 if wl["prec"] == "fp32" else 8           # df32 pairs are 8 bytes
-        # the evolution runs k_n + 2 orders (mu up to 2 k_n + 3)
-        bytes_evo += sum(3.0 * (int(p["kn"][r]) + 2) * (1 << models[r]["N"]) * wl["b"] * esz for r in range(R))
-        states_evo += sum((int(p["kn"][r]) + 2) * float(1 << models[r]["N"]) for r in range(R))
+        # the evolution runs k_n + 2 orders (mu up to 2 k_n + 3) on each of the handle's realizations
+        bytes_evo += sum(3.0 * (int(p["kn"][r]) + 2) * (1 << d.N[r]) * wl["b"] * esz for r in range(d.R))
+        states_evo += sum((int(p["kn"][r]) + 2) * float(1 << d.N[r]) for r in range(d.R))
     ev1.record(stream)
     torch.cuda.synchronize()
     dist_barrier()
@@ -442,16 +479,16 @@ def run_gpu(args, wl, rank, world):
     # 1e-7 E_max the moment form reaches its float64 floor
     residual_check = None
     if not args.no_accuracy_check and R > 0:
-        rs = sorted({0, R // 2, R - 1})
+        rs = sorted({0, d.R // 2, d.R - 1})
         worst, flagged, total = 0.0, 0, 0
         for r in rs:
-            _, res, nfr = d.residuals(r, n_eigs)
+            _, res, nfr = d.residuals(r, n_run)
             if nfr > 0:
                 em = float(params["emax"][r])
                 worst = max(worst, float(np.max(res)) / em)
                 flagged += int(np.sum(res > 1e-5 * em))
                 total += int(nfr)
-        residual_check = {"realizations": rs, "levels": total, "max_residual_over_emax": worst,
+        residual_check = {"realizations": rs, "sectors": sectors, "levels": total, "max_residual_over_emax": worst,
                           "levels_with_residual_above_1e-5_emax": flagged,
                           "note": "moment-form residual norms |H y - E y| of the returned levels (float64 floor "
                                   "about 1e-7 E_max)"}
@@ -515,30 +552,36 @@ def run_gpu(args, wl, rank, world):
 
     # ---- e2e: public API from pinned host buffers, H2D and D2H inside the timed region
     n_spins, J, h, g = W.pack_models(models)
-    psi_flat = np.concatenate([p.ravel() for p in psis])
+    psi_flat = np.concatenate([p.ravel() for p in (sec_psis if sectors else psis)])
     pin = torch.empty(psi_flat.size, dtype=torch.float64, pin_memory=True)
     pin.numpy()[:] = psi_flat
     psi_pinned = pin.numpy()
     h2d = psi_pinned.nbytes + J.nbytes + h.nbytes + g.nbytes + n_spins.nbytes
-    d2h = R * n_eigs * 8 + 2 * R * 4
+    R_run = 2 * R if sectors else R
+    d2h = R_run * n_run * 8 + 2 * R_run * 4
     e2e_steps = max(0, min(args.steps, args.e2e_steps))
     dist_barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     found_e2e = 0
     for _ in range(e2e_steps):
-        hd = P.dacp_create(n_spins, J, h, g, wl["b"], prec, psi_pinned, stream.cuda_stream)
+        if sectors:
+            hd = P.dacp_create_parity_sectors(n_spins, J, h, g, wl["b"], prec, psi_pinned, stream.cuda_stream)
+        else:
+            hd = P.dacp_create(n_spins, J, h, g, wl["b"], prec, psi_pinned, stream.cuda_stream)
         try:
-            P.dacp_choose_params(hd, n_eigs)
+            P.dacp_choose_params(hd, n_run)
             P.dacp_autotune(hd)            # cached: only switches the tile size
             if args.emax_rule:
                 P.dacp_set_emax_rule(hd, args.emax_rule)
             if mlp is not None:           # learned parameters, heuristic re-run in the library
-                eigs, nf, rk, _ = P.dacp_solve_learned(hd, mlp, R, n_eigs)
+                eigs, nf, rk, _ = P.dacp_solve_learned(hd, mlp, R_run, n_run)
             else:
                 if args.emax_rule:
-                    P.dacp_choose_params(hd, n_eigs)
-                eigs, nf, rk = P.dacp_solve(hd, R, n_eigs)
+                    P.dacp_choose_params(hd, n_run)
+                eigs, nf, rk = P.dacp_solve(hd, R_run, n_run)
+            if sectors:
+                eigs, nf = P.dacp_merge_sectors(eigs, nf, n_eigs)
             found_e2e += int(np.clip(nf, 0, None).sum())
         finally:
             P.dacp_destroy(hd)
@@ -550,7 +593,7 @@ def run_gpu(args, wl, rank, world):
         P.dacp_mlp_destroy(mlp)
 
     # ---- roofline of the dominant kernel (evolution stencil), per vector precision
-    roof = roofline(wl, models, phase, bytes_evo, states_evo, clk, sm_count(), launch_mode)
+    roof = roofline(wl, d.R, phase, bytes_evo, states_evo, clk, sm_count(), launch_mode, sectors)
     # H.v HBM bandwidth of the evolution (algorithmic bytes: read w_k, read w_{k-1},
     # write w_{k+1}) against the measured copy bandwidth, for every precision
     try:
@@ -564,7 +607,7 @@ def run_gpu(args, wl, rank, world):
            "bytes": "3 * 2^N * b * value size per realization and order, over T_E",
            "bound_here": roof["bound"]}
     esz = 4 if wl["prec"] == "fp32" else 8
-    ws = 3 * sum((1 << m["N"]) * wl["b"] * esz for m in models)
+    ws = 3 * sum((1 << m["N"]) * wl["b"] * esz for m in models)      # the two sectors hold as many states
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     l2_note = (f"inputs larger than L2: the evolution's working set (w_k, w_(k-1), w_(k+1)) is "
                f"{ws / 2**20:.0f} MiB against the {l2 / 2**20:.0f} MiB L2 ({ws / l2:.1f}x)")
@@ -579,7 +622,10 @@ def run_gpu(args, wl, rank, world):
                    "parallelism": f"independent realizations, {world} GPU(s)",
                    "emax_mean": float(np.mean(params["emax"])), "a_mean": float(np.mean(params["a"])),
                    "K_max": int(params["K"].max()), "kn_max": int(params["kn"].max()),
-                   "n": int(params["n"].max()), "emax_rule": args.emax_rule},
+                   "n": int(params["n"].max()), "emax_rule": args.emax_rule,
+                   "symmetry": (f"Z2 parity sectors: {d.R} realizations of N-1={wl['N'] - 1} spins (h = 0, so "
+                                f"the global flip X_0...X_(N-1) commutes with H), {n_run} levels asked of each, "
+                                f"merged to the {n_eigs} nearest E = 0 per shard") if sectors else None},
         "eigenvalues_found_per_step": found_all / args.steps,
         "phase_ms_per_step": {"T_F": phase[0] / args.steps, "T_E": phase[1] / args.steps,
                               "T_D": phase[2] / args.steps,
@@ -595,6 +641,7 @@ def run_gpu(args, wl, rank, world):
         "residual_check": residual_check,
         "fp64_same_gpu": fp64_arm,
         "fallback_realizations": fallbacks[0],
+        "sector_merges_short": short[0] if sectors else None,
         "tile_bytes": tile_bytes,
         "launch_mode": launch_mode,
         "roofline": roof,
@@ -630,6 +677,9 @@ def main():
                          "practice that shortens both recurrences (KPM window and learned features stay on "
                          "rule 0's bound; the fallback re-runs a realization whose moments exceed mu_0 under "
                          "rule 0); 0 the Ritz value + residual norm, a bound in theory")
+    ap.add_argument("--sectors", default="auto", choices=["auto", "on", "off"],
+                    help="solve each realization as its two parity sectors (auto: for the spin-glass shards, "
+                         "which have no z-fields)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-rank", type=int, default=0, help=argparse.SUPPRESS)

@@ -100,6 +100,64 @@ dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins,
 dacp_status dacp_set_pair_couplings(dacp_handle hd, const double* Jxx, const double* Jyy);
 
 /*
+ * dacp_set_global_flips -- add c_r X_0 X_1 ... X_{N_r - 1} (every spin of the
+ * realization flipped at once) to realization r's H. It is the term that the
+ * parity-sector reduction below leaves in each sector, and a model term in its
+ * own right.
+ *   coef  n_real doubles (copied; the caller keeps ownership), NULL or all
+ *         zero removes the term.
+ * Every stencil pass reads the partner s XOR (2^N - 1) (global memory, or the
+ * tile when the realization is one tile). The Pauli 1-norm that clamps the
+ * E_max bound grows by |c_r|. Parameters and results are reset (as after
+ * dacp_create). Errors: DACP_ERR_ARG for a non-finite coefficient;
+ * DACP_ERR_NOMEM, DACP_ERR_CUDA.
+ */
+dacp_status dacp_set_global_flips(dacp_handle hd, const double* coef);
+
+/*
+ * dacp_create_parity_sectors -- a handle whose realizations are the two parity
+ * sectors of each input realization. The paper's models without z-fields
+ * (Sec. III; the spin-glass shards) commute with P = X_0 X_1 ... X_{N-1}, so H
+ * splits into the sectors P = +1 and -1 of 2^(N-1) states each, whose levels
+ * together are H's levels. In the basis (|s> + sigma |s XOR (2^N - 1)>) / sqrt 2
+ * (s with bit N-1 clear) sector sigma is the (N-1)-spin model
+ *     sum_{i<j<N-1} J_ij Z_i Z_j + sum_{i<N-1} J_{i,N-1} Z_i
+ *       + sum_{i<N-1} Gamma_i X_i + sigma Gamma_{N-1} X_0 ... X_{N-2}
+ * (z-fields from the couplings to spin N-1, a global flip from its x-field).
+ * Each sector holds half the levels at half the density: for the same number
+ * of central levels a sector needs half the evolution orders on half-size
+ * vectors and a basis of half the size.
+ *   n_real, n_spins (2 .. 26), J, gamma, block_b, precision, stream: as
+ *            dacp_create for the full models; h must be all zero
+ *            (DACP_ERR_ARG otherwise).
+ *   psi0     start vectors of the 2 n_real sector realizations: realization
+ *            2r is sector +1 of input r, 2r+1 sector -1, each 2^(N_r - 1) x b
+ *            float64, [state][column], concatenated in that order.
+ * The result is an ordinary handle of 2 n_real realizations of N_r - 1 spins;
+ * dacp_merge_sectors turns their levels back into the inputs' levels.
+ */
+dacp_status dacp_create_parity_sectors(dacp_handle* out, int n_real, const int* n_spins, const double* J,
+                                       const double* h, const double* gamma, int block_b, int precision,
+                                       const double* psi0, void* stream);
+
+/*
+ * dacp_merge_sectors -- host arithmetic only: the levels of n_real
+ * realizations from those of their two sectors (realizations 2r and 2r+1 of a
+ * dacp_create_parity_sectors handle). Each sector returned the levels of
+ * smallest |E| it has, so the union holds every level up to the smaller of
+ * the two sectors' largest |E|; of those, the n_eigs of smallest |E| come back,
+ * ascending.
+ *   eigs_in, n_found_in  the sectors' results, [2 n_real][n_in] and [2 n_real],
+ *                        as dacp_central_eigs / dacp_solve write them.
+ *   eigs, n_found        [n_real][n_eigs] and [n_real]: n_found[r] < n_eigs
+ *                        when the union cannot vouch for n_eigs levels (ask the
+ *                        sectors for more); a failed sector's -status passes on.
+ * Errors: DACP_ERR_ARG for bad sizes or NULL.
+ */
+dacp_status dacp_merge_sectors(int n_real, int n_in, const double* eigs_in, const int* n_found_in, int n_eigs,
+                               double* eigs, int* n_found);
+
+/*
  * dacp_set_params -- explicit per-realization parameters (arrays of n_real).
  *   emax  bound on |E| (E_min = -E_max, Sec. II A); must be a true bound.
  *   a     window half-width, 0 < a < emax (Sec. II A).

@@ -8,6 +8,10 @@ with Y|b> = i z(b) |b XOR 1>, the pair Y_i Y_j carries -z_i(s) z_j(s), which is
 real, so every such H stays a real symmetric matrix (XXZ and Heisenberg chains,
 the paper's native sigma^x sigma^x couplings of Sec. III without rotation).
 
+A model may also carry ``gflip`` (a number c): + c X_0 X_1 ... X_{N-1}, every
+spin flipped at once. That is the term a parity sector keeps of the x-field of
+the spin it removes (parity_sector_models below).
+
 The paper works in matrix-free mode (Sec. II intro): H is a function taking a
 state to a state, each Pauli term "represented by a specific function"
 (Sec. III). ``apply_h`` is that function written out term by term.
@@ -69,6 +73,9 @@ def apply_h(model, x: np.ndarray, diag: np.ndarray | None = None) -> np.ndarray:
                 zz = (1.0 - 2.0 * ((s >> i) & 1)) * (1.0 - 2.0 * ((s >> j) & 1))
                 c = Jxx[i, j] - Jyy[i, j] * zz
                 y = y + (c if x.ndim == 1 else c[:, None]) * x[s ^ ((1 << i) | (1 << j))]
+    gf = float(model.get("gflip", 0.0))
+    if gf != 0.0:
+        y = y + gf * x[s ^ (D - 1)]
     return y
 
 
@@ -101,6 +108,11 @@ def apply_h_rows(model, x: np.ndarray, states, with_abs: bool = False):
                 t = (c if x.ndim == 1 else c[:, None]) * x[st ^ ((1 << i) | (1 << j))]
                 y = y + t
                 a = a + np.abs(t)
+    gf = float(model.get("gflip", 0.0))
+    if gf != 0.0:
+        t = gf * x[st ^ ((1 << N) - 1)]
+        y = y + t
+        a = a + np.abs(t)
     return (y, a) if with_abs else y
 
 
@@ -145,6 +157,9 @@ def dense_h(model) -> np.ndarray:
                 yy = _site_op(N, {i: _Y, j: _Y})          # complex Kronecker product
                 assert np.abs(yy.imag).max() == 0.0
                 H += Jyy[i, j] * yy.real
+    gf = float(model.get("gflip", 0.0))
+    if gf != 0.0:
+        H += gf * _site_op(N, {i: _X for i in range(N)})
     return H
 
 
@@ -154,7 +169,8 @@ def pauli_norm_bound(model) -> float:
     iu = np.triu_indices(N, 1)
     Jxx, Jyy = pair_couplings(model)
     return float(np.abs(model["J"][iu]).sum() + np.abs(model["h"]).sum()
-                 + np.abs(model["gamma"]).sum() + np.abs(Jxx).sum() + np.abs(Jyy).sum())
+                 + np.abs(model["gamma"]).sum() + np.abs(Jxx).sum() + np.abs(Jyy).sum()
+                 + abs(float(model.get("gflip", 0.0))))
 
 
 def trace_h2_per_state(model) -> float:
@@ -163,7 +179,8 @@ def trace_h2_per_state(model) -> float:
     iu = np.triu_indices(N, 1)
     Jxx, Jyy = pair_couplings(model)
     return float((model["J"][iu] ** 2).sum() + (model["h"] ** 2).sum()
-                 + (model["gamma"] ** 2).sum() + (Jxx ** 2).sum() + (Jyy ** 2).sum())
+                 + (model["gamma"] ** 2).sum() + (Jxx ** 2).sum() + (Jyy ** 2).sum()
+                 + float(model.get("gflip", 0.0)) ** 2)
 
 
 def bit_reverse(N: int) -> np.ndarray:
@@ -224,3 +241,31 @@ def reflection_sector_matrices(model, chunk: int = 1024):
             Hs[nf:, c0:c1] += sign * w[nf:, None] * Wc[b[nf:]]
         out.append(Hs)
     return out[0], out[1]
+
+
+def parity_sector_models(model):
+    """The two parity sectors of a model without z-fields, as (N-1)-spin models (sigma = +1, -1).
+
+    With h = 0 (and no pair terms) every term of H commutes with P = X_0 ... X_{N-1}: Z_i Z_j
+    because P flips both signs, X_i trivially. Take as basis of sector sigma the states
+    (e_s + sigma e_{s XOR (2^N - 1)}) / sqrt 2 with bit N-1 of s clear, labelled by s's lower
+    N-1 bits. On them z_{N-1} = +1, so Z_i Z_{N-1} acts as Z_i; X_i (i < N-1) maps label s to
+    s XOR 2^i; X_{N-1} maps e_s to e_{s XOR 2^(N-1)} = the partner of label s XOR (2^(N-1) - 1),
+    i.e. sigma times that basis state. Hence sector sigma is: J_ij for i < j < N-1, z-fields
+    h_i = J_{i,N-1}, x-fields Gamma_i (i < N-1) and gflip = sigma Gamma_{N-1}.
+    """
+    N = model["N"]
+    if N < 2:
+        raise ValueError("a parity sector needs N >= 2")
+    if np.any(np.asarray(model["h"]) != 0.0):
+        raise ValueError("z-fields break the parity symmetry")
+    Jxx, Jyy = pair_couplings(model)
+    if np.any(Jxx != 0.0) or np.any(Jyy != 0.0) or float(model.get("gflip", 0.0)) != 0.0:
+        raise ValueError("only zz couplings and x-fields")
+    J = np.triu(np.asarray(model["J"], dtype=np.float64), 1)
+    out = []
+    for sigma in (1.0, -1.0):
+        out.append({"N": N - 1, "J": J[:N - 1, :N - 1].copy(), "h": J[:N - 1, N - 1].copy(),
+                    "gamma": np.asarray(model["gamma"], dtype=np.float64)[:N - 1].copy(),
+                    "gflip": sigma * float(model["gamma"][N - 1])})
+    return out

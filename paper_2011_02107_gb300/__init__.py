@@ -37,7 +37,8 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_get_features", "dacp_autotune", "dacp_set_launch", "dacp_get_launch",
            "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings",
            "dacp_set_emax_rule", "dacp_test_emax_rule", "dacp_solve_learned",
-           "dacp_lanczos_filtered"]
+           "dacp_lanczos_filtered", "dacp_set_global_flips", "dacp_create_parity_sectors",
+           "dacp_merge_sectors"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -74,6 +75,9 @@ def _load():
         "dacp_solve": [P, I, D, D, P, P, P],
         "dacp_solve_learned": [P, P, I, D, D, P, P, P, P],
         "dacp_lanczos_filtered": [P, I, I, I, D, P, P, P, P, ctypes.POINTER(L)],
+        "dacp_set_global_flips": [P, P],
+        "dacp_create_parity_sectors": [ctypes.POINTER(P), I, P, P, P, P, I, I, P, P],
+        "dacp_merge_sectors": [I, I, P, P, I, P, P],
         "dacp_eigenvectors": [P, I, I, D, D, P, P, L, P],
         "dacp_apply_h": [P, I, P, P],
         "dacp_set_pair_couplings": [P, P, P],
@@ -216,6 +220,48 @@ def dacp_lanczos_filtered(hd, r, steps, n_eigs, res_tol=0.0):
     _check(hd, _lib.dacp_lanczos_filtered(hd, int(r), int(steps), int(n_eigs), float(res_tol), _ptr(eigs),
                                           ctypes.byref(nf), ctypes.byref(dim), _ptr(ms), ctypes.byref(hv)))
     return eigs[:nf.value].copy(), dim.value, ms, hv.value
+
+
+def dacp_set_global_flips(hd, coef):
+    coef = None if coef is None else np.ascontiguousarray(coef, dtype=np.float64)
+    _check(hd, _lib.dacp_set_global_flips(hd, _ptr(coef) if coef is not None else None))
+
+
+def dacp_create_parity_sectors(n_spins, J, h, gamma, block_b, precision, psi0, stream=None):
+    n_spins = np.ascontiguousarray(n_spins, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    psi0 = np.ascontiguousarray(psi0, dtype=np.float64)
+    out = ctypes.c_void_p()
+    st = _lib.dacp_create_parity_sectors(ctypes.byref(out), len(n_spins), _ptr(n_spins), _ptr(J), _ptr(h), _ptr(gamma),
+                                         int(block_b), int(precision), _ptr(psi0),
+                                         ctypes.c_void_p(stream) if stream else None)
+    _check(None, st)
+    return out.value
+
+
+def dacp_merge_sectors(eigs_in, n_found_in, n_eigs):
+    """eigs_in [2 R, n_in], n_found_in [2 R] -> (eigs [R, n_eigs], n_found [R])."""
+    eigs_in = np.ascontiguousarray(eigs_in, dtype=np.float64)
+    n_found_in = np.ascontiguousarray(n_found_in, dtype=np.int32)
+    R = len(n_found_in) // 2
+    eigs = np.zeros(R * n_eigs)
+    nf = np.zeros(R, dtype=np.int32)
+    _check(None, _lib.dacp_merge_sectors(R, eigs_in.shape[1], _ptr(eigs_in), _ptr(n_found_in), int(n_eigs), _ptr(eigs),
+                                         _ptr(nf)))
+    return eigs.reshape(R, n_eigs), nf
+
+
+def merge_sector_levels(eigs, n_found, n_eigs):
+    """dacp_merge_sectors over per-realization level lists (as Dacp.run returns them): sector
+    lists 2 r, 2 r + 1 -> the n_eigs central levels of model r. Returns (list, n_found)."""
+    n_in = max(1, max((len(e) for e in eigs), default=1))
+    buf = np.zeros((len(eigs), n_in))
+    for i, e in enumerate(eigs):
+        buf[i, :len(e)] = e
+    out, nf = dacp_merge_sectors(buf, n_found, n_eigs)
+    return [out[r, :max(nf[r], 0)].copy() for r in range(len(nf))], nf
 
 
 def dacp_get_moments(hd, r, cap):
@@ -428,6 +474,14 @@ def dacp_get_features(hd, R):
 
 # ---- convenience wrapper ---------------------------------------------------
 
+def _pack(models):
+    n_spins = np.array([m["N"] for m in models], dtype=np.int32)
+    J = np.concatenate([np.asarray(m["J"], dtype=np.float64).ravel() for m in models])
+    h = np.concatenate([np.asarray(m["h"], dtype=np.float64) for m in models])
+    g = np.concatenate([np.asarray(m["gamma"], dtype=np.float64) for m in models])
+    return n_spins, J, h, g
+
+
 class Dacp:
     """One handle over a batch of realizations (models from ``workloads``)."""
 
@@ -456,6 +510,30 @@ class Dacp:
             except Exception:
                 dacp_destroy(self.handle)
                 raise
+        if any(float(m.get("gflip", 0.0)) != 0.0 for m in self.models):
+            try:
+                dacp_set_global_flips(self.handle, [float(m.get("gflip", 0.0)) for m in self.models])
+            except Exception:
+                dacp_destroy(self.handle)
+                raise
+
+    @classmethod
+    def parity_sectors(cls, models, psi0_sectors, block_b=4, precision=DACP_FP64, stream=None):
+        """A handle whose realizations 2r, 2r+1 are the parity sectors +1, -1 of models[r] (no
+        z-fields; dacp_create_parity_sectors builds them in the library). psi0_sectors: 2 R start
+        blocks of shape (2^(N_r - 1), b), in that order."""
+        n_spins, J, h, g = _pack(models)
+        psi0 = np.concatenate([np.ascontiguousarray(p, dtype=np.float64).ravel() for p in psi0_sectors])
+        self = cls.__new__(cls)
+        self.models = list(models)
+        self.R = 2 * len(models)
+        self.b = int(block_b)
+        self.N = [m["N"] - 1 for m in models for _ in range(2)]
+        self.precision = precision
+        self.stream = stream
+        self.psi0_list = [np.ascontiguousarray(p, dtype=np.float64) for p in psi0_sectors]
+        self.handle = dacp_create_parity_sectors(n_spins, J, h, g, block_b, precision, psi0, stream)
+        return self
 
     def set_params(self, emax, a, K, n):
         R = self.R

@@ -92,6 +92,10 @@ struct dacp_ctx {
     std::vector<double> pnorm0;         // the same without the pair couplings
     bool has_pairs = false;             // dacp_set_pair_couplings gave nonzero XX / YY terms
     std::vector<double> jxx_h, jyy_h;   // the caller's pair couplings (packed as given), for re-runs
+    std::vector<double> pnorm_pairs;    // sum |Jxx| + |Jyy| of each realization
+    std::vector<double> gflip_h;        // coefficient of the global flip X_0 ... X_{N-1} per realization
+    bool has_gflip = false;
+    double* gflip_d = nullptr;          // [R]
     std::vector<double> psi0_h;         // the caller's start vectors (packed float64), for re-runs
     int* n_pairs_d = nullptr;           // [R]
     int* pair_ij_d = nullptr;           // [R][kMaxPairs]
@@ -309,6 +313,7 @@ StepArgs base_args(dacp_ctx* c) {
         a.pair_ij = c->pair_ij_d;
         a.pair_c = c->pair_c_d;
     }
+    if (c->has_gflip) a.gflip = c->gflip_d;
     return a;
 }
 
@@ -1513,6 +1518,11 @@ dacp_status dacp_solve_learned(dacp_handle c, dacp_mlp net, int n_eigs, double w
     std::vector<double> e2(static_cast<size_t>(nr) * n_eigs, 0.0);
     std::vector<int> nf2(nr, 0), rk2(nr, 0);
     if (c->has_pairs) st = dacp_set_pair_couplings(sub, jxx.data(), jyy.data());
+    if (st == DACP_OK && c->has_gflip) {
+        std::vector<double> gsub;
+        for (int r : redo) gsub.push_back(c->gflip_h[r]);
+        st = dacp_set_global_flips(sub, gsub.data());
+    }
     if (st == DACP_OK) st = dacp_set_emax_rule(sub, 0);      // the true bound: also recovers a rule-1 failure
     if (st == DACP_OK) st = dacp_choose_params(sub, n_eigs, 2.0, 1.5, 0.0, 20, 256);
     if (st == DACP_OK) st = dacp_solve(sub, n_eigs, window, eps, e2.data(), nf2.data(), rk2.data());
@@ -1862,6 +1872,7 @@ dacp_status dacp_lanczos_filtered(dacp_handle c, int r, int steps, int n_eigs, d
             std::vector<double> jy(c->jyy_h.begin() + joff, c->jyy_h.begin() + joff + static_cast<int64_t>(N) * N);
             TRY(dacp_set_pair_couplings(S, jx.data(), jy.data()));
         }
+        if (c->has_gflip) TRY(dacp_set_global_flips(S, &c->gflip_h[r]));
         const int one = 1, K = c->K[r];
         TRY(dacp_set_params(S, &c->emax[r], &c->a[r], &K, &one));
         const int m = steps;
@@ -2084,7 +2095,7 @@ dacp_status dacp_set_pair_couplings(dacp_handle c, const double* Jxx, const doub
     TRY(check_handle(c));
     std::vector<int> np(c->R, 0), ij(static_cast<size_t>(c->R) * kMaxPairs, 0);
     std::vector<double> cf(static_cast<size_t>(c->R) * kMaxPairs * 2, 0.0);
-    std::vector<double> pn = c->pnorm0;
+    std::vector<double> pn(c->R, 0.0);
     int64_t jo = 0;
     for (int r = 0; r < c->R; ++r) {
         const int Nr = c->N[r];
@@ -2102,6 +2113,9 @@ dacp_status dacp_set_pair_couplings(dacp_handle c, const double* Jxx, const doub
             }
         jo += static_cast<int64_t>(Nr) * Nr;
     }
+    c->pnorm_pairs = pn;
+    for (int r = 0; r < c->R; ++r)
+        pn[r] += c->pnorm0[r] + (c->has_gflip ? fabs(c->gflip_h[r]) : 0.0);
     bool any = false;
     for (int r = 0; r < c->R; ++r) any = any || np[r] > 0;
     if (any && !c->n_pairs_d) {
@@ -2131,6 +2145,109 @@ dacp_status dacp_set_pair_couplings(dacp_handle c, const double* Jxx, const doub
         g->exec = nullptr;
     }
     c->state = 0;                                 // H changed: parameters and results are stale
+    return DACP_OK;
+}
+
+dacp_status dacp_set_global_flips(dacp_handle c, const double* coef) {
+    TRY(check_handle(c));
+    std::vector<double> g(c->R, 0.0);
+    bool any = false;
+    for (int r = 0; r < c->R && coef; ++r) {
+        if (!isfinite(coef[r])) return fail(c, DACP_ERR_ARG, "non-finite global-flip coefficient");
+        g[r] = coef[r];
+        any = any || coef[r] != 0.0;
+    }
+    if (any && !c->gflip_d) TRY(dalloc_t(c, &c->gflip_d, static_cast<size_t>(c->R)));
+    if (any) CK(cudaMemcpyAsync(c->gflip_d, g.data(), sizeof(double) * c->R, cudaMemcpyHostToDevice, c->st));
+    c->gflip_h = g;
+    c->has_gflip = any;
+    for (int r = 0; r < c->R; ++r)
+        c->pnorm[r] = c->pnorm0[r] + (c->pnorm_pairs.empty() ? 0.0 : c->pnorm_pairs[r]) + fabs(g[r]);
+    CK(cudaMemcpyAsync(c->pnorm_d, c->pnorm.data(), sizeof(double) * c->R, cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (Graph* gr : {&c->gf, &c->ge}) {         // captured launches hold the old arguments
+        if (gr->exec) cudaGraphExecDestroy(gr->exec);
+        gr->exec = nullptr;
+    }
+    c->state = 0;                                 // H changed: parameters and results are stale
+    return DACP_OK;
+}
+
+dacp_status dacp_create_parity_sectors(dacp_handle* out, int n_real, const int* n_spins, const double* J,
+                                       const double* h, const double* gamma, int block_b, int precision,
+                                       const double* psi0, void* stream) {
+    if (!out) return DACP_ERR_ARG;
+    *out = nullptr;
+    if (n_real <= 0 || !n_spins || !J || !h || !gamma || !psi0) return DACP_ERR_ARG;
+    int64_t jo = 0, ho = 0;
+    std::vector<int> ns;
+    std::vector<double> Js, hs, gs, gf;
+    for (int r = 0; r < n_real; ++r) {
+        const int N = n_spins[r];
+        if (N < 2 || N > kMaxSpins) return DACP_ERR_ARG;
+        for (int i = 0; i < N; ++i)
+            if (h[ho + i] != 0.0) return DACP_ERR_ARG;           // a z-field breaks the parity symmetry
+        for (int sigma = 1; sigma >= -1; sigma -= 2) {
+            const int M = N - 1;
+            ns.push_back(M);
+            for (int i = 0; i < M; ++i)
+                for (int j = 0; j < M; ++j) Js.push_back(j > i ? J[jo + static_cast<int64_t>(i) * N + j] : 0.0);
+            for (int i = 0; i < M; ++i) {
+                hs.push_back(J[jo + static_cast<int64_t>(i) * N + (N - 1)]);    // z_{N-1} = +1 on the representatives
+                gs.push_back(gamma[ho + i]);
+            }
+            gf.push_back(sigma * gamma[ho + N - 1]);
+        }
+        jo += static_cast<int64_t>(N) * N;
+        ho += N;
+    }
+    dacp_handle c = nullptr;
+    dacp_status st = dacp_create(&c, 2 * n_real, ns.data(), Js.data(), hs.data(), gs.data(), block_b, precision, psi0,
+                                 stream);
+    if (st != DACP_OK) return st;
+    st = dacp_set_global_flips(c, gf.data());
+    if (st != DACP_OK) {
+        dacp_destroy(c);
+        return st;
+    }
+    *out = c;
+    return DACP_OK;
+}
+
+dacp_status dacp_merge_sectors(int n_real, int n_in, const double* eigs_in, const int* n_found_in, int n_eigs,
+                               double* eigs, int* n_found) {
+    if (n_real <= 0 || n_in < 1 || n_eigs < 1 || !eigs_in || !n_found_in || !eigs || !n_found) return DACP_ERR_ARG;
+    for (int r = 0; r < n_real; ++r) {
+        const int a = 2 * r, b = 2 * r + 1;
+        if (n_found_in[a] < 0 || n_found_in[b] < 0) {          // a failed sector fails the realization
+            n_found[r] = n_found_in[a] < 0 ? n_found_in[a] : n_found_in[b];
+            continue;
+        }
+        // every level of a sector inside the largest |E| it returned came back: the union is complete
+        // up to the smaller of the two radii
+        double cover = 1e300;
+        std::vector<double> all;
+        for (int s2 : {a, b}) {
+            const int nf = std::min(n_found_in[s2], n_in);
+            double m = 0.0;
+            for (int i = 0; i < nf; ++i) {
+                const double v = eigs_in[static_cast<int64_t>(s2) * n_in + i];
+                all.push_back(v);
+                m = std::max(m, fabs(v));
+            }
+            cover = std::min(cover, m);
+        }
+        std::stable_sort(all.begin(), all.end(), [](double x, double y) {
+            return fabs(x) < fabs(y) || (fabs(x) == fabs(y) && x < y);
+        });
+        int cnt = 0;
+        for (double v : all) {
+            if (cnt == n_eigs || fabs(v) > cover) break;
+            eigs[static_cast<int64_t>(r) * n_eigs + cnt++] = v;
+        }
+        std::sort(eigs + static_cast<int64_t>(r) * n_eigs, eigs + static_cast<int64_t>(r) * n_eigs + cnt);
+        n_found[r] = cnt;
+    }
     return DACP_OK;
 }
 

@@ -129,6 +129,7 @@ struct StepArgs {
     const int* pair_ij;      // [R][kMaxPairs] bit i | (bit j << 8), i < j
     const double* pair_c;    // [R][kMaxPairs][2] coefficient when bits i, j are equal (Jxx - Jyy)
                              // and when they differ (Jxx + Jyy)
+    const double* gflip;     // [R] coefficient of the global flip X_0 X_1 ... X_{N-1}; nullptr: none
 };
 
 }  // namespace dacp

@@ -282,7 +282,7 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
     constexpr bool kEarlyY = sizeof(T) == 4;     // prefetch y1 / y2 before the flips (float32 only)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
-    __shared__ T gam_s[kMaxSpins];
+    __shared__ T gam_s[kMaxSpins + 1];             // x-fields, then the global-flip coefficient
     __shared__ double red_s[kThreads / 32][2 * B * B];
     __shared__ int last_s;
     __shared__ __align__(8) uint64_t bar_s;
@@ -346,6 +346,10 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
         if (tid < R.N) {
             const T g = static_cast<const T*>(a.gam)[it.r * kMaxSpins + tid];
             gam_s[tid] = kFold ? ch * g : g;
+        }
+        if (tid == kMaxSpins && a.gflip) {
+            const T g = static_cast<T>(__ldg(a.gflip + it.r));
+            gam_s[kMaxSpins] = kFold ? ch * g : g;
         }
 
         if (tstates >= SU) {
@@ -528,6 +532,33 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                         }
                     }
                 }
+                // global flip X_0 ... X_{N-1}: partner s XOR (2^N - 1); within a unit of SU
+                // states the partners run backwards, so one unit's worth is read element by element
+                if (a.gflip) {
+                    const T gf = gam_s[kMaxSpins];
+                    const int64_t fm = (static_cast<int64_t>(1) << R.N) - 1;
+#pragma unroll
+                    for (int k = 0; k < UP; ++k) {
+                        if (!val[k]) continue;
+                        const int64_t s0 = tile0 + static_cast<int64_t>(uu[k]) * SU;
+                        if constexpr (SU == 1) {
+                            T pv[VU];
+                            ld_unit_g<T, B, COHERENT>(xg + (s0 ^ fm) * B, pv);
+#pragma unroll
+                            for (int v = 0; v < VU; ++v) AC::mad(acc[k][v], gf, pv[v]);
+                        } else {
+#pragma unroll
+                            for (int js = 0; js < SU; ++js) {
+#pragma unroll
+                                for (int col = 0; col < B; ++col) {
+                                    const int64_t e = ((s0 + js) ^ fm) * B + col;
+                                    const T xp = COHERENT ? ld_cg(xg + e) : ld_ro(xg + e);
+                                    AC::mad(acc[k][js * B + col], gf, xp);
+                                }
+                            }
+                        }
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < UP; ++k) {
                     if (!val[k]) continue;
@@ -579,6 +610,12 @@ __device__ __forceinline__ void tile_step(const StepArgs& a, const int item, con
                     const T* q = tile + (sl ^ (1 << i)) * B;
 #pragma unroll
                     for (int p = 0; p < B; ++p) acc[p] = fma(g, q[p], acc[p]);
+                }
+                if (a.gflip) {                       // global flip: the whole realization is this tile
+                    const T gf = gam_s[kMaxSpins];
+                    const T* q = tile + (sl ^ ((1 << R.N) - 1)) * B;
+#pragma unroll
+                    for (int p = 0; p < B; ++p) acc[p] = fma(gf, q[p], acc[p]);
                 }
                 T o[B];
 #pragma unroll
@@ -862,6 +899,17 @@ __device__ __forceinline__ void tile_step_df4(const StepArgs& a, const int item,
                     dot2_mad(acc1, cf2, p1);
                 }
             }
+            if (a.gflip) {                                  // global flip X_0 ... X_{N-1}
+                const double gfv = __ldg(a.gflip + it.r);
+                if (gfv != 0.0) {
+                    const T gf = ch * T(gfv);
+                    const uint32_t fm = (R.N >= 32) ? 0xffffffffu : ((1u << R.N) - 1u);
+                    T p0, p1;
+                    ld2_g<COHERENT>(xg + ((sg ^ fm) * B + col), p0, p1);
+                    dot2_mad(acc0, gf, p0);
+                    dot2_mad(acc1, gf, p1);
+                }
+            }
             // diagonal term, then w_{k+1} = c_h H x + c_1 y + c_2 z
             const T d = ch * dr;
             dot2_mad(acc0, d, a0);
@@ -1015,8 +1063,8 @@ __device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int ite
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
     // per spin: (g.hi, g.hi, g.lo, g.lo) and (-g.hi, -g.hi), the register pairs of a DF2m
-    __shared__ __align__(16) float4 gam_s[kMaxSpins];
-    __shared__ __align__(8) float2 ngam_s[kMaxSpins];
+    __shared__ __align__(16) float4 gam_s[kMaxSpins + 1];        // slot kMaxSpins: the global flip
+    __shared__ __align__(8) float2 ngam_s[kMaxSpins + 1];
     __shared__ double red_s[kThreads / 32][2 * B * B];
     __shared__ int last_s;
     __shared__ __align__(8) uint64_t bar_s;
@@ -1075,6 +1123,11 @@ __device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int ite
             gam_s[tid] = make_float4(g.hi, g.hi, g.lo, g.lo);
             ngam_s[tid] = make_float2(-g.hi, -g.hi);
         }
+        if (tid == kMaxSpins && a.gflip) {
+            const T g = ch * T(__ldg(a.gflip + it.r));
+            gam_s[kMaxSpins] = make_float4(g.hi, g.hi, g.lo, g.lo);
+            ngam_s[kMaxSpins] = make_float2(-g.hi, -g.hi);
+        }
 
         constexpr uint32_t nbytes = static_cast<uint32_t>(tstates) * B * sizeof(T);
         if (tid == 0) {
@@ -1103,6 +1156,7 @@ __device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int ite
         constexpr int nhalf = 2 * tstates;               // (state, column pair) slots of the tile
         const ulonglong2* g2 = reinterpret_cast<const ulonglong2*>(gam_s);
         const uint64_t* ng2 = reinterpret_cast<const uint64_t*>(ngam_s);
+
         for (int hb = 0; hb < nhalf; hb += kThreads) {
             const int hs = hb + tid;
             const bool val = (TB >= 7) || hs < nhalf;
@@ -1141,6 +1195,11 @@ __device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int ite
                 const ulonglong2 gv = g2[TB + j];
                 dot2x2_mad(acc, DF2m{gv.x, ng2[TB + j], gv.y},
                            ld_df2_g<COHERENT>(xg + ((sg ^ (1u << (TB + j))) * B + col)));
+            }
+            if (a.gflip) {                                  // global flip X_0 ... X_{N-1}
+                const ulonglong2 gv = g2[kMaxSpins];
+                dot2x2_mad(acc, DF2m{gv.x, ng2[kMaxSpins], gv.y},
+                           ld_df2_g<COHERENT>(xg + ((sg ^ ((1u << R.N) - 1u)) * B + col)));
             }
             // diagonal term, then w_{k+1} = c_h H x + c_1 y + c_2 z
             dot2x2_mad(acc, df2m_bcast(ch * dr), A);

@@ -42,12 +42,12 @@ def test_roofline_arithmetic():
     clk = {"sm_mhz": 2000.0}
     states = 1e9
     wl = dict(B.WORKLOADS["c3"])
-    r = B.roofline(wl, models, phase, 3e12, states, clk, 152)
+    r = B.roofline(wl, len(models), phase, 3e12, states, clk, 152)
     # double-float: (N b + b + b (b + 1)) multiply-adds x 12 float32 lane operations per state, and
     # b subtractions of w_(k-1) x 8
     ops = 12 * (14 * 4 + 4 + 4 * 5) + 8 * 4
     assert r["bound"] == "alu" and abs(r["achieved"] - states * ops / 1e12) < 1e-9
     assert abs(r["peak"] - 152 * 128 * 2000e6 / 1e12) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     wl["prec"] = "fp32"
-    r = B.roofline(wl, models, phase, 3e12, states, clk, 152)
+    r = B.roofline(wl, len(models), phase, 3e12, states, clk, 152)
     assert r["bound"] == "hbm" and abs(r["achieved"] - 3000.0) < 1e-9 and r["unit"] == "GB/s"

@@ -214,3 +214,36 @@ def test_reflection_sector_blocks_reproduce_the_spectrum():
 def test_reflection_sectors_refuse_an_asymmetric_model():
     with pytest.raises(ValueError):
         Hm.reflection_sector_matrices(W.random_model(6, seed=2))
+
+
+def test_global_flip_matches_kronecker_products_and_trace():
+    """The global flip c X_0 ... X_{N-1}: the matrix-free apply, the row-wise apply and the
+    Kronecker builder agree, and Tr H^2 / D gains c^2 (Pauli strings are orthonormal)."""
+    m = dict(W.random_model(6, seed=4))
+    m["gflip"] = 0.731
+    Hd = Hm.dense_h(m)
+    x = W.start_vectors(6, 2, seed=1)
+    assert np.abs(Hm.apply_h(m, x) - Hd @ x).max() < 1e-13 * np.abs(Hd).max() * np.abs(x).max() * 64
+    y, _ = Hm.apply_h_rows(m, x, np.arange(64), with_abs=True)
+    assert np.abs(y - Hd @ x).max() < 1e-12
+    assert abs(np.trace(Hd @ Hd) / 64 - Hm.trace_h2_per_state(m)) < 1e-12
+    assert np.abs(Hd - Hd.T).max() == 0.0
+
+
+@pytest.mark.parametrize("N,seed", [(8, 3), (10, 7)])
+def test_parity_sectors_split_the_spectrum(N, seed):
+    """The two (N-1)-spin sector models of a spin-glass shard (h = 0) have spectra whose union is
+    the full spectrum (dense eigh of both sides), 2^(N-1) levels each."""
+    m = W.spin_glass_shard(N, seed=seed)
+    E = np.linalg.eigvalsh(Hm.dense_h(m))
+    sp, sm = Hm.parity_sector_models(m)
+    assert sp["N"] == sm["N"] == N - 1 and sp["gflip"] == -sm["gflip"] == m["gamma"][N - 1]
+    Ep = np.linalg.eigvalsh(Hm.dense_h(sp))
+    Em = np.linalg.eigvalsh(Hm.dense_h(sm))
+    assert len(Ep) == len(Em) == 1 << (N - 1)
+    assert np.abs(np.sort(np.concatenate([Ep, Em])) - E).max() < 1e-10 * np.abs(E).max()
+    # a z-field breaks the symmetry and is refused
+    bad = dict(m)
+    bad["h"] = np.full(N, 0.1)
+    with pytest.raises(ValueError):
+        Hm.parity_sector_models(bad)

@@ -140,6 +140,12 @@ def start_vectors(N: int, b: int, seed: int, r: int = 0) -> np.ndarray:
     return np.ascontiguousarray(rng.standard_normal((1 << N, b)))
 
 
+def sector_start_vectors(N: int, b: int, seed: int, r: int = 0):
+    """Start blocks of the two parity sectors (+1, -1) of an N-spin realization r: two draws of
+    start_vectors(N - 1, b, seed, ...) keyed 2 r and 2 r + 1."""
+    return [start_vectors(N - 1, b, seed, 2 * r), start_vectors(N - 1, b, seed, 2 * r + 1)]
+
+
 def pack_models(models):
     """Concatenate a list of models into the flat arrays the C ABI takes.
 
