@@ -76,9 +76,10 @@ def make_inputs(wl, rank=0):
 
 
 # Levels asked of each parity sector when a model is solved as its two sectors: the two sectors
-# share the central levels about evenly, so 0.6 n_eigs each leaves a margin of 0.1 n_eigs per
-# sector (the merge returns fewer levels, never wrong ones, when a sector falls short).
-SECTOR_SHARE = 0.6
+# share the central levels about evenly (the larger held at most 0.503 of the 300 central levels of
+# N = 13 shards, by dense eigh), so 0.55 n_eigs each leaves a margin of 0.05 n_eigs per sector. The
+# merge returns fewer levels, never wrong ones, when a sector falls short; the line counts those.
+SECTOR_SHARE = 0.55
 
 
 def use_sectors(args, wl):
@@ -95,9 +96,9 @@ def sector_inputs(wl, rank=0):
 # DRAM bytes (read + write) of one evolution launch of step_kernel_df4tb<kEvolve, 11> with all 256
 # realizations of the default workload active, from one ncu capture of the current kernel (the
 # profile summaries keep the command); other workloads report none.
-DF32_EVOLVE_TRAFFIC = 319496192 + 102434304
+DF32_EVOLVE_TRAFFIC = 316232448 + 101191936
 # the same for the launch over the 512 parity sectors (N - 1 = 13 spins) of that batch
-DF32_SECTOR_EVOLVE_TRAFFIC = 317191936 + 104094208
+DF32_SECTOR_EVOLVE_TRAFFIC = 318150144 + 103256832
 DF32_TRAFFIC_SOURCE = "stored ncu capture of the current kernel, one launch, not re-measured in this run"
 # One error-free double-float multiply-add (the Dot2 step): TwoProduct 2,
 # TwoSum 6, and 4 float32 operations that fold the cross terms and the two
@@ -420,7 +421,7 @@ def run_gpu(args, wl, rank, world):
         # built in the library; levels merged per shard (dacp_merge_sectors) inside the step
         sec_psis = sector_inputs(wl, rank)
         d = P.Dacp.parity_sectors(models, sec_psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
-        n_run = int(np.ceil(SECTOR_SHARE * n_eigs))
+        n_run = int(np.ceil(args.sector_share * n_eigs))
     else:
         d = P.Dacp(models, psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
         n_run = n_eigs
@@ -680,6 +681,8 @@ def main():
     ap.add_argument("--sectors", default="auto", choices=["auto", "on", "off"],
                     help="solve each realization as its two parity sectors (auto: for the spin-glass shards, "
                          "which have no z-fields)")
+    ap.add_argument("--sector-share", type=float, default=SECTOR_SHARE,
+                    help="levels asked of each parity sector, as a fraction of n_eigs")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-rank", type=int, default=0, help=argparse.SUPPRESS)

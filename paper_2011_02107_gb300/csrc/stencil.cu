@@ -1164,10 +1164,15 @@ __device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int ite
             const uint32_t sg = static_cast<uint32_t>(tile0) + static_cast<uint32_t>(sl);
             const int col = 2 * h;
             const DF2 A = ld_df2_s(tile + sl * B + col);
+            // the global flip's partner takes the first free early slot (parity sectors: ngb = 2)
+            const bool gflip = a.gflip != nullptr;
+            const uint32_t gfm = (1u << R.N) - 1u;
             DF2 pe[EG > 0 ? EG : 1];
 #pragma unroll
-            for (int j = 0; j < EG; ++j)
+            for (int j = 0; j < EG; ++j) {
                 if (j < ngb) pe[j] = ld_df2_g<COHERENT>(xg + ((sg ^ (1u << (TB + j))) * B + col));
+                else if (j == ngb && gflip) pe[j] = ld_df2_g<COHERENT>(xg + ((sg ^ gfm) * B + col));
+            }
             const T dr = ld_ro(dg + sg);
             DF2 Y = DF2{0ull, 0ull}, Z = DF2{0ull, 0ull};
             if (MODE != kFilter1 && use1) Y = ld_df2_rw<COHERENT>(y1g + (sg * B + col));
@@ -1189,6 +1194,9 @@ __device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int ite
                 if (j < ngb) {
                     const ulonglong2 gv = g2[TB + j];
                     dot2x2_mad(acc, DF2m{gv.x, ng2[TB + j], gv.y}, pe[j]);
+                } else if (j == ngb && gflip) {           // global flip X_0 ... X_{N-1}, loaded early
+                    const ulonglong2 gv = g2[kMaxSpins];
+                    dot2x2_mad(acc, DF2m{gv.x, ng2[kMaxSpins], gv.y}, pe[j]);
                 }
             }
             for (int j = EG; j < ngb; ++j) {
@@ -1196,10 +1204,10 @@ __device__ __forceinline__ void tile_step_df4x2(const StepArgs& a, const int ite
                 dot2x2_mad(acc, DF2m{gv.x, ng2[TB + j], gv.y},
                            ld_df2_g<COHERENT>(xg + ((sg ^ (1u << (TB + j))) * B + col)));
             }
-            if (a.gflip) {                                  // global flip X_0 ... X_{N-1}
+            if (gflip && ngb >= EG) {                       // global flip, no early slot left
                 const ulonglong2 gv = g2[kMaxSpins];
                 dot2x2_mad(acc, DF2m{gv.x, ng2[kMaxSpins], gv.y},
-                           ld_df2_g<COHERENT>(xg + ((sg ^ ((1u << R.N) - 1u)) * B + col)));
+                           ld_df2_g<COHERENT>(xg + ((sg ^ gfm) * B + col)));
             }
             // diagonal term, then w_{k+1} = c_h H x + c_1 y + c_2 z
             dot2x2_mad(acc, df2m_bcast(ch * dr), A);

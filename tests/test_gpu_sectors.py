@@ -115,3 +115,32 @@ def test_sector_path_at_the_benchmark_size_against_exact_levels():
         spacing = np.array([MT.local_spacing(lv, first + i) for i in range(n_eigs)])
         err = np.abs(eigs[j] - ref) / spacing
         assert err.max() <= 1e-2, (s, float(err.max()))
+
+
+def test_apply_h_with_global_flip_tile_specialised_kernel():
+    """Double-float b = 4 with 64 KB tiles (11 in-tile bits, the benchmark's kernel): the flip's
+    partner load takes a free early slot when fewer than three bits lie beyond the tile (N = 12,
+    13) and is issued late otherwise (N = 14, 15)."""
+    models = [_with_flip(W.random_model(N, seed=40 + N), 0.53 * (-1) ** N) for N in (12, 13, 14, 15)]
+    psis = [W.start_vectors(m["N"], 4, seed=6, r=i) for i, m in enumerate(models)]
+    d = P.Dacp(models, psis, block_b=4, precision=P.DACP_DF32)
+    try:
+        d.set_launch(0, 65536)
+        for r, m in enumerate(models):
+            N = m["N"]
+            x = W.start_vectors(N, 4, seed=10, r=r)
+            pk = df32_pack(x)
+            xd, xin = torch.from_numpy(pk).cuda(), df32_unpack(pk, 4)
+            yd = torch.zeros_like(xd)
+            torch.cuda.synchronize()
+            d.apply_h(r, xd.data_ptr(), yd.data_ptr())
+            torch.cuda.synchronize()
+            got = df32_unpack(yd.cpu().numpy(), 4)
+            rows = np.random.default_rng(N).choice(1 << N, size=4096, replace=False)
+            ref, scale = Hm.apply_h_rows(m, xin, rows, with_abs=True)
+            dscale = (np.abs(np.triu(m["J"], 1)).sum() + np.abs(m["h"]).sum()) * np.abs(xin[rows])
+            tol = 4 * ((N + 4) * 2.0 ** -44 * scale + (N * (N + 1) // 2 + 1) * 2.0 ** -53 * dscale)
+            err = np.abs(got[rows] - ref)
+            assert (err <= tol).all(), (N, float(err.max()), float((err / scale).max()))
+    finally:
+        d.close()
