@@ -404,9 +404,9 @@ dacp_status dacp_test_emax_rule(int k, const double* alpha, const double* beta2,
 
 /*
  * dacp_set_solver -- how dacp_central_eigs runs the dense float64 algebra:
- * 1 (default) = one batched cuSOLVER syev call per group for S and one for
- * H~, with a strided-batched dgemm (W = H U) and a syrkx per realization
- * (the lower triangle of H~ = U^T W) between them; smaller bases are
+ * 1 (default) = one batched cuSOLVER syev call per group (up to 256
+ * realizations) for S and one for H~, with two strided-batched dgemms
+ * (W = H U, H~ = U^T W) between them; smaller bases are
  * zero-padded to the largest (the padding only adds S eigenvalues 0, which
  * the cut-off removes). Used when there are several realizations and every
  * basis is at least 3/4 of the largest. 0 = concurrent lanes (own stream,
