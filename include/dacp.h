@@ -425,6 +425,18 @@ dacp_status dacp_set_solver(dacp_handle hd, int mode);
 dacp_status dacp_test_poison_barrier(dacp_handle hd);
 
 /*
+ * dacp_test_fail_alloc -- test hook for allocation failure: after `after`
+ * more device allocations by this library (0 = the next one), one allocation
+ * fails as if cudaMalloc had run out of memory, and the call that made it
+ * returns DACP_ERR_NOMEM after freeing what it allocated (dacp_create frees
+ * the whole handle; a handle whose call failed can still be destroyed).
+ * Negative `after` switches the hook off; it also switches itself off once
+ * it has fired. Process-wide, so it reaches dacp_create. Allocations inside
+ * cuSOLVER / cuBLAS and of the parameter network are not counted.
+ */
+dacp_status dacp_test_fail_alloc(int64_t after);
+
+/*
  * dacp_get_launch_count -- number of this library's own CUDA kernels launched
  * on the handle since dacp_create (kernels inside cuSOLVER / cuBLAS calls are
  * not counted). A graph replay counts each kernel node it runs.

@@ -38,7 +38,7 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings",
            "dacp_set_emax_rule", "dacp_test_emax_rule", "dacp_solve_learned",
            "dacp_lanczos_filtered", "dacp_set_global_flips", "dacp_create_parity_sectors",
-           "dacp_merge_sectors"]
+           "dacp_merge_sectors", "dacp_test_fail_alloc"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -99,6 +99,7 @@ def _load():
         "dacp_autotune": [P, I, ctypes.POINTER(I)],
         "dacp_set_launch": [P, I, I],
         "dacp_test_poison_barrier": [P],
+        "dacp_test_fail_alloc": [L],
         "dacp_set_solver": [P, I],
         "dacp_moments_noalloc": [I, P, P, P, D, P, I, P, P],
         "dacp_get_launch": [P, ctypes.POINTER(I), ctypes.POINTER(I)],
@@ -458,6 +459,10 @@ def dacp_set_solver(hd, mode):
 
 def dacp_test_poison_barrier(hd):
     _check(hd, _lib.dacp_test_poison_barrier(hd))
+
+
+def dacp_test_fail_alloc(after):
+    _check(None, _lib.dacp_test_fail_alloc(int(after)))
 
 
 def dacp_get_launch(hd):

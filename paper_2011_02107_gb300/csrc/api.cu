@@ -5,6 +5,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -195,9 +196,28 @@ dacp_status fail(dacp_ctx* c, dacp_status s, const char* fmt, ...) {
         if (s_ != DACP_OK) return s_;             \
     } while (0)
 
+// NVTX range over one library call (T_F / T_E / T_D and the rest show by name on an
+// Nsight timeline; without a tool attached a push / pop costs a few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Allocation-failure injection (dacp_test_fail_alloc): the number of device allocations still to
+// succeed before one fails; negative = off. Process-wide, so that dacp_create can be reached too.
+static std::atomic<int64_t> g_alloc_countdown{-1};
+
 dacp_status dalloc(dacp_ctx* c, void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    for (int64_t left = g_alloc_countdown.load(); left >= 0;) {
+        if (g_alloc_countdown.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) return fail(c, DACP_ERR_NOMEM, "injected allocation failure (%zu bytes)", bytes);
+            break;
+        }
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -531,6 +551,7 @@ void dacp_destroy(dacp_handle c) {
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->st) cudaStreamSynchronize(c->st);
+    if (c->st2) cudaStreamSynchronize(c->st2);
     free_lanes(c);
     if (c->gf.exec) cudaGraphExecDestroy(c->gf.exec);
     if (c->ge.exec) cudaGraphExecDestroy(c->ge.exec);
@@ -550,6 +571,7 @@ void dacp_destroy(dacp_handle c) {
 
 dacp_status dacp_create(dacp_handle* out, int n_real, const int* n_spins, const double* J, const double* h,
                         const double* gamma, int block_b, int precision, const double* psi0, void* stream) {
+    NvtxRange nvtx_("dacp_create");
     if (!out) return DACP_ERR_ARG;
     *out = nullptr;
     if (n_real <= 0 || !n_spins || !J || !h || !gamma || !psi0) return DACP_ERR_ARG;
@@ -897,11 +919,13 @@ extern "C" {
 
 dacp_status dacp_choose_params(dacp_handle c, int n_eigs, double d_ratio, double basis_ratio, double c_order,
                                int lanczos_steps, int kpm_moments) {
+    NvtxRange nvtx_("dacp_choose_params");
     TRY(check_handle(c));
     return choose_impl(c, n_eigs, d_ratio, basis_ratio, c_order, lanczos_steps, kpm_moments, nullptr);
 }
 
 dacp_status dacp_choose_params_mlp(dacp_handle c, dacp_mlp net, int n_eigs, int lanczos_steps, int kpm_moments) {
+    NvtxRange nvtx_("dacp_choose_params_mlp");
     TRY(check_handle(c));
     if (!net) return fail(c, DACP_ERR_ARG, "NULL network");
     return choose_impl(c, n_eigs, 2.0, 1.5, 0.0, lanczos_steps, kpm_moments, net);
@@ -930,6 +954,7 @@ dacp_status dacp_get_params(dacp_handle c, double* emax, double* a, int* K, int*
 }
 
 dacp_status dacp_filter(dacp_handle c) {
+    NvtxRange nvtx_("dacp_filter (T_F)");
     TRY(check_handle(c));
     if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_filter before parameters");
     const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
@@ -953,6 +978,7 @@ dacp_status dacp_filter(dacp_handle c) {
 }
 
 dacp_status dacp_basis_moments(dacp_handle c) {
+    NvtxRange nvtx_("dacp_basis_moments (T_E)");
     TRY(check_handle(c));
     if (c->state < 2) return fail(c, DACP_ERR_STATE, "dacp_basis_moments before dacp_filter");
     const size_t vec_bytes = static_cast<size_t>(c->Dtot) * c->b * c->esz;
@@ -1066,6 +1092,7 @@ dacp_status ws_alloc(dacp_ctx* c, BatchWs& w, const SolveRes& s, int G, int M, i
 // central selection.
 dacp_status solve_batch(dacp_ctx* c, BatchWs& w, const SolveRes& s, const int* idx, int g, int n_eigs, double window,
                         double eps, double* eigs, int* n_found, int* rank) {
+    NvtxRange nvtx_("solve_batch");
     const int b = c->b;
     int Mg = 0;
     for (int i = 0; i < g; ++i) Mg = std::max(Mg, b * (2 * c->n[idx[i]] + 1));
@@ -1181,6 +1208,7 @@ extern "C" {
 
 dacp_status dacp_central_eigs(dacp_handle c, int n_eigs, double window, double eps, double* eigs, int* n_found,
                               int* rank) {
+    NvtxRange nvtx_("dacp_central_eigs (T_D)");
     TRY(check_handle(c));
     if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_central_eigs before dacp_basis_moments");
     if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
@@ -1342,6 +1370,7 @@ void size_batches(const dacp_ctx* c, std::vector<int>& idx, int G, std::vector<s
 extern "C" {
 
 dacp_status dacp_solve(dacp_handle c, int n_eigs, double window, double eps, double* eigs, int* n_found, int* rank) {
+    NvtxRange nvtx_("dacp_solve");
     TRY(check_handle(c));
     if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_solve before parameters");
     if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
@@ -1482,6 +1511,7 @@ dacp_status dacp_solve(dacp_handle c, int n_eigs, double window, double eps, dou
 // copies of their couplings, fields and start vectors.
 dacp_status dacp_solve_learned(dacp_handle c, dacp_mlp net, int n_eigs, double window, double eps, double* eigs,
                                int* n_found, int* rank, int* n_fallback) {
+    NvtxRange nvtx_("dacp_solve_learned");
     TRY(check_handle(c));
     if (!net) return fail(c, DACP_ERR_ARG, "NULL network");
     if (n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad output arguments");
@@ -1711,6 +1741,7 @@ extern "C" {
 
 dacp_status dacp_residuals(dacp_handle c, int r, int n_eigs, double window, double eps, double* eigs, double* resid,
                            int* n_found) {
+    NvtxRange nvtx_("dacp_residuals");
     TRY(check_handle(c));
     if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_residuals before dacp_basis_moments");
     if (r < 0 || r >= c->R || n_eigs < 1 || !eigs || !resid || !n_found)
@@ -1743,6 +1774,7 @@ dacp_status dacp_residuals(dacp_handle c, int r, int n_eigs, double window, doub
 
 dacp_status dacp_eigenvectors(dacp_handle c, int r, int n_eigs, double window, double eps, double* eigs,
                               double* phi_dev, int64_t ld, int* n_found) {
+    NvtxRange nvtx_("dacp_eigenvectors");
     TRY(check_handle(c));
     if (c->state < 3) return fail(c, DACP_ERR_STATE, "dacp_eigenvectors before dacp_basis_moments");
     if (r < 0 || r >= c->R || n_eigs < 1 || !eigs || !phi_dev || !n_found)
@@ -1821,6 +1853,7 @@ dacp_status dacp_eigenvectors(dacp_handle c, int r, int n_eigs, double window, d
 // the converged Ritz values.
 dacp_status dacp_lanczos_filtered(dacp_handle c, int r, int steps, int n_eigs, double res_tol, double* eigs,
                                   int* n_found, int* dim_out, double* ms_out, int64_t* hv_out) {
+    NvtxRange nvtx_("dacp_lanczos_filtered");
     TRY(check_handle(c));
     if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_lanczos_filtered before parameters");
     if (r < 0 || r >= c->R || n_eigs < 1 || !eigs || !n_found) return fail(c, DACP_ERR_ARG, "bad arguments");
@@ -2034,6 +2067,7 @@ static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tune_cache;
 
 dacp_status dacp_autotune(dacp_handle c, int orders, int* tile_bytes_out) {
+    NvtxRange nvtx_("dacp_autotune");
     TRY(check_handle(c));
     if (c->state < 1) return fail(c, DACP_ERR_STATE, "dacp_autotune before parameters");
     if (orders < 4 || orders > 100000) return fail(c, DACP_ERR_ARG, "orders out of range");
@@ -2266,6 +2300,11 @@ dacp_status dacp_set_solver(dacp_handle c, int mode) {
     TRY(check_handle(c));
     if (mode != 0 && mode != 1) return fail(c, DACP_ERR_ARG, "solver mode must be 0 or 1");
     c->batched_solve = mode == 1;
+    return DACP_OK;
+}
+
+dacp_status dacp_test_fail_alloc(int64_t after) {
+    g_alloc_countdown.store(after < 0 ? -1 : after);
     return DACP_OK;
 }
 
