@@ -376,8 +376,11 @@ dacp_status dacp_get_launch(dacp_handle hd, int* mode, int* tile_bytes);
  *                residual of any Ritz pair (z_i the eigenvectors of the
  *                tridiagonal matrix, taken from the interlacing identity
  *                without forming them).
- * Both are times 1.001 and clamped to the Pauli 1-norm. Rule 1 runs about 1.14
- * times the spectral radius where rule 0 runs about 1.46 (measured against
+ * Both are times 1.001 and clamped to the Pauli 1-norm. Rule 0 takes the
+ * call's lanczos_steps (20 by default); rule 1 runs the same recurrence on to
+ * 64 steps (at most 2^N), whose first steps are rule 0's, so rule 0's bound is
+ * the same under either rule. Rule 1 then runs about 1.08 times the spectral
+ * radius (1.14 at 20 steps) where rule 0 runs about 1.46 (measured against
  * dense spectra). Under rule 1 the KPM moments, the network's features and
  * the window a still come from rule 0's bound (so a network sees the features
  * it was trained on); rule 1's bound becomes E_max of the two recurrences and

@@ -773,6 +773,8 @@ dacp_status dacp_set_params(dacp_handle c, const double* emax, const double* a, 
 
 namespace {
 
+constexpr int kRule1LanczosSteps = 64;
+
 // Lanczos bound + KPM moments of column 0 of psi0, then the window, order and
 // basis size: from (d_ratio, basis_ratio, c_order) or from the network.
 dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ratio, double c_order,
@@ -785,7 +787,15 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
         return fail(c, DACP_ERR_ARG, "the parameter network needs %d inputs and 3 outputs", kFeatures);
     int minN = kMaxSpins;
     for (int r = 0; r < c->R; ++r) minN = std::min(minN, c->N[r]);
-    const int steps = static_cast<int>(std::min<int64_t>(lanczos_steps, static_cast<int64_t>(1) << minN));
+    // Rule 0 takes the first lanczos_steps steps. Rule 1 runs the same recurrence on to
+    // kRule1LanczosSteps: its bound falls from about 1.14 to 1.08 times the spectral radius
+    // (N = 11, 12 shards), and rule 0's bound, hence the window and the network's features, is
+    // unchanged because the first steps are the same.
+    const int64_t dim_min = static_cast<int64_t>(1) << minN;
+    const int steps0 = static_cast<int>(std::min<int64_t>(lanczos_steps, dim_min));
+    const int steps = c->emax_rule == 1
+                          ? static_cast<int>(std::min<int64_t>(std::max(lanczos_steps, kRule1LanczosSteps), dim_min))
+                          : steps0;
     const int R = c->R;
     const int ni = static_cast<int>(c->items.size());
     const size_t sv = static_cast<size_t>(c->Dtot) * c->esz;   // one column
@@ -851,9 +861,9 @@ dacp_status choose_impl(dacp_ctx* c, int n_eigs, double d_ratio, double basis_ra
         }
         // the residual rule's bound normalises the KPM moments, the network's features and the window
         // whatever the rule; rule 1's tighter bound only shortens the two recurrences (below)
-        CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax_d, 0, c->st));
+        CK(launch_lanczos_bound(R, lmom, rows, beta2, steps0, steps, c->pnorm_d, 1e-3, emax_d, 0, c->st));
         if (c->emax_rule == 1)
-            CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, c->pnorm_d, 1e-3, emax1_d, 1, c->st));
+            CK(launch_lanczos_bound(R, lmom, rows, beta2, steps, steps, c->pnorm_d, 1e-3, emax1_d, 1, c->st));
         // reset the apply coefficients of the test hook
         for (int r = 0; r < R; ++r) lc[8 * r + 1] = 0.0;
         CK(cudaMemcpyAsync(c->apply_coef_d, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice, c->st));

@@ -63,7 +63,7 @@ cudaError_t launch_lanczos_orth(int prec, const Item* items, const RealInfo* rea
                                 double* beta2, int steps, cudaStream_t st);
 cudaError_t launch_lanczos_scale(int prec, const Item* items, const RealInfo* real, int n_items, void* w,
                                  const double* beta2, int j, int steps, double* coef, int R, cudaStream_t st);
-cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps,
+cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps, int stride,
                                  const double* pnorm, double safety, double* emax, int rule, cudaStream_t st);
 cudaError_t launch_kpm_window(int R, const RealInfo* real, const double* P, int M, const double* emax,
                               double d_target, double c_order, double basis_ratio, int b, const float* knobs,

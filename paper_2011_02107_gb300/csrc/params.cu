@@ -5,6 +5,7 @@
 // The H.v steps reuse the fused stencil kernel; these kernels do the vector
 // updates, the small tridiagonal eigenproblem and the window search.
 
+#include <float.h>
 #include <math.h>
 
 #include "../../include/dacp.h"
@@ -100,82 +101,109 @@ __host__ __device__ int sturm_count(const double* al, const double* b2, int k, d
 }
 
 // The idx-th smallest eigenvalue (0-based) of the k x k tridiagonal, by bisection
-// on the Sturm count inside the Gershgorin interval [-gmax, gmax].
+// on the Sturm count inside the Gershgorin interval [-gmax, gmax], until the interval
+// is a few units of rounding of the matrix scale wide (about 52 halvings): the bounds
+// below need the eigenvalues to the matrix's absolute accuracy only.
 __host__ __device__ double tridiag_eig(const double* al, const double* b2, int k, int idx, double gmax) {
     double lo = -gmax - 1.0, hi = gmax + 1.0;
+    const double tol = 4.0 * DBL_EPSILON * (gmax + 1.0);
     for (int it = 0; it < 200; ++it) {
+        if (!(hi - lo > tol)) break;
         const double mid = 0.5 * (lo + hi);
         if (sturm_count(al, b2, k, mid) >= idx + 1) hi = mid; else lo = mid;
     }
     return 0.5 * (lo + hi);
 }
 
+// Gershgorin radius of the tridiagonal: max_i |alpha_i| + beta_i + beta_{i+1}.
+__host__ __device__ double tridiag_gmax_row(const double* al, const double* b2, int k, int i) {
+    const double bl = i > 0 ? sqrt(b2[i - 1]) : 0.0;
+    const double br = i < k - 1 ? sqrt(b2[i]) : 0.0;
+    return fabs(al[i]) + bl + br;
+}
+
+// z_{k,i}^2, the squared last component of the tridiagonal's i-th eigenvector, from its
+// eigenvalues th[0..k) and those of the leading (k-1) x (k-1) block mu[0..k-1):
+// prod_j (theta_i - mu_j) / prod_{j != i} (theta_i - theta_j). Cauchy interlacing pairs each
+// factor into a ratio of magnitude at most one; a zero denominator counts as one, which can
+// only enlarge the bound.
+__host__ __device__ double ritz_last_comp2(const double* th, const double* mu, int k, int i) {
+    double v = 1.0;
+    for (int j = 0; j < k; ++j) {
+        if (j == i) continue;
+        const double num = th[i] - mu[j < i ? j : j - 1];
+        const double den = th[i] - th[j];
+        if (den != 0.0) v *= fmin(1.0, fabs(num / den));
+    }
+    return v;
+}
+
 // Ritz-residual rule (rule 1): max |theta| + beta_{k+1} max_i |e_k^T z_i|, before the
-// safety factor. The last components of the tridiagonal's eigenvectors come without
-// the vectors, from z_{k,i}^2 = prod_j (theta_i - mu_j) / prod_{j != i} (theta_i - theta_j)
-// (mu: eigenvalues of the leading (k-1) x (k-1) block). Cauchy interlacing pairs each
-// factor into a ratio of magnitude at most one; a zero denominator counts as one, which
-// can only enlarge the bound. b2[0..k-2] are the squared off-diagonals, b2[k-1] the
-// squared residual norm. k <= 64.
+// safety factor. The last components come without the vectors (ritz_last_comp2).
+// b2[0..k-2] are the squared off-diagonals, b2[k-1] the squared residual norm. k <= 64.
+// Host form (test hook); the kernel below spreads the same steps over a warp.
 __host__ __device__ double ritz_rule_bound(const double* al, const double* b2, int k) {
     double gmax = 0.0;
-    for (int i = 0; i < k; ++i) {
-        const double bl = i > 0 ? sqrt(b2[i - 1]) : 0.0;
-        const double br = i < k - 1 ? sqrt(b2[i]) : 0.0;
-        gmax = fmax(gmax, fabs(al[i]) + bl + br);
-    }
+    for (int i = 0; i < k; ++i) gmax = fmax(gmax, tridiag_gmax_row(al, b2, k, i));
     double th[64], mu[64];
     for (int i = 0; i < k; ++i) th[i] = tridiag_eig(al, b2, k, i, gmax);
     for (int i = 0; i < k - 1; ++i) mu[i] = tridiag_eig(al, b2, k - 1, i, gmax);
     double zmax = k == 1 ? 1.0 : 0.0;
-    for (int i = 0; k > 1 && i < k; ++i) {
-        double v = 1.0;
-        for (int j = 0; j < k; ++j) {
-            if (j == i) continue;
-            const double num = th[i] - mu[j < i ? j : j - 1];
-            const double den = th[i] - th[j];
-            if (den != 0.0) v *= fmin(1.0, fabs(num / den));
-        }
-        zmax = fmax(zmax, sqrt(v));
-    }
+    for (int i = 0; k > 1 && i < k; ++i) zmax = fmax(zmax, sqrt(ritz_last_comp2(th, mu, k, i)));
     return fmax(fabs(th[0]), fabs(th[k - 1])) + sqrt(b2[k - 1]) * zmax;
 }
 
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+constexpr int kBoundWarps = 4;
+
 // Extreme Ritz values by bisection; bound = max(|theta_min|, |theta_max|) + beta_{k+1}
 // (rule 0) or the Ritz-residual rule (rule 1), times (1 + safety), clamped to the
-// Pauli 1-norm pnorm[r].
-__global__ void lanczos_bound_kernel(int R, const double* __restrict__ lmom, int rows,
-                                     const double* __restrict__ beta2, int steps,
-                                     const double* __restrict__ pnorm, double safety, double* emax, int rule) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    double al[64], b2[64];
+// Pauli 1-norm pnorm[r]. One warp per realization: the lanes bisect different
+// eigenvalues (rule 1 needs all k of them and the k - 1 of the leading block). The first
+// `steps` of a run of `stride` Lanczos steps (beta2's row length) enter the bound.
+__global__ void __launch_bounds__(32 * kBoundWarps) lanczos_bound_kernel(int R, const double* __restrict__ lmom,
+                                                                         int rows, const double* __restrict__ beta2,
+                                                                         int steps, int stride,
+                                                                         const double* __restrict__ pnorm,
+                                                                         double safety, double* emax, int rule) {
+    __shared__ double s_al[kBoundWarps][64], s_b2[kBoundWarps][64], s_th[kBoundWarps][64], s_mu[kBoundWarps][64];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * kBoundWarps + wid;
+    if (r >= R) return;                          // uniform per warp; no block-wide barrier follows
+    double* al = s_al[wid];
+    double* b2 = s_b2[wid];
+    double* th = s_th[wid];
+    double* mu = s_mu[wid];
     const int k = steps;
-    double gmax = 0.0;
-    for (int i = 0; i < k; ++i) {
+    for (int i = lane; i < k; i += 32) {
         al[i] = lmom[static_cast<int64_t>(r) * rows + 2 * i + 1];
-        b2[i] = beta2[r * steps + i];
+        b2[i] = beta2[static_cast<int64_t>(r) * stride + i];
     }
-    for (int i = 0; i < k; ++i) {
-        const double bl = i > 0 ? sqrt(b2[i - 1]) : 0.0;
-        const double br = i < k - 1 ? sqrt(b2[i]) : 0.0;
-        gmax = fmax(gmax, fabs(al[i]) + bl + br);
+    __syncwarp();
+    double gmax = 0.0;
+    for (int i = lane; i < k; i += 32) gmax = fmax(gmax, tridiag_gmax_row(al, b2, k, i));
+    gmax = warp_max_d(gmax);
+    double bound;
+    if (rule == 1) {
+        for (int i = lane; i < k; i += 32) th[i] = tridiag_eig(al, b2, k, i, gmax);
+        for (int i = lane; i < k - 1; i += 32) mu[i] = tridiag_eig(al, b2, k - 1, i, gmax);
+        __syncwarp();
+        double zmax = k == 1 ? 1.0 : 0.0;
+        for (int i = lane; k > 1 && i < k; i += 32) zmax = fmax(zmax, sqrt(ritz_last_comp2(th, mu, k, i)));
+        zmax = warp_max_d(zmax);
+        bound = (fmax(fabs(th[0]), fabs(th[k - 1])) + sqrt(b2[k - 1]) * zmax) * (1.0 + safety);
+    } else {
+        double t = 0.0;
+        if (lane < 2) t = tridiag_eig(al, b2, k, lane == 0 ? 0 : k - 1, gmax);
+        const double tmin = __shfl_sync(0xffffffffu, t, 0), tmax = __shfl_sync(0xffffffffu, t, 1);
+        bound = (fmax(fabs(tmin), fabs(tmax)) + sqrt(b2[k - 1])) * (1.0 + safety);
     }
-    double lo = -gmax - 1.0, hi = gmax + 1.0;
-    for (int it = 0; it < 200; ++it) {          // theta_min: count(x) >= 1
-        const double mid = 0.5 * (lo + hi);
-        if (sturm_count(al, b2, k, mid) >= 1) hi = mid; else lo = mid;
-    }
-    const double tmin = 0.5 * (lo + hi);
-    lo = -gmax - 1.0; hi = gmax + 1.0;
-    for (int it = 0; it < 200; ++it) {          // theta_max: count(x) >= k
-        const double mid = 0.5 * (lo + hi);
-        if (sturm_count(al, b2, k, mid) >= k) hi = mid; else lo = mid;
-    }
-    const double tmax = 0.5 * (lo + hi);
-    double bound = (fmax(fabs(tmin), fabs(tmax)) + sqrt(b2[k - 1])) * (1.0 + safety);
-    if (rule == 1) bound = ritz_rule_bound(al, b2, k) * (1.0 + safety);
-    emax[r] = fmin(bound, pnorm[r]);
+    if (lane == 0) emax[r] = fmin(bound, pnorm[r]);
 }
 
 // Kernel-polynomial window: mu_j = 2 P_j - P_{j mod 2} (j < M) of the
@@ -263,9 +291,11 @@ cudaError_t launch_lanczos_scale(int prec, const Item* items, const RealInfo* re
     return cudaGetLastError();
 }
 
-cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps,
+cudaError_t launch_lanczos_bound(int R, const double* lmom, int rows, const double* beta2, int steps, int stride,
                                  const double* pnorm, double safety, double* emax, int rule, cudaStream_t st) {
-    lanczos_bound_kernel<<<(R + 63) / 64, 64, 0, st>>>(R, lmom, rows, beta2, steps, pnorm, safety, emax, rule);
+    if (steps < 1 || steps > stride || steps > 64) return cudaErrorInvalidValue;
+    lanczos_bound_kernel<<<(R + kBoundWarps - 1) / kBoundWarps, 32 * kBoundWarps, 0, st>>>(
+        R, lmom, rows, beta2, steps, stride, pnorm, safety, emax, rule);
     return cudaGetLastError();
 }
 
@@ -332,11 +362,7 @@ extern "C" dacp_status dacp_test_emax_rule(int k, const double* alpha, const dou
         return DACP_OK;
     }
     double gmax = 0.0;
-    for (int i = 0; i < k; ++i) {
-        const double bl = i > 0 ? sqrt(beta2[i - 1]) : 0.0;
-        const double br = i < k - 1 ? sqrt(beta2[i]) : 0.0;
-        gmax = fmax(gmax, fabs(alpha[i]) + bl + br);
-    }
+    for (int i = 0; i < k; ++i) gmax = fmax(gmax, dacp::tridiag_gmax_row(alpha, beta2, k, i));
     const double tmin = dacp::tridiag_eig(alpha, beta2, k, 0, gmax);
     const double tmax = dacp::tridiag_eig(alpha, beta2, k, k - 1, gmax);
     *bound = fmax(fabs(tmin), fabs(tmax)) + sqrt(beta2[k - 1]);

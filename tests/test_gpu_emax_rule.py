@@ -8,9 +8,17 @@ theory, so it is checked here where the exact spectral radius is known: the
 four N = 14 benchmark shards and the N = 16 mixed-field chain, whose extreme
 levels are stored in tests/golden (dense eigh, oracle-only scripts).
 
-  * E_max from the device (20 Lanczos steps on column 0 of the start block,
-    eigenvector-free interlacing form) equals oracle.params.emax_bound(rule=
-    "ritz") to 1e-9 relative, and is never below the exact radius;
+  * E_max from the device (64 Lanczos steps on column 0 of the start block:
+    rule 1 runs the recurrence on past rule 0's 20 steps; eigenvector-free
+    interlacing form) equals oracle.params.emax_bound(rule="ritz", steps=64)
+    to 1e-5 relative, and is never below the exact radius (1.08 and 1.066
+    times it on the shards and the chain). The tolerance is the recurrence's
+    own sensitivity: without reorthogonalisation the Lanczos vectors lose
+    orthogonality, and a start vector perturbed by 1e-15 relative moves the
+    64-step bound of the uniform chain by 1.0e-6 relative (of the shards by
+    8e-15); the interlacing form itself matches eigh of the same tridiagonal
+    to rounding (dacp_test_emax_rule). Rule 0's 20-step bound matches the
+    oracle to 1e-9;
   * it is smaller than rule 0's bound, so the filter order K and the last
     basis order k_n shrink with it;
   * the levels computed with it still meet the float64 target: within 1e-9
@@ -62,8 +70,10 @@ def _run_rule1(models, psis, n_eigs):
 
 def _check_bounds(models, psis, p1, p0, radii):
     for r, m in enumerate(models):
-        ref = OP.emax_bound(m, psis[r][:, 0], steps=20, rule="ritz")
-        assert abs(p1["emax"][r] - ref) <= 1e-9 * ref, (r, p1["emax"][r], ref)
+        ref = OP.emax_bound(m, psis[r][:, 0], steps=64, rule="ritz")
+        ref0 = OP.emax_bound(m, psis[r][:, 0], steps=20, rule="residual")
+        assert abs(p0["emax"][r] - ref0) <= 1e-9 * ref0, (r, p0["emax"][r], ref0)
+        assert abs(p1["emax"][r] - ref) <= 1e-5 * ref, (r, p1["emax"][r], ref)
         assert p1["emax"][r] >= radii[r], (r, p1["emax"][r], radii[r])
         assert p1["emax"][r] < p0["emax"][r]
         assert p1["K"][r] < p0["K"][r] and p1["kn"][r] < p0["kn"][r]
