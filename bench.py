@@ -409,10 +409,11 @@ def run_gpu(args, wl, rank, world):
     mlp = None
     if args.params == "mlp":
         from paper_2011_02107_gb300 import train_mlp
-        if os.path.exists(train_mlp.DEFAULT_PATH):
-            z = np.load(train_mlp.DEFAULT_PATH)
+        path = args.weights or train_mlp.DEFAULT_PATH
+        if os.path.exists(path):
+            z = np.load(path)
             if str(z["precision"]) == wl["prec"]:          # knobs are learned per vector precision
-                mlp = train_mlp.load(stream=stream.cuda_stream)
+                mlp = train_mlp.load(path, stream=stream.cuda_stream)
 
     # ---- value: inputs resident on the device, K whole-path steps
     sectors = use_sectors(args, wl)
@@ -681,6 +682,7 @@ def main():
     ap.add_argument("--sectors", default="auto", choices=["auto", "on", "off"],
                     help="solve each realization as its two parity sectors (auto: for the spin-glass shards, "
                          "which have no z-fields)")
+    ap.add_argument("--weights", default=None, help="parameter-network weights file (default: the shipped one)")
     ap.add_argument("--sector-share", type=float, default=SECTOR_SHARE,
                     help="levels asked of each parity sector, as a fraction of n_eigs")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)

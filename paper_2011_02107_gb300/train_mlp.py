@@ -57,15 +57,28 @@ LABEL_MARGIN = 0.25          # labels must meet LABEL_MARGIN * SPACING_TOL
 MIN_PASS = 0.99              # eligible knob settings keep every level on >= 99 % of the problems
 
 
-def make_problems(n, seed=0):
+# problem mixes: (sizes, their weights, requested fractions of the spectrum per size)
+MIXES = {
+    "small": ((10, 11, 12, 13, 14), (0.22, 0.22, 0.22, 0.2, 0.14), {N: (0.012, 0.025, 0.05) for N in range(10, 15)}),
+    # N = 12-16; the larger shards ask for smaller fractions (the N = 18 workload asks for 0.76 %)
+    "large": ((12, 13, 14, 15, 16), (0.33, 0.28, 0.22, 0.11, 0.06),
+              {12: (0.012, 0.025), 13: (0.012, 0.025), 14: (0.012, 0.025), 15: (0.008, 0.015), 16: (0.008, 0.015)}),
+}
+# levels asked of each parity sector, as a fraction of the model's n_eigs (the two sectors share the
+# central levels about evenly)
+SECTOR_SHARE = 0.55
+
+
+def make_problems(n, seed=0, mix="small"):
     """Spin-glass shards of varied size, coupling scale and requested count."""
+    sizes, weights, fracs = MIXES[mix]
     rng = np.random.default_rng(seed)
     probs = []
     for i in range(n):
-        N = int(rng.choice([10, 11, 12, 13, 14], p=[0.22, 0.22, 0.22, 0.2, 0.14]))
+        N = int(rng.choice(sizes, p=weights))
         js = float(rng.choice([0.5, 1.0, 1.5]))
         m = W.spin_glass_shard(N, seed=10_000 + i, j_scale=js)
-        frac = float(rng.choice([0.012, 0.025, 0.05]))
+        frac = float(rng.choice(fracs[N]))
         n_eigs = max(20, int(frac * (1 << N)))
         probs.append((m, n_eigs))
     return probs
@@ -92,13 +105,21 @@ def accurate(eigs, ref):
     return bool(err.max() <= SPACING_TOL), float(err.max())
 
 
-def run_batch(probs, b, prec, knobs=None, n_eigs_all=None):
-    """One handle over problems sharing N; returns per-problem (eigs, params)."""
+def run_batch(probs, b, prec, knobs=None, sectors=False, rule=0):
+    """One handle over problems sharing N; returns per-realization (eigs, params). With sectors,
+    the realizations are the two parity sectors of each problem (2 j, 2 j + 1), each asked for
+    SECTOR_SHARE of the problem's levels."""
     models = [m for m, _ in probs]
-    psis = [W.start_vectors(m["N"], b, seed=1, r=i) for i, m in enumerate(models)]
     n_eigs = max(ne for _, ne in probs)
-    d = P.Dacp(models, psis, block_b=b, precision=prec)
+    if sectors:
+        psis = [p for i, m in enumerate(models) for p in W.sector_start_vectors(m["N"], b, seed=1, r=i)]
+        n_eigs = int(math.ceil(SECTOR_SHARE * n_eigs))
+        d = P.Dacp.parity_sectors(models, psis, block_b=b, precision=prec)
+    else:
+        psis = [W.start_vectors(m["N"], b, seed=1, r=i) for i, m in enumerate(models)]
+        d = P.Dacp(models, psis, block_b=b, precision=prec)
     try:
+        d.set_emax_rule(rule)
         if knobs is None:
             d.choose_params(n_eigs)
         else:
@@ -181,6 +202,11 @@ def main():
     ap.add_argument("--margin", type=float, default=LABEL_MARGIN)
     ap.add_argument("--min-pass", type=float, default=MIN_PASS)
     ap.add_argument("--relabel", default=None, help="retrain from the tables of this .npz")
+    ap.add_argument("--mix", default="small", choices=sorted(MIXES), help="problem sizes and requested fractions")
+    ap.add_argument("--sectors", default="no", choices=["no", "yes", "both"],
+                    help="label the problems' parity-sector realizations (N - 1 spins), or both kinds")
+    ap.add_argument("--emax-rule", type=int, default=1, choices=[0, 1],
+                    help="E_max rule of the labelling runs (1: the benchmark's)")
     args = ap.parse_args()
     t0 = time.time()
     if args.relabel:
@@ -192,28 +218,47 @@ def main():
     else:
         prec = {"fp32": P.DACP_FP32, "df32": P.DACP_DF32, "fp64": P.DACP_FP64}[args.precision]
         WINDOW_RATIOS, C_ORDERS, BASIS_RATIOS = GRIDS[args.precision]
-        probs = make_problems(args.problems)
-        # group by N so that one handle batches equal n_eigs / N
+        probs = make_problems(args.problems, mix=args.mix)
+        kinds = {"no": (False,), "yes": (True,), "both": (False, True)}[args.sectors]
+        # group by N so that one handle batches equal n_eigs / N; each group once per kind
         groups = {}
         for i, (m, ne) in enumerate(probs):
             groups.setdefault((m["N"], ne), []).append(i)
         grid = list(itertools.product(WINDOW_RATIOS, C_ORDERS, BASIS_RATIOS))
-        feats = np.zeros((len(probs), P.N_FEATURES), np.float32)
-        errs = np.full((len(probs), len(grid)), np.inf)
-        costs = np.full((len(probs), len(grid)), np.inf)
-        for (N, ne), idx in sorted(groups.items()):
+        rows = {}
+        n_rows = 0
+        for key, idx in sorted(groups.items()):
+            for sec in kinds:
+                rows[key + (sec,)] = (n_rows, idx)
+                n_rows += len(idx) * (2 if sec else 1)
+        feats = np.zeros((n_rows, P.N_FEATURES), np.float32)
+        errs = np.full((n_rows, len(grid)), np.inf)
+        costs = np.full((n_rows, len(grid)), np.inf)
+        done = np.zeros(n_rows, dtype=bool)
+        for (N, ne, sec), (row0, idx) in sorted(rows.items()):
             sub = [probs[i] for i in idx]
-            ref, nf_ref, _, f, _ = run_batch(sub, args.b, P.DACP_FP64)
-            feats[idx] = f
+            ne_r = int(math.ceil(SECTOR_SHARE * ne)) if sec else ne
+            Nr = N - 1 if sec else N
+            nr = len(idx) * (2 if sec else 1)
+            ref, nf_ref, _, f, _ = run_batch(sub, args.b, P.DACP_FP64, sectors=sec)
+            feats[row0:row0 + nr] = f
             for gi, kn in enumerate(grid):
-                eigs, nf, prm, _, _ = run_batch(sub, args.b, prec, knobs=kn)
-                for j, i in enumerate(idx):
-                    if nf_ref[j] < ne or nf[j] < ne:
+                eigs, nf, prm, _, _ = run_batch(sub, args.b, prec, knobs=kn, sectors=sec, rule=args.emax_rule)
+                for j in range(nr):
+                    if nf_ref[j] < ne_r or nf[j] < ne_r:
                         continue
-                    _, err = accurate(np.asarray(eigs[j])[:ne], np.asarray(ref[j])[:ne])
-                    errs[i, gi] = err
-                    costs[i, gi] = cost(N, args.b, prm, j)
-            print(f"N={N} n_eigs={ne}: {len(idx)} problems labelled ({time.time() - t0:.0f}s)", flush=True)
+                    _, err = accurate(np.asarray(eigs[j])[:ne_r], np.asarray(ref[j])[:ne_r])
+                    errs[row0 + j, gi] = err
+                    costs[row0 + j, gi] = cost(Nr, args.b, prm, j)
+            done[row0:row0 + nr] = True
+            print(f"N={N} n_eigs={ne} sectors={sec}: {nr} realizations labelled ({time.time() - t0:.0f}s)",
+                  flush=True)
+            # the rows labelled so far, in a form --relabel reads (a cut-short run still trains)
+            np.savez(args.out + ".partial.npz", features=feats[done], errs=errs[done], costs=costs[done],
+                     grid=np.array(grid), precision=args.precision,
+                     meta=json.dumps({"b": args.b, "mix": args.mix, "sectors": args.sectors,
+                                      "emax_rule": args.emax_rule, "rows": int(done.sum()),
+                                      "seconds": time.time() - t0}))
     r = label_and_train(feats, errs, costs, grid, args.margin, args.epochs, min_pass=args.min_pass)
     ok_count = (errs <= SPACING_TOL).sum(0)
     np.savez(args.out, weights=r["weights"], in_mean=r["in_mean"], in_std=r["in_std"], out_mean=r["out_mean"],
@@ -221,6 +266,8 @@ def main():
              grid=np.array(grid), labels=r["labels"], features=feats, errs=errs, costs=costs,
              precision=args.precision,
              meta=json.dumps({"problems": int(len(feats)), "b": args.b, "epochs": args.epochs,
+                              "mix": getattr(args, "mix", "small"), "sectors": getattr(args, "sectors", "no"),
+                              "emax_rule": getattr(args, "emax_rule", 0),
                               "final_loss": r["loss"], "precision": args.precision, "margin": args.margin,
                               "min_pass": args.min_pass,
                               "grid_ok_counts": ok_count.tolist(), "seconds": time.time() - t0}))
