@@ -76,10 +76,15 @@ def make_inputs(wl, rank=0):
 
 
 # Levels asked of each parity sector when a model is solved as its two sectors: the two sectors
-# share the central levels about evenly (the larger held at most 0.503 of the 300 central levels of
-# N = 13 shards, by dense eigh), so 0.55 n_eigs each leaves a margin of 0.05 n_eigs per sector. The
-# merge returns fewer levels, never wrong ones, when a sector falls short; the line counts those.
-SECTOR_SHARE = 0.55
+# share the central levels about evenly (by dense eigh, the larger held at most 1-3 levels more than
+# half: 33 of 60 at N = 10, 102 of 200 at N = 12, 151 of 300 at N = 13), so each is asked for half
+# plus 1 % of n_eigs, at least 5 levels (255 of 500). A model whose merge still comes up short has
+# both sectors solved again, each asked for all n_eigs levels (dacp_solve_sectors); the line counts
+# those models.
+def sector_levels(n_eigs, share=None):
+    if share:
+        return int(np.ceil(share * n_eigs))
+    return int(np.ceil(0.5 * n_eigs + max(5.0, 0.01 * n_eigs)))
 
 
 def use_sectors(args, wl):
@@ -457,7 +462,7 @@ def run_gpu(args, wl, rank, world):
         # built in the library; levels merged per shard (dacp_merge_sectors) inside the step
         sec_psis = sector_inputs(wl, rank)
         d = P.Dacp.parity_sectors(models, sec_psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
-        n_run = int(np.ceil(args.sector_share * n_eigs))
+        n_run = sector_levels(n_eigs, args.sector_share)
     else:
         d = P.Dacp(models, psis, block_b=wl["b"], precision=prec, stream=stream.cuda_stream)
         n_run = n_eigs
@@ -470,11 +475,13 @@ def run_gpu(args, wl, rank, world):
     short = [0]
 
     def step():
+        if sectors:
+            # solve, merge per shard, and re-solve any shard whose merge came up short (library)
+            eigs, nf, nre = d.solve_sectors(n_eigs, n_run, mlp=mlp)
+            short[0] += nre
+            return eigs, nf, None
         eigs, nf, rank, nfb = d.solve(n_run, mlp=mlp)
         fallbacks[0] += nfb
-        if sectors:
-            eigs, nf = P.merge_sector_levels(eigs, nf, n_eigs)
-            short[0] += int(np.sum(np.asarray(nf) < n_eigs))
         return eigs, nf, rank
 
     for _ in range(args.warmup):
@@ -595,7 +602,7 @@ def run_gpu(args, wl, rank, world):
     psi_pinned = pin.numpy()
     h2d = psi_pinned.nbytes + J.nbytes + h.nbytes + g.nbytes + n_spins.nbytes
     R_run = 2 * R if sectors else R
-    d2h = R_run * n_run * 8 + 2 * R_run * 4
+    d2h = R * n_eigs * 8 + R * 4 if sectors else R_run * n_run * 8 + 2 * R_run * 4
     e2e_steps = max(0, min(args.steps, args.e2e_steps))
     dist_barrier()
     torch.cuda.synchronize()
@@ -611,14 +618,14 @@ def run_gpu(args, wl, rank, world):
             P.dacp_autotune(hd)            # cached: only switches the tile size
             if args.emax_rule:
                 P.dacp_set_emax_rule(hd, args.emax_rule)
-            if mlp is not None:           # learned parameters, heuristic re-run in the library
+            if sectors:                   # solve, merge, re-solve short merges: all in the library
+                eigs, nf, _ = P.dacp_solve_sectors(hd, mlp, R, n_eigs, n_run)
+            elif mlp is not None:         # learned parameters, heuristic re-run in the library
                 eigs, nf, rk, _ = P.dacp_solve_learned(hd, mlp, R_run, n_run)
             else:
                 if args.emax_rule:
                     P.dacp_choose_params(hd, n_run)
                 eigs, nf, rk = P.dacp_solve(hd, R_run, n_run)
-            if sectors:
-                eigs, nf = P.dacp_merge_sectors(eigs, nf, n_eigs)
             found_e2e += int(np.clip(nf, 0, None).sum())
         finally:
             P.dacp_destroy(hd)
@@ -684,7 +691,7 @@ def run_gpu(args, wl, rank, world):
         "residual_check": residual_check,
         "fp64_same_gpu": fp64_arm,
         "fallback_realizations": fallbacks[0],
-        "sector_merges_short": short[0] if sectors else None,
+        "sector_models_resolved": short[0] if sectors else None,
         "tile_bytes": tile_bytes,
         "launch_mode": launch_mode,
         "roofline": roof,
@@ -727,8 +734,9 @@ def main():
     ap.add_argument("--weights", default=None, help="parameter-network weights file (default: the shipped one)")
     ap.add_argument("--no-hbm-4x-l2", dest="hbm_4x_l2", action="store_false",
                     help="skip the float32 H.v bandwidth measurement at a working set of 4x L2")
-    ap.add_argument("--sector-share", type=float, default=SECTOR_SHARE,
-                    help="levels asked of each parity sector, as a fraction of n_eigs")
+    ap.add_argument("--sector-share", type=float, default=None,
+                    help="levels asked of each parity sector, as a fraction of n_eigs (default: half plus 1 %%, "
+                         "at least 5 levels)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--budget", type=float, default=15.0, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-rank", type=int, default=0, help=argparse.SUPPRESS)

@@ -157,6 +157,7 @@ dacp_status dacp_create_parity_sectors(dacp_handle* out, int n_real, const int* 
 dacp_status dacp_merge_sectors(int n_real, int n_in, const double* eigs_in, const int* n_found_in, int n_eigs,
                                double* eigs, int* n_found);
 
+
 /*
  * dacp_set_params -- explicit per-realization parameters (arrays of n_real).
  *   emax  bound on |E| (E_min = -E_max, Sec. II A); must be a true bound.
@@ -537,6 +538,28 @@ dacp_status dacp_choose_params_mlp(dacp_handle hd, dacp_mlp m, int n_eigs, int l
  */
 dacp_status dacp_solve_learned(dacp_handle hd, dacp_mlp net, int n_eigs, double window, double eps, double* eigs,
                                int* n_found, int* rank, int* n_fallback);
+
+/*
+ * dacp_solve_sectors -- the whole path on a dacp_create_parity_sectors handle,
+ * with levels per model: each sector is asked for n_sector levels (parameters
+ * from `net` with dacp_solve_learned's fallback when net is not NULL, else the
+ * Sec. III heuristic under the handle's E_max rule), the two sectors of every
+ * model are merged (dacp_merge_sectors), and every model whose merge comes up
+ * short of n_eigs -- its sectors split the central levels more unevenly than
+ * n_sector allows -- or whose sector failed has both sectors solved again on
+ * a handle of their own (E_max rule 0, the heuristic), each asked for all
+ * n_eigs levels, which the union then always covers.
+ *   n_eigs     levels wanted per model; n_sector in [1, n_eigs] per sector
+ *              (the central levels split about evenly: a little above
+ *              n_eigs / 2 is enough almost always).
+ *   eigs       [R/2][n_eigs] float64 host buffer, n_found [R/2] host ints
+ *              (as dacp_merge_sectors writes them).
+ *   n_redone   models solved again (may be NULL).
+ * Errors: DACP_ERR_ARG for a handle not made by dacp_create_parity_sectors or
+ * bad sizes; the errors of dacp_solve / dacp_solve_learned.
+ */
+dacp_status dacp_solve_sectors(dacp_handle hd, dacp_mlp net, int n_eigs, int n_sector, double* eigs, int* n_found,
+                               int* n_redone);
 
 /* dacp_get_features -- the 40 network features of every realization
  * (float32, [n_real][40]) from the last parameter choice. */

@@ -38,7 +38,7 @@ EXPORTS = ["dacp_create", "dacp_set_params", "dacp_choose_params", "dacp_get_par
            "dacp_test_poison_barrier", "dacp_moments_noalloc", "dacp_set_solver", "dacp_set_pair_couplings",
            "dacp_set_emax_rule", "dacp_test_emax_rule", "dacp_solve_learned",
            "dacp_lanczos_filtered", "dacp_set_global_flips", "dacp_create_parity_sectors",
-           "dacp_merge_sectors", "dacp_test_fail_alloc"]
+           "dacp_merge_sectors", "dacp_test_fail_alloc", "dacp_solve_sectors"]
 
 N_FEATURES = 40
 N_KNOBS = 3
@@ -74,6 +74,7 @@ def _load():
         "dacp_residuals": [P, I, I, D, D, P, P, P],
         "dacp_solve": [P, I, D, D, P, P, P],
         "dacp_solve_learned": [P, P, I, D, D, P, P, P, P],
+        "dacp_solve_sectors": [P, P, I, I, P, P, P],
         "dacp_lanczos_filtered": [P, I, I, I, D, P, P, P, P, ctypes.POINTER(L)],
         "dacp_set_global_flips": [P, P],
         "dacp_create_parity_sectors": [ctypes.POINTER(P), I, P, P, P, P, I, I, P, P],
@@ -209,6 +210,17 @@ def dacp_solve_learned(hd, m, R, n_eigs, window=0.0, eps=0.0):
     _check(hd, _lib.dacp_solve_learned(hd, m, int(n_eigs), float(window), float(eps), _ptr(eigs), _ptr(nf),
                                        _ptr(rank), ctypes.byref(nfb)))
     return eigs.reshape(R, n_eigs), nf, rank, nfb.value
+
+
+def dacp_solve_sectors(hd, m, n_models, n_eigs, n_sector):
+    """Parity-sector handle: solve with n_sector levels per sector (network m or the heuristic),
+    merge per model, re-solve the models whose merge came up short (all in the library).
+    Returns (eigs [n_models, n_eigs], n_found, n_redone)."""
+    eigs = np.zeros(n_models * n_eigs)
+    nf = np.zeros(n_models, dtype=np.int32)
+    nre = ctypes.c_int(0)
+    _check(hd, _lib.dacp_solve_sectors(hd, m, int(n_eigs), int(n_sector), _ptr(eigs), _ptr(nf), ctypes.byref(nre)))
+    return eigs.reshape(n_models, n_eigs), nf, nre.value
 
 
 def dacp_lanczos_filtered(hd, r, steps, n_eigs, res_tol=0.0):
@@ -594,6 +606,14 @@ class Dacp:
             return eigs, nf, rank, 0
         e, nf, rank, nfb = dacp_solve_learned(self.handle, mlp, self.R, n_eigs, window, eps)
         return [e[r, :max(nf[r], 0)].copy() for r in range(self.R)], nf, rank, nfb
+
+    def solve_sectors(self, n_eigs, n_sector, mlp=None):
+        """Parity-sector handle (Dacp.parity_sectors): the levels of each model, merged from its two
+        sectors, with short merges re-solved in the library (dacp_solve_sectors).
+        Returns (eigs list per model, n_found, n_redone)."""
+        nm = self.R // 2
+        e, nf, nre = dacp_solve_sectors(self.handle, mlp, nm, n_eigs, n_sector)
+        return [e[m, :max(nf[m], 0)].copy() for m in range(nm)], nf, nre
 
     def run(self, n_eigs, window=0.0, eps=0.0):
         """Filter, evolution and subspace solves with the solves overlapped (dacp_solve)."""

@@ -96,6 +96,7 @@ struct dacp_ctx {
     std::vector<double> pnorm_pairs;    // sum |Jxx| + |Jyy| of each realization
     std::vector<double> gflip_h;        // coefficient of the global flip X_0 ... X_{N-1} per realization
     bool has_gflip = false;
+    bool sector_pairs = false;          // dacp_create_parity_sectors: realizations 2m, 2m+1 are model m's sectors
     double* gflip_d = nullptr;          // [R]
     std::vector<double> psi0_h;         // the caller's start vectors (packed float64), for re-runs
     int* n_pairs_d = nullptr;           // [R]
@@ -1516,6 +1517,49 @@ dacp_status dacp_solve(dacp_handle c, int n_eigs, double window, double eps, dou
     return DACP_OK;
 }
 
+// A handle over realizations rs of c, built from c's host copies of their couplings, fields, pair
+// couplings, global flips and start vectors (the re-runs of dacp_solve_learned and dacp_solve_sectors).
+static dacp_status sub_handle(dacp_ctx* c, const std::vector<int>& rs, dacp_handle* out) {
+    const int nr = static_cast<int>(rs.size()), b = c->b;
+    std::vector<int64_t> psi_off(c->R + 1, 0), j_off(c->R + 1, 0);
+    for (int r = 0; r < c->R; ++r) {
+        psi_off[r + 1] = psi_off[r] + (static_cast<int64_t>(1) << c->N[r]) * b;
+        j_off[r + 1] = j_off[r] + static_cast<int64_t>(c->N[r]) * c->N[r];
+    }
+    std::vector<int> ns;
+    std::vector<double> J, h, g, psi, jxx, jyy;
+    for (int r : rs) {
+        const int Nr = c->N[r];
+        ns.push_back(Nr);
+        for (int i = 0; i < Nr; ++i) {
+            h.push_back(c->h_h[static_cast<size_t>(r) * kMaxSpins + i]);
+            g.push_back(c->g_h[static_cast<size_t>(r) * kMaxSpins + i]);
+            for (int j = 0; j < Nr; ++j)
+                J.push_back(c->J_h[static_cast<size_t>(r) * kMaxSpins * kMaxSpins + i * kMaxSpins + j]);
+        }
+        psi.insert(psi.end(), c->psi0_h.begin() + psi_off[r], c->psi0_h.begin() + psi_off[r + 1]);
+        if (c->has_pairs) {
+            jxx.insert(jxx.end(), c->jxx_h.begin() + j_off[r], c->jxx_h.begin() + j_off[r + 1]);
+            jyy.insert(jyy.end(), c->jyy_h.begin() + j_off[r], c->jyy_h.begin() + j_off[r + 1]);
+        }
+    }
+    dacp_handle sub = nullptr;
+    dacp_status st = dacp_create(&sub, nr, ns.data(), J.data(), h.data(), g.data(), b, c->prec, psi.data(), c->st);
+    if (st != DACP_OK) return st;
+    if (c->has_pairs) st = dacp_set_pair_couplings(sub, jxx.data(), jyy.data());
+    if (st == DACP_OK && c->has_gflip) {
+        std::vector<double> gsub;
+        for (int r : rs) gsub.push_back(c->gflip_h[r]);
+        st = dacp_set_global_flips(sub, gsub.data());
+    }
+    if (st != DACP_OK) {
+        dacp_destroy(sub);
+        return st;
+    }
+    *out = sub;
+    return DACP_OK;
+}
+
 // Realizations whose learned parameters returned fewer than n_eigs levels go
 // through the heuristic on a handle of their own, built from this handle's host
 // copies of their couplings, fields and start vectors.
@@ -1533,40 +1577,12 @@ dacp_status dacp_solve_learned(dacp_handle c, dacp_mlp net, int n_eigs, double w
         if (n_found[r] < n_eigs) redo.push_back(r);
     if (n_fallback) *n_fallback = static_cast<int>(redo.size());
     if (redo.empty()) return DACP_OK;
-    const int nr = static_cast<int>(redo.size()), b = c->b;
-    std::vector<int64_t> psi_off(c->R + 1, 0), j_off(c->R + 1, 0);
-    for (int r = 0; r < c->R; ++r) {
-        psi_off[r + 1] = psi_off[r] + (static_cast<int64_t>(1) << c->N[r]) * b;
-        j_off[r + 1] = j_off[r] + static_cast<int64_t>(c->N[r]) * c->N[r];
-    }
-    std::vector<int> ns;
-    std::vector<double> J, h, g, psi, jxx, jyy;
-    for (int r : redo) {
-        const int Nr = c->N[r];
-        ns.push_back(Nr);
-        for (int i = 0; i < Nr; ++i) {
-            h.push_back(c->h_h[static_cast<size_t>(r) * kMaxSpins + i]);
-            g.push_back(c->g_h[static_cast<size_t>(r) * kMaxSpins + i]);
-            for (int j = 0; j < Nr; ++j)
-                J.push_back(c->J_h[static_cast<size_t>(r) * kMaxSpins * kMaxSpins + i * kMaxSpins + j]);
-        }
-        psi.insert(psi.end(), c->psi0_h.begin() + psi_off[r], c->psi0_h.begin() + psi_off[r + 1]);
-        if (c->has_pairs) {
-            jxx.insert(jxx.end(), c->jxx_h.begin() + j_off[r], c->jxx_h.begin() + j_off[r + 1]);
-            jyy.insert(jyy.end(), c->jyy_h.begin() + j_off[r], c->jyy_h.begin() + j_off[r + 1]);
-        }
-    }
+    const int nr = static_cast<int>(redo.size());
     dacp_handle sub = nullptr;
-    dacp_status st = dacp_create(&sub, nr, ns.data(), J.data(), h.data(), g.data(), b, c->prec, psi.data(), c->st);
+    dacp_status st = sub_handle(c, redo, &sub);
     if (st != DACP_OK) return fail(c, st, "heuristic re-run: set-up failed");
     std::vector<double> e2(static_cast<size_t>(nr) * n_eigs, 0.0);
     std::vector<int> nf2(nr, 0), rk2(nr, 0);
-    if (c->has_pairs) st = dacp_set_pair_couplings(sub, jxx.data(), jyy.data());
-    if (st == DACP_OK && c->has_gflip) {
-        std::vector<double> gsub;
-        for (int r : redo) gsub.push_back(c->gflip_h[r]);
-        st = dacp_set_global_flips(sub, gsub.data());
-    }
     if (st == DACP_OK) st = dacp_set_emax_rule(sub, 0);      // the true bound: also recovers a rule-1 failure
     if (st == DACP_OK) st = dacp_choose_params(sub, n_eigs, 2.0, 1.5, 0.0, 20, 256);
     if (st == DACP_OK) st = dacp_solve(sub, n_eigs, window, eps, e2.data(), nf2.data(), rk2.data());
@@ -2258,6 +2274,7 @@ dacp_status dacp_create_parity_sectors(dacp_handle* out, int n_real, const int* 
         dacp_destroy(c);
         return st;
     }
+    c->sector_pairs = true;
     *out = c;
     return DACP_OK;
 }
@@ -2295,6 +2312,60 @@ dacp_status dacp_merge_sectors(int n_real, int n_in, const double* eigs_in, cons
         }
         std::sort(eigs + static_cast<int64_t>(r) * n_eigs, eigs + static_cast<int64_t>(r) * n_eigs + cnt);
         n_found[r] = cnt;
+    }
+    return DACP_OK;
+}
+
+dacp_status dacp_solve_sectors(dacp_handle c, dacp_mlp net, int n_eigs, int n_sector, double* eigs, int* n_found,
+                               int* n_redone) {
+    NvtxRange nvtx_("dacp_solve_sectors");
+    TRY(check_handle(c));
+    if (!c->sector_pairs) return fail(c, DACP_ERR_ARG, "not a parity-sector handle (dacp_create_parity_sectors)");
+    if (n_eigs < 1 || n_sector < 1 || n_sector > n_eigs || !eigs || !n_found)
+        return fail(c, DACP_ERR_ARG, "need 1 <= n_sector <= n_eigs and output buffers");
+    const int nm = c->R / 2;
+    if (n_redone) *n_redone = 0;
+    std::vector<double> es(static_cast<size_t>(c->R) * n_sector, 0.0);
+    std::vector<int> nfs(c->R, 0);
+    if (net) {
+        TRY(dacp_solve_learned(c, net, n_sector, 0.0, 0.0, es.data(), nfs.data(), nullptr, nullptr));
+    } else {
+        TRY(dacp_choose_params(c, n_sector, 2.0, 1.5, 0.0, 20, 256));
+        TRY(dacp_solve(c, n_sector, 0.0, 0.0, es.data(), nfs.data(), nullptr));
+    }
+    TRY(dacp_merge_sectors(nm, n_sector, es.data(), nfs.data(), n_eigs, eigs, n_found));
+    // models whose merge came up short (or whose sectors failed): both sectors again, each asked for
+    // all n_eigs levels, so the union's n_eigs central levels lie inside both returned radii
+    std::vector<int> redo_m, redo_r;
+    for (int m = 0; m < nm; ++m)
+        if (n_found[m] < n_eigs) {
+            redo_m.push_back(m);
+            redo_r.push_back(2 * m);
+            redo_r.push_back(2 * m + 1);
+        }
+    if (n_redone) *n_redone = static_cast<int>(redo_m.size());
+    if (redo_m.empty()) return DACP_OK;
+    const int nr = static_cast<int>(redo_r.size());
+    dacp_handle sub = nullptr;
+    dacp_status st = sub_handle(c, redo_r, &sub);
+    if (st != DACP_OK) return fail(c, st, "sector re-run: set-up failed");
+    std::vector<double> e2(static_cast<size_t>(nr) * n_eigs, 0.0), em(static_cast<size_t>(nr / 2) * n_eigs, 0.0);
+    std::vector<int> nf2(nr, 0), nfm(nr / 2, 0);
+    st = dacp_set_emax_rule(sub, 0);                 // the true bound: also recovers a rule-1 failure
+    if (st == DACP_OK) st = dacp_choose_params(sub, n_eigs, 2.0, 1.5, 0.0, 20, 256);
+    if (st == DACP_OK) st = dacp_solve(sub, n_eigs, 0.0, 0.0, e2.data(), nf2.data(), nullptr);
+    if (st != DACP_OK) {
+        const std::string msg = dacp_last_error(sub);
+        dacp_destroy(sub);
+        return fail(c, st, "sector re-run: %s", msg.c_str());
+    }
+    c->launches += sub->launches.load();
+    dacp_destroy(sub);
+    TRY(dacp_merge_sectors(nr / 2, n_eigs, e2.data(), nf2.data(), n_eigs, em.data(), nfm.data()));
+    for (size_t j = 0; j < redo_m.size(); ++j) {
+        const int m = redo_m[j];
+        memcpy(eigs + static_cast<size_t>(m) * n_eigs, em.data() + j * n_eigs, sizeof(double) * n_eigs);
+        n_found[m] = nfm[j];
     }
     return DACP_OK;
 }

@@ -51,3 +51,14 @@ def test_roofline_arithmetic():
     wl["prec"] = "fp32"
     r = B.roofline(wl, len(models), phase, 3e12, states, clk, 152)
     assert r["bound"] == "hbm" and abs(r["achieved"] - 3000.0) < 1e-9 and r["unit"] == "GB/s"
+
+
+def test_sector_levels_rule():
+    """Each parity sector is asked for half of n_eigs plus a margin of 1 % (at least 5 levels);
+    --sector-share overrides it."""
+    sys.path.insert(0, ROOT)
+    import bench as B
+    assert [B.sector_levels(n) for n in (60, 100, 500, 2000)] == [35, 55, 255, 1020]
+    for n in (1, 7, 64, 333, 5000):
+        assert n / 2 + 5 <= B.sector_levels(n) <= n / 2 + max(5, 0.01 * n) + 1
+    assert B.sector_levels(500, 0.55) == 275

@@ -144,3 +144,39 @@ def test_apply_h_with_global_flip_tile_specialised_kernel():
             assert (err <= tol).all(), (N, float(err.max()), float((err / scale).max()))
     finally:
         d.close()
+
+
+def test_solve_sectors_resolves_short_merges():
+    """dacp_solve_sectors: with n_sector well below n_eigs / 2 every model's merge comes up short and
+    both its sectors are solved again (each asked for all n_eigs levels): the levels still match
+    dense eigh to 1e-9 of the width. With a comfortable n_sector nothing is redone and the result
+    equals run + merge. A handle that is not a parity-sector handle, and n_sector > n_eigs, are
+    refused."""
+    models = [W.spin_glass_shard(10, seed=s) for s in (21, 22)]
+    n_eigs = 60
+    dense = [np.linalg.eigvalsh(Hm.dense_h(m)) for m in models]
+    for n_sec, redone in ((20, 2), (36, 0)):
+        d = P.Dacp.parity_sectors(models, _sector_starts(models, 4, 3), block_b=4, precision=P.DACP_FP64)
+        try:
+            eigs, nf, nre = d.solve_sectors(n_eigs, n_sec)
+            assert nre == redone and all(int(x) == n_eigs for x in nf)
+            if redone == 0:
+                d.choose_params(n_sec)
+                e, nfr, _ = d.run(n_sec)
+                ref, _ = P.merge_sector_levels(e, nfr, n_eigs)
+                for a, b in zip(eigs, ref):
+                    assert np.array_equal(a, b)
+            with pytest.raises(P.DacpError) as err:
+                d.solve_sectors(n_eigs, n_eigs + 1)
+            assert err.value.status == 1
+        finally:
+            d.close()
+        for r, E in enumerate(dense):
+            assert np.abs(eigs[r] - MT.central_exact(E, n_eigs)).max() <= 1e-9 * (E[-1] - E[0])
+    d = P.Dacp(models, [W.start_vectors(10, 4, seed=3, r=i) for i in range(2)], block_b=4, precision=P.DACP_FP64)
+    try:
+        with pytest.raises(P.DacpError) as err:
+            P.dacp_solve_sectors(d.handle, None, 1, n_eigs, 36)
+        assert err.value.status == 1
+    finally:
+        d.close()
