@@ -64,8 +64,8 @@ MIXES = {
     "large": ((12, 13, 14, 15, 16), (0.33, 0.28, 0.22, 0.11, 0.06),
               {12: (0.012, 0.025), 13: (0.012, 0.025), 14: (0.012, 0.025), 15: (0.008, 0.015), 16: (0.008, 0.015)}),
 }
-# levels asked of each parity sector, as a fraction of the model's n_eigs (the two sectors share the
-# central levels about evenly)
+# levels asked of each parity sector in the labelling runs, as a fraction of the model's n_eigs (the
+# two sectors share the central levels about evenly; the shipped weights were labelled at 0.55)
 SECTOR_SHARE = 0.55
 
 

@@ -84,7 +84,7 @@ def test_learned_parameters_keep_accuracy_and_cut_cost():
 @pytest.mark.skipif(not os.path.exists(WEIGHTS), reason="no trained weights")
 def test_learned_parameters_on_parity_sectors():
     """The benchmark's use of the network: held-out N = 14 shards solved as their parity
-    sectors (275 of 500 levels per sector, E_max rule 1), learned knobs against the
+    sectors (255 of 500 levels per sector, E_max rule 1), learned knobs against the
     heuristic. The merged levels of the learned run must match plain float64 DACP on
     the full shards within 1e-2 of the local spacing, and the learned run must cost
     less, in the GB300 cost model and in the measured T_F + T_E + T_D of a second run
@@ -95,7 +95,7 @@ def test_learned_parameters_on_parity_sectors():
     if str(z["precision"]) != "df32":
         pytest.skip("weights trained for another precision")
     mlp = TM.load(WEIGHTS)
-    N, ne, n_sec = 14, 500, 275
+    N, ne, n_sec = 14, 500, 255
     models = [W.spin_glass_shard(N, seed=s) for s in range(930_000, 930_016)]
     full_psis = [W.start_vectors(N, 4, seed=77, r=i) for i in range(len(models))]
     sec_psis = [p for i in range(len(models)) for p in W.sector_start_vectors(N, 4, seed=77, r=i)]

@@ -7,10 +7,13 @@
     merged by dacp_merge_sectors against the full models' dense spectra, float64, within 1e-9 of
     the width; the merge is exact because the union of the sector spectra is the spectrum (the
     oracle's pin, test_oracle_hamiltonian);
-  * the benchmark's sector path (double-float, heuristic parameters, 300 levels per sector,
-    merged to 500) on the four shards with stored exact levels, within 1e-2 of the local mean
-    spacing (Sec. III accuracy measure).
+  * the benchmark's sector path (double-float, E_max rule 1, the shipped parameter network,
+    255 levels per sector, dacp_solve_sectors merging to 500) on the four shards with stored exact
+    levels, within 1e-2 of the local mean spacing (Sec. III accuracy measure);
+  * dacp_solve_sectors re-solving short merges, and its refusals.
 """
+
+import os
 
 import numpy as np
 import pytest
@@ -97,16 +100,21 @@ def test_sector_path_at_the_benchmark_size_against_exact_levels():
             exact.setdefault(int(row[0]), []).append(float(row[1]))
     seeds = sorted(exact)
     models = [W.spin_glass_shard(14, seed=s) for s in seeds]
-    n_eigs, n_sec = 500, 300
-    d = P.Dacp.parity_sectors(models, _sector_starts(models, 4, 0), block_b=4, precision=P.DACP_DF32)
+    # the benchmark's start vectors are keyed by the shard's index in its batch, which is its seed
+    psis = [p for s in seeds for p in W.sector_start_vectors(14, 4, seed=0, r=s)]
+    n_eigs, n_sec = 500, 255
+    from paper_2011_02107_gb300 import train_mlp as TM
+    mlp = TM.load() if os.path.exists(TM.DEFAULT_PATH) else None
+    d = P.Dacp.parity_sectors(models, psis, block_b=4, precision=P.DACP_DF32)
     try:
         d.set_emax_rule(1)
         d.choose_params(n_sec)
-        e, nf, rank = d.run(n_sec)
+        d.autotune(64)
+        eigs, nf2, _ = d.solve_sectors(n_eigs, n_sec, mlp=mlp)
     finally:
         d.close()
-    assert all(int(x) == n_sec for x in nf)
-    eigs, nf2 = P.merge_sector_levels(e, nf, n_eigs)
+        if mlp is not None:
+            P.dacp_mlp_destroy(mlp)
     for j, s in enumerate(seeds):
         lv = np.sort(np.asarray(exact[s]))
         ref = MT.central_exact(lv, n_eigs)
