@@ -42,3 +42,45 @@ def test_parity_sectors_refuse_z_fields_and_tiny_models():
             P.dacp_create_parity_sectors(nsp, J[:nsp[0] ** 2], h[:nsp[0]], np.ones(nsp[0]), 1, 0,
                                          np.zeros(2 * (1 << max(nsp[0] - 1, 0))))
         assert e.value.status == 1
+
+
+def test_merge_of_dense_sector_spectra_gives_the_full_central_levels():
+    """The library's host merge on real spectra: each sector's n_sec levels of smallest |E| (dense
+    eigh of the oracle's sector models, reading of the global-flip split) merge to exactly the full
+    model's n central levels (dense eigh of the full model)."""
+    import workloads as W
+    from oracle import hamiltonian as Hm
+    from oracle import metrics as MT
+    for N, n, seed in ((8, 30, 1), (9, 50, 2), (10, 60, 3)):
+        m = W.spin_glass_shard(N, seed=seed)
+        full = np.linalg.eigvalsh(Hm.dense_h(m))
+        n_sec = n // 2 + 6
+        rows, nfs = [], []
+        for ms in Hm.parity_sector_models(m):
+            E = np.linalg.eigvalsh(Hm.dense_h(ms))
+            rows.append(np.sort(E[np.argsort(np.abs(E), kind="stable")[:n_sec]]))
+            nfs.append(n_sec)
+        eigs, nf = P.dacp_merge_sectors(np.stack(rows), np.array(nfs), n)
+        assert nf[0] == n
+        assert np.abs(eigs[0] - MT.central_exact(full, n)).max() < 1e-12 * (full[-1] - full[0])
+
+
+def test_sector_level_rule_covers_the_sector_split():
+    """The benchmark asks each sector for half of n_eigs plus 1 % (at least 5 levels). On 24 shards
+    at N = 10 (60 levels) and 8 at N = 11 (120 levels) the larger sector's share of the central
+    levels, from dense sector spectra, stays at least 2 levels inside that rule."""
+    import os
+    import sys
+    import workloads as W
+    from oracle import hamiltonian as Hm
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench as B
+    for N, n, seeds in ((10, 60, range(24)), (11, 120, range(8))):
+        worst = 0
+        for s in seeds:
+            m = W.spin_glass_shard(N, seed=100 + s)
+            sp = [np.linalg.eigvalsh(Hm.dense_h(ms)) for ms in Hm.parity_sector_models(m)]
+            lab = np.concatenate([np.zeros(len(sp[0])), np.ones(len(sp[1]))])
+            idx = np.argsort(np.abs(np.concatenate(sp)), kind="stable")[:n]
+            worst = max(worst, int(max((lab[idx] == 0).sum(), (lab[idx] == 1).sum())))
+        assert worst + 2 <= B.sector_levels(n), (N, n, worst, B.sector_levels(n))
