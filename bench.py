@@ -602,7 +602,9 @@ def run_gpu(args, wl, rank, world):
     psi_pinned = pin.numpy()
     h2d = psi_pinned.nbytes + J.nbytes + h.nbytes + g.nbytes + n_spins.nbytes
     R_run = 2 * R if sectors else R
-    d2h = R * n_eigs * 8 + R * 4 if sectors else R_run * n_run * 8 + 2 * R_run * 4
+    # the device-to-host copies are the per-realization results (for sectors: of every sector; the
+    # library merges them on the host): levels, counts and ranks
+    d2h = R_run * n_run * 8 + 2 * R_run * 4
     e2e_steps = max(0, min(args.steps, args.e2e_steps))
     dist_barrier()
     torch.cuda.synchronize()
