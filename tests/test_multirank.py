@@ -1,6 +1,7 @@
 """Weak-scaling launch logic of bench.py on world_size 2 with the gloo backend (CPU only).
 
-Each rank draws its own batch (seeds offset by rank, no data-path exchange);
+Each rank draws its own batch (seeds offset by rank, no data-path exchange), its full-model and its
+parity-sector start vectors alike;
 the timed region's length is the max over ranks and the found count the sum.
 """
 
@@ -29,7 +30,9 @@ def _worker(rank, world, port, out):
     import bench
     wl = dict(bench.WORKLOADS["c3"], N=6, R=3)
     models, psis = bench.make_inputs(wl, rank)
-    sig = float(sum(m["J"].sum() for m in models) + sum(p.sum() for p in psis))
+    sec = bench.sector_inputs(wl, rank)              # the parity-sector start blocks of the same batch
+    assert len(sec) == 2 * wl["R"] and all(p.shape == (1 << (wl["N"] - 1), wl["b"]) for p in sec)
+    sig = float(sum(m["J"].sum() for m in models) + sum(p.sum() for p in psis) + sum(p.sum() for p in sec))
     t = bench.reduce_across_ranks(1.0 + rank, "max", world)
     n = bench.reduce_across_ranks(10.0 * (rank + 1), "sum", world)
     sigs = [None] * world
